@@ -1,0 +1,170 @@
+/*
+ * msrcg — recursive multi-scale preconditioned conjugate gradient on GB300.
+ *
+ * C ABI of libmsrcg.so.  Method: Lackner & Menikoff, "Multi-scale linear
+ * solvers for very large systems derived from PDEs" (arXiv math/9809043):
+ * a PCG (Sec. 3, Templates Fig. 2.5) whose preconditioner, eq. (2.10), is m
+ * symmetric Gauss-Seidel steps, a coarse correction E A_c^-1 R in which A_c^-1
+ * is applied by the same PCG one level down (Sec. 2.3), and m more smoothing
+ * steps; the coarsest level is solved exactly.  The operator is the
+ * cell-centred 5-point (2D) / 7-point (3D) discretisation of -div(K grad p)
+ * with harmonic-mean face permeabilities (Sec. 3).
+ *
+ * Conventions shared by every entry point
+ *  - Cells are numbered c = i + nx*(j + ny*k), x fastest.
+ *  - "device" arrays live in the memory of the current CUDA device; the
+ *    caller owns them and keeps them alive until the stream has passed the
+ *    call.  "host" arrays are read before the call returns.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    stream ordered; a call returns once the work is enqueued unless it says
+ *    that it synchronises.
+ *  - Return value: MSRCG_OK (0) or a negative MSRCG_E* code;
+ *    msrcg_strerror() names it.  No entry point falls back to the CPU.
+ */
+#ifndef MSRCG_H
+#define MSRCG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MSRCG_OK 0
+#define MSRCG_EINVAL (-1)      /* malformed argument */
+#define MSRCG_ENOMEM (-2)      /* device allocation failed */
+#define MSRCG_ENOCONV (-3)     /* a level hit its iteration cap */
+#define MSRCG_EBREAKDOWN (-4)  /* p.Ap <= 0 or a non-finite CG scalar */
+#define MSRCG_ETIMEOUT (-5)    /* a bounded device wait ran out */
+#define MSRCG_ENANINF (-6)     /* non-finite value in b */
+#define MSRCG_ECUDA (-7)       /* a CUDA runtime call failed */
+
+#define MSRCG_MAXLEV 16
+
+/* Grid: dim = 2 or 3; n = cells per axis (n[2] ignored in 2D); h = cell
+ * sizes (h[2] ignored in 2D). */
+typedef struct {
+  int dim;
+  int n[3];
+  double h[3];
+} msrcg_grid;
+
+/* Method parameters (Sec. 3): scale factor s (about 4), smoothing degree m
+ * (= s), level tolerance factor f (0.1), coarsest side limit (a level whose
+ * every side is <= this is the coarsest; 0 = 8 in 2D, 4 in 3D), precision
+ * (0 = FP64 everywhere, 1 = FP32 preconditioner inside the FP64 outer PCG),
+ * iteration caps per level-0 PCG / inner PCG call, the bound of every
+ * device-side wait in nanoseconds, and inner_floor (precision 1 only: an
+ * inner level also stops once ||r_k|| < inner_floor ||b_k||; 0 disables). */
+typedef struct {
+  int scale;
+  int m;
+  double f;
+  int coarsest_max_side;
+  int precision;
+  int maxit_outer;
+  int maxit_inner;
+  uint64_t timeout_ns;
+  double inner_floor;
+  int small_cells;   /* levels with at most this many cells run in one CTA; 0 = default */
+  int reserved[7];
+} msrcg_opts;
+
+/* Per-solve statistics.  iters[k] = PCG iterations summed over all calls at
+ * level k, calls[k] = PCG invocations at level k (Table 1 of the paper). */
+typedef struct {
+  int levels;
+  int dims[MSRCG_MAXLEV][3];
+  int64_t iters[MSRCG_MAXLEV];
+  int64_t calls[MSRCG_MAXLEV];
+  double relres_recursive;  /* ||r||/||b|| of the level-0 recursion */
+  double relres_true;       /* ||b - A x|| / ||b||, recomputed at the end */
+  int status;
+  int restarts;
+} msrcg_stats;
+
+typedef struct msrcg_hier msrcg_hier;
+
+/* Fill *o with the paper's defaults: s = m = 4, f = 0.1, FP64, caps 200/500,
+ * 2 s wait bound.  Returns MSRCG_OK, or MSRCG_EINVAL if o is NULL. */
+int msrcg_default_opts(msrcg_opts* o);
+
+/* Build the level hierarchy G_0..G_kmax (Sec. 2.2, 3) of one problem.
+ *  grid     host; validated (dim 2/3, every n >= 1, h > 0).
+ *  K        device, double, ncomp*N: cell permeability, scalar (ncomp 1) or
+ *           the diagonal tensor (ncomp = dim), component-major.
+ *  bc       device, uint8, one entry per boundary face (1 = Dirichlet,
+ *           0 = Neumann) in blocks x-low, x-high (ny*nz each), y-low, y-high
+ *           (nx*nz each), z-low, z-high (nx*ny each, 3D only).
+ *  Computes on the device: face transmissibilities T = (h_perp/h_par) K_face
+ *  with K_face the harmonic mean of the adjacent cells (Sec. 3; boundary
+ *  Dirichlet face 2 (h_perp/h_par) K_cell, Neumann 0), the series-parallel
+ *  coarse transmissibilities of every level (Sec. 3), FP32 copies, and the
+ *  exact inverse of the coarsest operator (FP64 Cholesky).  The hierarchy owns
+ *  all device memory it allocates.  Synchronises `stream`.
+ *  Errors: MSRCG_EINVAL, MSRCG_ENOMEM, MSRCG_ECUDA, MSRCG_EBREAKDOWN (coarsest
+ *  operator not positive definite). */
+int msrcg_build(const msrcg_grid* grid, const double* K, int ncomp, const uint8_t* bc,
+                const msrcg_opts* opts, void* stream, msrcg_hier** out);
+
+/* Right-hand side of the lifted problem, Sec. 3: with a field P_bf that
+ * matches the boundary values, writes b = f*vol + g_D - A P_bf, where g_D
+ * sums T_face * gD over the Dirichlet faces of each boundary cell.
+ *  bc, gD   device, the boundary layout of msrcg_build (gD = Dirichlet value).
+ *  f        device, N source densities, or NULL for no source.
+ *  pbf      device, N values of the lifting field.
+ *  b        device, N, output.  Errors: MSRCG_EINVAL, MSRCG_ECUDA. */
+int msrcg_lift_rhs(msrcg_hier* h, const uint8_t* bc, const double* gD, const double* f,
+                   const double* pbf, double* b, void* stream);
+
+/* Solve A x = b to relative residual tol with the recursive multi-scale PCG
+ * (eq. 2.10, Sec. 3): level k stops once ||r||^2/N_k < f^k eps^2 with
+ * eps^2 = tol^2 ||b||^2 / N_0.  x starts from zero.
+ *  b  device, N doubles (read only).   x  device, N doubles (output).
+ *  stats  host, or NULL.  With stats != NULL the call synchronises `stream`
+ *  to read the counters; with NULL it only enqueues (no restart on a missed
+ *  true residual in that case).
+ *  Errors: MSRCG_EINVAL, MSRCG_ENANINF, MSRCG_ENOCONV, MSRCG_EBREAKDOWN,
+ *  MSRCG_ETIMEOUT, MSRCG_ECUDA.  The hierarchy is reusable after an error. */
+int msrcg_solve(msrcg_hier* h, const double* b, double tol, double* x, msrcg_stats* stats,
+                void* stream);
+
+/* Solve `count` independent problems, each with its own hierarchy, in one
+ * persistent launch: one CTA runs the whole recursion of one problem, CTAs
+ * take problems largest first.  The hierarchies must be distinct and built
+ * on the current device.
+ *  hs, b, x  host arrays of `count` entries; b[i], x[i] device, N_i doubles.
+ *  stats     host, `count` entries, or NULL.  Synchronises `stream`.
+ *  Errors: as msrcg_solve; the first failing problem's code is returned. */
+int msrcg_batch_solve(int count, msrcg_hier* const* hs, const double* const* b, double tol,
+                      double* const* x, msrcg_stats* stats, void* stream);
+
+/* Level k's dimensions (dims[3], host) and the iteration / call counters of
+ * the last solve.  Errors: MSRCG_EINVAL for a bad level. */
+int msrcg_level_info(const msrcg_hier* h, int level, int dims[3], int64_t* iters, int64_t* calls);
+
+/* Copy level k's transmissibilities (FP64) into device arrays Tx
+ * ((nx+1)*ny*nz), Ty (nx*(ny+1)*nz) and, in 3D, Tz (nx*ny*(nz+1)); Tz may be
+ * NULL in 2D.  Stream ordered.  Errors: MSRCG_EINVAL, MSRCG_ECUDA. */
+int msrcg_get_trans(const msrcg_hier* h, int level, double* Tx, double* Ty, double* Tz, void* stream);
+
+/* Apply level k's operator: y = A_k x, device arrays of N_k doubles (FP64
+ * transmissibilities).  Stream ordered.  Errors: MSRCG_EINVAL, MSRCG_ECUDA. */
+int msrcg_apply(const msrcg_hier* h, int level, const double* x, double* y, void* stream);
+
+/* Number of levels and device bytes held by the hierarchy. */
+int msrcg_num_levels(const msrcg_hier* h);
+size_t msrcg_device_bytes(const msrcg_hier* h);
+
+/* Release everything the hierarchy owns (synchronises the device first). */
+void msrcg_free(msrcg_hier* h);
+
+/* Static description of an error code. */
+const char* msrcg_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSRCG_H */
