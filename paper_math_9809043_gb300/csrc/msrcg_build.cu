@@ -1,0 +1,689 @@
+// Hierarchy build of libmsrcg (Sec. 2.2 and Sec. 3 of Lackner & Menikoff):
+// face transmissibilities, series-parallel coarse transmissibilities of every
+// level, transfer tables, the exact inverse of the coarsest operator, plus
+// the lifting right-hand side, the FP64 operator apply and bookkeeping.
+//
+// The build kernels use explicitly rounded FP64 operations (__dmul_rn and
+// friends) so that no multiply-add is fused: the transmissibilities are then
+// reproducible to the bit on any device and compiler setting.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "msrcg_internal.cuh"
+
+using namespace msrcg;
+
+int msrcg_cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+  if (getenv("MSRCG_DEBUG")) fprintf(stderr, "msrcg: %s failed at %s:%d: %s\n", what, file, line, cudaGetErrorString(e));
+  (void)cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? MSRCG_ENOMEM : MSRCG_ECUDA;
+}
+
+int msrcg_alloc(msrcg_hier* h, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    *p = nullptr;
+    return MSRCG_ENOMEM;
+  }
+  h->allocs.push_back(*p);
+  h->bytes += bytes;
+  return MSRCG_OK;
+}
+
+int msrcg_status_from_bits(int bits) {
+  if (bits & kStNanInf) return MSRCG_ENANINF;
+  if (bits & kStTimeout) return MSRCG_ETIMEOUT;
+  if (bits & kStBreakdown) return MSRCG_EBREAKDOWN;
+  if (bits & kStNoConv) return MSRCG_ENOCONV;
+  return MSRCG_OK;
+}
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Level sides: scale factor s (~4) adjusted to integer sizes, Sec. 3.  An axis
+// longer than the coarsest side limit shrinks to max(2, floor(n/s + 1/2));
+// the hierarchy ends when no axis is longer than the limit.
+// ---------------------------------------------------------------------------
+int level_sides(int dim, const int n[3], int s, int limit, int out[][3]) {
+  int cur[3] = {n[0], n[1], dim == 3 ? n[2] : 1};
+  int nl = 0;
+  for (;;) {
+    if (nl >= kMaxLev) return -1;
+    for (int a = 0; a < 3; ++a) out[nl][a] = cur[a];
+    ++nl;
+    bool longer = false;
+    for (int a = 0; a < dim; ++a) longer = longer || cur[a] > limit;
+    if (!longer) return nl;
+    for (int a = 0; a < dim; ++a)
+      if (cur[a] > limit) cur[a] = std::max(2, (2 * cur[a] + s) / (2 * s));
+  }
+}
+
+// Zero-slope linear interpolation between cell centres along one axis of
+// the unit interval, Sec. 3: fine centre (i+1/2)/nf sits at coarse coordinate
+// t = ((2i+1) nc - nf) / (2 nf) in units of the coarse spacing, measured from
+// the first coarse centre.  Outside [0, nc-1] the end value is held.
+struct Axis1D {
+  std::vector<int> c0, c1, lo, hi;
+  std::vector<double> w;
+};
+
+Axis1D axis_tables(int nf, int nc) {
+  Axis1D A;
+  A.c0.resize(nf);
+  A.c1.resize(nf);
+  A.w.resize(nf);
+  const long long den = 2LL * nf;
+  for (int i = 0; i < nf; ++i) {
+    long long num = (2LL * i + 1) * nc - nf;
+    int a, b;
+    double w;
+    if (num <= 0) {
+      a = b = 0;
+      w = 0.0;
+    } else if (num / den >= nc - 1) {
+      a = b = nc - 1;
+      w = 0.0;
+    } else if (num % den == 0) {
+      a = b = (int)(num / den);
+      w = 0.0;
+    } else {
+      a = (int)(num / den);
+      b = a + 1;
+      w = (double)(num % den) / (double)den;
+    }
+    A.c0[i] = a;
+    A.c1[i] = b;
+    A.w[i] = w;
+  }
+  // restriction windows: fine cells with a non-zero weight on coarse cell I
+  A.lo.assign(nc, nf);
+  A.hi.assign(nc, -1);
+  for (int i = 0; i < nf; ++i) {
+    int cs[2] = {A.c0[i], A.c1[i]};
+    double ws[2] = {1.0 - A.w[i], A.w[i]};
+    for (int e = 0; e < 2; ++e) {
+      if (ws[e] == 0.0 && !(e == 0 && A.c0[i] == A.c1[i])) continue;
+      A.lo[cs[e]] = std::min(A.lo[cs[e]], i);
+      A.hi[cs[e]] = std::max(A.hi[cs[e]], i);
+    }
+  }
+  return A;
+}
+
+// ---------------------------------------------------------------------------
+// Kernels
+// ---------------------------------------------------------------------------
+
+// Face transmissibilities, Sec. 3: T = (h_perp/h_par) K_face; K_face is the
+// harmonic mean 2 K_L K_R / (K_L + K_R) of the adjacent cells; a Dirichlet
+// boundary face (half a cell from the centre) has 2 (h_perp/h_par) K_cell, a
+// Neumann face 0.
+__global__ void k_face_trans(int ax, int nx, int ny, int nz, double ratio, const double* __restrict__ K,
+                             const uint8_t* __restrict__ blo, const uint8_t* __restrict__ bhi,
+                             double* __restrict__ T) {
+  const int fx = nx + (ax == 0), fy = ny + (ax == 1), fz = nz + (ax == 2);
+  const long long nf = (long long)fx * fy * fz;
+  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf; f += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(f % fx);
+    long long rest = f / fx;
+    int j = (int)(rest % fy);
+    int k = (int)(rest / fy);
+    int g[3] = {i, j, k}, lim[3] = {nx, ny, nz};
+    int e = g[ax];
+    double t;
+    if (e == 0 || e == lim[ax]) {
+      // boundary face: index of the face inside its block
+      long long bi;
+      if (ax == 0) bi = j + (long long)ny * k;
+      else if (ax == 1) bi = i + (long long)nx * k;
+      else bi = i + (long long)nx * j;
+      const uint8_t* msk = e == 0 ? blo : bhi;
+      int gc[3] = {i, j, k};
+      gc[ax] = e == 0 ? 0 : lim[ax] - 1;
+      double kc = K[gc[0] + (long long)nx * (gc[1] + (long long)ny * gc[2])];
+      t = msk[bi] ? __dmul_rn(ratio, __dmul_rn(2.0, kc)) : 0.0;
+    } else {
+      int gl[3] = {i, j, k};
+      gl[ax] = e - 1;
+      int gr[3] = {i, j, k};
+      gr[ax] = e;
+      double kl = K[gl[0] + (long long)nx * (gl[1] + (long long)ny * gl[2])];
+      double kr = K[gr[0] + (long long)nx * (gr[1] + (long long)ny * gr[2])];
+      double s = __dadd_rn(kl, kr);
+      t = s > 0.0 ? __dmul_rn(ratio, __ddiv_rn(__dmul_rn(__dmul_rn(2.0, kl), kr), s)) : 0.0;
+    }
+    T[f] = t;
+  }
+}
+
+__device__ __forceinline__ long long d_overlap(long long a0, long long a1, long long b0, long long b1) {
+  long long lo = a0 > b0 ? a0 : b0, hi = a1 < b1 ? a1 : b1;
+  return hi > lo ? hi - lo : 0;
+}
+
+// Coarse transmissibility of the faces normal to axis `ax`, Sec. 3:
+//   1/T^c = sum_i 1/C_i,  C_i = (w_i / o_i) * sum_j (o_j / h_j) T(i, j)
+// i runs over the fine faces along the normal whose conductor block (between
+// adjacent cell centres, half a cell at the boundary) overlaps the coarse
+// face's block by o_i (w_i = the fine block's width); j runs over the fine
+// faces across the coarse face, weighted by the fraction of their extent
+// inside it.  Lengths along an axis with nf fine / nc coarse cells are exact
+// integers in units of 1/(2 nf nc) of the unit interval.  One thread per
+// coarse face; sums run in ascending index order, one rounding per operation.
+__global__ void k_upscale(int ax, int3 nf, int3 nc, const double* __restrict__ Tf, double* __restrict__ Tc) {
+  const int p1 = (ax + 1) % 3, p2 = (ax + 2) % 3;
+  const int F[3] = {nf.x, nf.y, nf.z}, Cn[3] = {nc.x, nc.y, nc.z};
+  int fd[3] = {F[0], F[1], F[2]}, cd[3] = {Cn[0], Cn[1], Cn[2]};
+  fd[ax] += 1;
+  cd[ax] += 1;
+  const long long ncf = (long long)cd[0] * cd[1] * cd[2];
+  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < ncf; f += (long long)gridDim.x * blockDim.x) {
+    int c[3];
+    c[0] = (int)(f % cd[0]);
+    long long rest = f / cd[0];
+    c[1] = (int)(rest % cd[1]);
+    c[2] = (int)(rest / cd[1]);
+    const long long nfa = F[ax], nca = Cn[ax], L = 2 * nfa * nca;
+    long long clo = (2LL * c[ax] - 1) * nfa, chi = (2LL * c[ax] + 1) * nfa;
+    clo = clo < 0 ? 0 : clo;
+    chi = chi > L ? L : chi;
+    // fine faces i whose block [(2i-1) nc, (2i+1) nc] can meet [clo, chi]
+    long long ia = (clo / nca - 1) / 2 - 1, ib = (chi / nca + 1) / 2 + 1;
+    ia = ia < 0 ? 0 : ia;
+    ib = ib > nfa ? nfa : ib;
+    // fine cells j along p1 / p2 that can meet coarse cell c[p]
+    auto win = [](int J, int nf_, int nc_, int* lo, int* hi) {
+      long long a = ((long long)J * nf_) / nc_ - 1, b = (((long long)J + 1) * nf_) / nc_ + 1;
+      *lo = a < 0 ? 0 : (int)a;
+      *hi = b > nf_ - 1 ? nf_ - 1 : (int)b;
+    };
+    int alo, ahi, blo, bhi;
+    win(c[p1], F[p1], Cn[p1], &alo, &ahi);
+    win(c[p2], F[p2], Cn[p2], &blo, &bhi);
+    double inv = 0.0;
+    bool zero = false, any = false;
+    for (long long i = ia; i <= ib && !zero; ++i) {
+      long long flo = (2 * i - 1) * nca, fhi = (2 * i + 1) * nca;
+      flo = flo < 0 ? 0 : flo;
+      fhi = fhi > L ? L : fhi;
+      long long o = d_overlap(flo, fhi, clo, chi);
+      if (o == 0) continue;
+      any = true;
+      double S = 0.0;
+      for (int b = blo; b <= bhi; ++b) {
+        long long o2 = d_overlap(2LL * b * Cn[p2], 2LL * (b + 1) * Cn[p2], 2LL * c[p2] * F[p2], 2LL * (c[p2] + 1) * F[p2]);
+        if (o2 == 0) continue;
+        double f2 = __ddiv_rn((double)o2, (double)(2LL * Cn[p2]));
+        double inner = 0.0;
+        for (int a = alo; a <= ahi; ++a) {
+          long long o1 = d_overlap(2LL * a * Cn[p1], 2LL * (a + 1) * Cn[p1], 2LL * c[p1] * F[p1], 2LL * (c[p1] + 1) * F[p1]);
+          if (o1 == 0) continue;
+          double f1 = __ddiv_rn((double)o1, (double)(2LL * Cn[p1]));
+          int g[3];
+          g[ax] = (int)i;
+          g[p1] = a;
+          g[p2] = b;
+          double t = Tf[g[0] + (long long)fd[0] * (g[1] + (long long)fd[1] * g[2])];
+          inner = __dadd_rn(inner, __dmul_rn(f1, t));
+        }
+        S = __dadd_rn(S, __dmul_rn(f2, inner));
+      }
+      double C = __ddiv_rn(__dmul_rn(S, (double)(fhi - flo)), (double)o);
+      if (C == 0.0) {
+        zero = true;
+        break;
+      }
+      inv = __dadd_rn(inv, __ddiv_rn(1.0, C));
+    }
+    Tc[f] = (zero || !any) ? 0.0 : __ddiv_rn(1.0, inv);
+  }
+}
+
+__global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+// Dense operator of a (small) level: A[c][c] = sum of its face T,
+// A[c][nb] = -T_face.  Row-major n x n.
+__global__ void k_dense_assemble(int nx, int ny, int nz, const double* __restrict__ Tx, const double* __restrict__ Ty,
+                                 const double* __restrict__ Tz, double* __restrict__ A) {
+  const long long n = (long long)nx * ny * nz;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * n; e += (long long)gridDim.x * blockDim.x)
+    A[e] = 0.0;
+  __syncthreads();
+  for (long long c = threadIdx.x; c < n; c += blockDim.x) {
+    int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
+    long long row = j + (long long)ny * k;
+    double d = 0.0, t;
+    t = Tx[c + row];
+    d += t;
+    if (i > 0) A[c * n + c - 1] = -t;
+    t = Tx[c + row + 1];
+    d += t;
+    if (i < nx - 1) A[c * n + c + 1] = -t;
+    t = Ty[c + (long long)nx * k];
+    d += t;
+    if (j > 0) A[c * n + c - nx] = -t;
+    t = Ty[c + (long long)nx * k + nx];
+    d += t;
+    if (j < ny - 1) A[c * n + c + nx] = -t;
+    if (Tz) {
+      long long pl = (long long)nx * ny;
+      t = Tz[c];
+      d += t;
+      if (k > 0) A[c * n + c - pl] = -t;
+      t = Tz[c + pl];
+      d += t;
+      if (k < nz - 1) A[c * n + c + pl] = -t;
+    }
+    A[c * n + c] = d;
+  }
+}
+
+// In-place Cholesky A = C C^T (lower), then the explicit inverse, by one
+// CTA in FP64.  The coarsest level is solved exactly (Sec. 2.2 / 2.3); the
+// inverse turns each coarsest solve into one matrix-vector product.
+__global__ void k_chol_inverse(int n, double* __restrict__ A, double* __restrict__ Ainv, int* __restrict__ fail) {
+  __shared__ double piv;
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      double d = A[(long long)j * n + j];
+      if (!(d > 0.0)) *fail = 1;
+      piv = sqrt(d > 0.0 ? d : 1.0);
+      A[(long long)j * n + j] = piv;
+    }
+    __syncthreads();
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[(long long)i * n + j] /= piv;
+    __syncthreads();
+    const int m = n - j - 1;
+    for (long long e = threadIdx.x; e < (long long)m * m; e += blockDim.x) {
+      int i = j + 1 + (int)(e / m), k = j + 1 + (int)(e % m);
+      if (k <= i) A[(long long)i * n + k] -= A[(long long)i * n + j] * A[(long long)k * n + j];
+    }
+    __syncthreads();
+  }
+  // column c of the inverse: solve C y = e_c, C^T x = y (x stored in Ainv[:, c])
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    for (int i = 0; i < n; ++i) {
+      double s = (i == c) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) s -= A[(long long)i * n + k] * Ainv[(long long)k * n + c];
+      Ainv[(long long)i * n + c] = s / A[(long long)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double s = Ainv[(long long)i * n + c];
+      for (int k = i + 1; k < n; ++k) s -= A[(long long)k * n + i] * Ainv[(long long)k * n + c];
+      Ainv[(long long)i * n + c] = s / A[(long long)i * n + i];
+    }
+  }
+}
+
+// y = A x with FP64 transmissibilities: (A x)_c = sum_faces T (x_c - x_nb),
+// T x_c on a boundary face.
+__global__ void k_apply64(int nx, int ny, int nz, const double* __restrict__ Tx, const double* __restrict__ Ty,
+                          const double* __restrict__ Tz, const double* __restrict__ x, double* __restrict__ y) {
+  const long long n = (long long)nx * ny * nz;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
+    long long row = j + (long long)ny * k;
+    double xc = x[c], s = 0.0, t;
+    t = Tx[c + row];
+    s += i > 0 ? t * (xc - x[c - 1]) : t * xc;
+    t = Tx[c + row + 1];
+    s += i < nx - 1 ? t * (xc - x[c + 1]) : t * xc;
+    t = Ty[c + (long long)nx * k];
+    s += j > 0 ? t * (xc - x[c - nx]) : t * xc;
+    t = Ty[c + (long long)nx * k + nx];
+    s += j < ny - 1 ? t * (xc - x[c + nx]) : t * xc;
+    if (Tz) {
+      long long pl = (long long)nx * ny;
+      t = Tz[c];
+      s += k > 0 ? t * (xc - x[c - pl]) : t * xc;
+      t = Tz[c + pl];
+      s += k < nz - 1 ? t * (xc - x[c + pl]) : t * xc;
+    }
+    y[c] = s;
+  }
+}
+
+// Lifted right-hand side, Sec. 3: b = f vol + g_D - A P_bf.
+__global__ void k_lift(int nx, int ny, int nz, const double* __restrict__ Tx, const double* __restrict__ Ty,
+                       const double* __restrict__ Tz, const uint8_t* __restrict__ bc, const double* __restrict__ gD,
+                       const double* __restrict__ f, double vol, const double* __restrict__ pbf, double* __restrict__ b) {
+  const long long n = (long long)nx * ny * nz;
+  const long long nyz = (long long)ny * nz, nxz = (long long)nx * nz, nxy = (long long)nx * ny;
+  const long long ox1 = nyz, oy0 = 2 * nyz, oy1 = 2 * nyz + nxz, oz0 = 2 * nyz + 2 * nxz, oz1 = oz0 + nxy;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / nxy);
+    long long row = j + (long long)ny * k;
+    double v = f ? f[c] * vol : 0.0;
+    if (i == 0 && bc[row]) v += Tx[c + row] * gD[row];
+    if (i == nx - 1 && bc[ox1 + row]) v += Tx[c + row + 1] * gD[ox1 + row];
+    long long xz = i + (long long)nx * k;
+    if (j == 0 && bc[oy0 + xz]) v += Ty[c + (long long)nx * k] * gD[oy0 + xz];
+    if (j == ny - 1 && bc[oy1 + xz]) v += Ty[c + (long long)nx * k + nx] * gD[oy1 + xz];
+    if (Tz) {
+      long long xy = i + (long long)nx * j;
+      if (k == 0 && bc[oz0 + xy]) v += Tz[c] * gD[oz0 + xy];
+      if (k == nz - 1 && bc[oz1 + xy]) v += Tz[c + nxy] * gD[oz1 + xy];
+    }
+    // A P_bf
+    double xc = pbf[c], s = 0.0, t;
+    t = Tx[c + row];
+    s += i > 0 ? t * (xc - pbf[c - 1]) : t * xc;
+    t = Tx[c + row + 1];
+    s += i < nx - 1 ? t * (xc - pbf[c + 1]) : t * xc;
+    t = Ty[c + (long long)nx * k];
+    s += j > 0 ? t * (xc - pbf[c - nx]) : t * xc;
+    t = Ty[c + (long long)nx * k + nx];
+    s += j < ny - 1 ? t * (xc - pbf[c + nx]) : t * xc;
+    if (Tz) {
+      t = Tz[c];
+      s += k > 0 ? t * (xc - pbf[c - nxy]) : t * xc;
+      t = Tz[c + nxy];
+      s += k < nz - 1 ? t * (xc - pbf[c + nxy]) : t * xc;
+    }
+    b[c] = v - s;
+  }
+}
+
+int grid_for(long long n, int threads, int maxblocks) {
+  long long g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > maxblocks) g = maxblocks;
+  return (int)g;
+}
+
+template <typename T>
+int upload(msrcg_hier* h, const std::vector<T>& v, const void** out) {
+  void* p;
+  int rc = msrcg_alloc(h, &p, sizeof(T) * v.size());
+  if (rc) return rc;
+  MSRCG_CUDA_TRY(cudaMemcpy(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+  *out = p;
+  return MSRCG_OK;
+}
+
+void release(msrcg_hier* h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  for (void* p : h->allocs) cudaFree(p);
+  (void)cudaGetLastError();
+  delete h;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" int msrcg_default_opts(msrcg_opts* o) {
+  if (!o) return MSRCG_EINVAL;
+  memset(o, 0, sizeof(*o));
+  o->scale = 4;
+  o->m = 4;
+  o->f = 0.1;
+  o->coarsest_max_side = 0;
+  o->precision = 0;
+  o->maxit_outer = 200;
+  o->maxit_inner = 500;
+  o->timeout_ns = 2000000000ull;
+  o->inner_floor = 0.0;
+  o->small_cells = 0;
+  return MSRCG_OK;
+}
+
+extern "C" const char* msrcg_strerror(int code) {
+  switch (code) {
+    case MSRCG_OK: return "ok";
+    case MSRCG_EINVAL: return "invalid argument";
+    case MSRCG_ENOMEM: return "device allocation failed";
+    case MSRCG_ENOCONV: return "iteration cap reached before the level tolerance";
+    case MSRCG_EBREAKDOWN: return "conjugate gradient breakdown (p.Ap <= 0 or non-finite scalar)";
+    case MSRCG_ETIMEOUT: return "bounded device wait timed out";
+    case MSRCG_ENANINF: return "non-finite value in the right-hand side";
+    case MSRCG_ECUDA: return "CUDA runtime error";
+    default: return "unknown error";
+  }
+}
+
+extern "C" int msrcg_build(const msrcg_grid* grid, const double* K, int ncomp, const uint8_t* bc,
+                           const msrcg_opts* opts, void* stream, msrcg_hier** out) {
+  if (!out) return MSRCG_EINVAL;
+  *out = nullptr;
+  if (!grid || !K || !bc) return MSRCG_EINVAL;
+  const int dim = grid->dim;
+  if (dim != 2 && dim != 3) return MSRCG_EINVAL;
+  for (int a = 0; a < dim; ++a)
+    if (grid->n[a] < 1 || !(grid->h[a] > 0.0) || !isfinite(grid->h[a])) return MSRCG_EINVAL;
+  if (ncomp != 1 && ncomp != dim) return MSRCG_EINVAL;
+  msrcg_opts o;
+  if (opts) o = *opts;
+  else msrcg_default_opts(&o);
+  if (o.scale < 2 || o.m < 1 || !(o.f > 0.0) || o.maxit_outer < 1 || o.maxit_inner < 1) return MSRCG_EINVAL;
+  if (o.precision != 0 && o.precision != 1) return MSRCG_EINVAL;
+  if (o.coarsest_max_side <= 0) o.coarsest_max_side = dim == 2 ? 8 : 4;
+  if (o.timeout_ns == 0) o.timeout_ns = 2000000000ull;
+  if (o.small_cells <= 0) o.small_cells = o.precision == 1 ? 4096 : 4096;
+  cudaStream_t st = (cudaStream_t)stream;
+
+  msrcg_hier* h = new msrcg_hier();
+  h->dim = dim;
+  h->o = o;
+  for (int a = 0; a < 3; ++a) h->hsz[a] = a < dim ? grid->h[a] : 1.0;
+  int rc = MSRCG_OK;
+  auto fail = [&](int code) {
+    release(h);
+    return code;
+  };
+  if (cudaGetDevice(&h->device) != cudaSuccess) return fail(MSRCG_ECUDA);
+  cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+  int n3[3] = {grid->n[0], grid->n[1], dim == 3 ? grid->n[2] : 1};
+  h->nlev = level_sides(dim, n3, o.scale, o.coarsest_max_side, h->dims);
+  if (h->nlev < 1) return fail(MSRCG_EINVAL);
+  for (int k = 0; k < h->nlev; ++k) h->N[k] = (long long)h->dims[k][0] * h->dims[k][1] * h->dims[k][2];
+  if (h->N[h->nlev - 1] > 4096) return fail(MSRCG_EINVAL);
+  h->ks = h->nlev - 1;
+  while (h->ks > 0 && h->N[h->ks - 1] <= o.small_cells) --h->ks;
+
+  const bool f32 = o.precision == 1;
+  const size_t rsz = f32 ? sizeof(float) : sizeof(double);
+  const int gmax = std::min(h->sms * 8, kMaxGrid);
+
+  // ---- level 0 transmissibilities from cell K (A1) ----
+  double hh[3] = {grid->h[0], grid->h[1], dim == 3 ? grid->h[2] : 1.0};
+  double ratio[3] = {(hh[1] * hh[2]) / hh[0], (hh[0] * hh[2]) / hh[1], (hh[0] * hh[1]) / hh[2]};
+  const long long nyz = (long long)n3[1] * n3[2], nxz = (long long)n3[0] * n3[2], nxy = (long long)n3[0] * n3[1];
+  const uint8_t* blo[3] = {bc, bc + 2 * nyz, bc + 2 * nyz + 2 * nxz};
+  const uint8_t* bhi[3] = {bc + nyz, bc + 2 * nyz + nxz, bc + 2 * nyz + 2 * nxz + nxy};
+  for (int k = 0; k < h->nlev; ++k) {
+    const int* d = h->dims[k];
+    for (int a = 0; a < dim; ++a) {
+      long long nf = (long long)(d[0] + (a == 0)) * (d[1] + (a == 1)) * (d[2] + (a == 2));
+      void* p;
+      if ((rc = msrcg_alloc(h, &p, sizeof(double) * nf))) return fail(rc);
+      h->T64[k][a] = (double*)p;
+    }
+  }
+  for (int a = 0; a < dim; ++a) {
+    long long nf = (long long)(n3[0] + (a == 0)) * (n3[1] + (a == 1)) * (n3[2] + (a == 2));
+    const double* Ka = K + (ncomp > 1 ? a * h->N[0] : 0);
+    k_face_trans<<<grid_for(nf, 256, gmax), 256, 0, st>>>(a, n3[0], n3[1], n3[2], ratio[a], Ka, blo[a], bhi[a],
+                                                           h->T64[0][a]);
+  }
+  // ---- coarse transmissibilities (A2) ----
+  for (int k = 0; k + 1 < h->nlev; ++k) {
+    int3 nf = make_int3(h->dims[k][0], h->dims[k][1], h->dims[k][2]);
+    int3 nc = make_int3(h->dims[k + 1][0], h->dims[k + 1][1], h->dims[k + 1][2]);
+    for (int a = 0; a < dim; ++a) {
+      long long ncf = (long long)(nc.x + (a == 0)) * (nc.y + (a == 1)) * (nc.z + (a == 2));
+      k_upscale<<<grid_for(ncf, 128, gmax), 128, 0, st>>>(a, nf, nc, h->T64[k][a], h->T64[k + 1][a]);
+    }
+  }
+  if (cudaGetLastError() != cudaSuccess) return fail(MSRCG_ECUDA);
+  // ---- smoother-precision copies ----
+  for (int k = 0; k < h->nlev; ++k)
+    for (int a = 0; a < dim; ++a) {
+      const int* d = h->dims[k];
+      long long nf = (long long)(d[0] + (a == 0)) * (d[1] + (a == 1)) * (d[2] + (a == 2));
+      if (f32) {
+        void* p;
+        if ((rc = msrcg_alloc(h, &p, sizeof(float) * nf))) return fail(rc);
+        k_to_float<<<grid_for(nf, 256, gmax), 256, 0, st>>>(h->T64[k][a], (float*)p, nf);
+        h->TR[k][a] = p;
+      } else {
+        h->TR[k][a] = h->T64[k][a];
+      }
+    }
+  // ---- transfer tables, vectors and level descriptors ----
+  double fk = 1.0;
+  for (int k = 0; k < h->nlev; ++k) {
+    DevLevel& L = h->hL[k];
+    memset(&L, 0, sizeof(L));
+    L.nx = h->dims[k][0];
+    L.ny = h->dims[k][1];
+    L.nz = h->dims[k][2];
+    L.dim = dim;
+    L.n = h->N[k];
+    for (int a = 0; a < dim; ++a) {
+      L.T[a] = h->TR[k][a];
+      L.T64[a] = h->T64[k][a];
+    }
+    L.fk = fk;
+    fk *= o.f;
+    L.maxit = k == 0 ? o.maxit_outer : o.maxit_inner;
+    if (k + 1 < h->nlev) {
+      for (int a = 0; a < 3; ++a) {
+        Axis1D ax = axis_tables(h->dims[k][a], h->dims[k + 1][a]);
+        const void* p;
+        if ((rc = upload(h, ax.c0, &p))) return fail(rc);
+        L.c0[a] = (const int*)p;
+        if ((rc = upload(h, ax.c1, &p))) return fail(rc);
+        L.c1[a] = (const int*)p;
+        if ((rc = upload(h, ax.lo, &p))) return fail(rc);
+        L.lo[a] = (const int*)p;
+        if ((rc = upload(h, ax.hi, &p))) return fail(rc);
+        L.hi[a] = (const int*)p;
+        if (f32) {
+          std::vector<float> wf(ax.w.begin(), ax.w.end());
+          if ((rc = upload(h, wf, &p))) return fail(rc);
+        } else {
+          if ((rc = upload(h, ax.w, &p))) return fail(rc);
+        }
+        L.w[a] = p;
+      }
+    }
+    const size_t vsz = k == 0 ? sizeof(double) : rsz;
+    void* p;
+    if ((rc = msrcg_alloc(h, &p, vsz * L.n))) return fail(rc);
+    L.x = p;
+    if ((rc = msrcg_alloc(h, &p, vsz * L.n))) return fail(rc);
+    L.r = p;
+    if ((rc = msrcg_alloc(h, &p, vsz * L.n))) return fail(rc);
+    L.p = p;
+    if ((rc = msrcg_alloc(h, &p, vsz * L.n))) return fail(rc);
+    L.q = p;
+    if ((rc = msrcg_alloc(h, &p, rsz * L.n))) return fail(rc);
+    L.z = p;
+    if ((rc = msrcg_alloc(h, &p, rsz * L.n))) return fail(rc);
+    L.t = p;
+  }
+  // ---- coarsest exact inverse (A3) ----
+  {
+    const int kc = h->nlev - 1;
+    h->nc = (int)h->N[kc];
+    void *A, *Ai, *fl;
+    if ((rc = msrcg_alloc(h, &A, sizeof(double) * h->nc * h->nc))) return fail(rc);
+    if ((rc = msrcg_alloc(h, &Ai, sizeof(double) * h->nc * h->nc))) return fail(rc);
+    if ((rc = msrcg_alloc(h, &fl, sizeof(int)))) return fail(rc);
+    MSRCG_CUDA_TRY(cudaMemsetAsync(fl, 0, sizeof(int), st));
+    k_dense_assemble<<<1, 512, 0, st>>>(h->dims[kc][0], h->dims[kc][1], h->dims[kc][2], h->T64[kc][0], h->T64[kc][1],
+                                        dim == 3 ? h->T64[kc][2] : nullptr, (double*)A);
+    k_chol_inverse<<<1, 512, 0, st>>>(h->nc, (double*)A, (double*)Ai, (int*)fl);
+    int hf = 0;
+    if (cudaMemcpyAsync(&hf, fl, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return fail(MSRCG_ECUDA);
+    if (hf) return fail(MSRCG_EBREAKDOWN);
+    h->Ainv = (double*)Ai;
+  }
+  // ---- solve state ----
+  {
+    void* p;
+    if ((rc = msrcg_alloc(h, &p, sizeof(DevLevel) * h->nlev))) return fail(rc);
+    h->dL = (DevLevel*)p;
+    MSRCG_CUDA_TRY(cudaMemcpy(h->dL, h->hL, sizeof(DevLevel) * h->nlev, cudaMemcpyHostToDevice));
+    if ((rc = msrcg_alloc(h, &p, sizeof(SolveState)))) return fail(rc);
+    h->dS = (SolveState*)p;
+    MSRCG_CUDA_TRY(cudaMemset(h->dS, 0, sizeof(SolveState)));
+    if ((rc = msrcg_alloc(h, &p, sizeof(double) * kMaxLev * (size_t)std::max(gmax, kMaxGrid)))) return fail(rc);
+    h->partials = (double*)p;
+    if ((rc = msrcg_alloc(h, &p, sizeof(double) * h->N[0]))) return fail(rc);
+    h->b0 = (double*)p;
+    if ((rc = msrcg_alloc(h, &p, sizeof(double) * h->N[0]))) return fail(rc);
+    h->xs = (double*)p;
+    if ((rc = msrcg_alloc(h, &p, sizeof(ProblemDesc)))) return fail(rc);
+    h->dP = (ProblemDesc*)p;
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return fail(MSRCG_ECUDA);
+  *out = h;
+  return MSRCG_OK;
+}
+
+extern "C" int msrcg_lift_rhs(msrcg_hier* h, const uint8_t* bc, const double* gD, const double* f, const double* pbf,
+                              double* b, void* stream) {
+  if (!h || !bc || !gD || !pbf || !b) return MSRCG_EINVAL;
+  const int* d = h->dims[0];
+  const double vol = h->hsz[0] * h->hsz[1] * (h->dim == 3 ? h->hsz[2] : 1.0);
+  k_lift<<<grid_for(h->N[0], 256, h->sms * 8), 256, 0, (cudaStream_t)stream>>>(
+      d[0], d[1], d[2], h->T64[0][0], h->T64[0][1], h->dim == 3 ? h->T64[0][2] : nullptr, bc, gD, f, vol, pbf, b);
+  MSRCG_CUDA_TRY(cudaGetLastError());
+  return MSRCG_OK;
+}
+
+extern "C" int msrcg_level_info(const msrcg_hier* h, int level, int dims[3], int64_t* iters, int64_t* calls) {
+  if (!h || level < 0 || level >= h->nlev) return MSRCG_EINVAL;
+  if (dims)
+    for (int a = 0; a < 3; ++a) dims[a] = h->dims[level][a];
+  if (iters) *iters = h->last_iters[level];
+  if (calls) *calls = h->last_calls[level];
+  return MSRCG_OK;
+}
+
+extern "C" int msrcg_get_trans(const msrcg_hier* h, int level, double* Tx, double* Ty, double* Tz, void* stream) {
+  if (!h || level < 0 || level >= h->nlev || !Tx || !Ty || (h->dim == 3 && !Tz)) return MSRCG_EINVAL;
+  const int* d = h->dims[level];
+  double* outs[3] = {Tx, Ty, Tz};
+  for (int a = 0; a < h->dim; ++a) {
+    long long nf = (long long)(d[0] + (a == 0)) * (d[1] + (a == 1)) * (d[2] + (a == 2));
+    MSRCG_CUDA_TRY(cudaMemcpyAsync(outs[a], h->T64[level][a], sizeof(double) * nf, cudaMemcpyDeviceToDevice,
+                                   (cudaStream_t)stream));
+  }
+  return MSRCG_OK;
+}
+
+extern "C" int msrcg_apply(const msrcg_hier* h, int level, const double* x, double* y, void* stream) {
+  if (!h || level < 0 || level >= h->nlev || !x || !y) return MSRCG_EINVAL;
+  const int* d = h->dims[level];
+  k_apply64<<<grid_for(h->N[level], 256, h->sms * 8), 256, 0, (cudaStream_t)stream>>>(
+      d[0], d[1], d[2], h->T64[level][0], h->T64[level][1], h->dim == 3 ? h->T64[level][2] : nullptr, x, y);
+  MSRCG_CUDA_TRY(cudaGetLastError());
+  return MSRCG_OK;
+}
+
+extern "C" int msrcg_num_levels(const msrcg_hier* h) { return h ? h->nlev : 0; }
+extern "C" size_t msrcg_device_bytes(const msrcg_hier* h) { return h ? h->bytes : 0; }
+extern "C" void msrcg_free(msrcg_hier* h) { release(h); }

@@ -1,0 +1,126 @@
+// Internal declarations of libmsrcg: device-visible level descriptors, solve
+// state, error handling and small device helpers shared by the build and the
+// solve translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "msrcg.h"
+
+#define MSRCG_CUDA_TRY(expr)                      \
+  do {                                            \
+    cudaError_t e_ = (expr);                      \
+    if (e_ != cudaSuccess) return msrcg_cuda_fail(e_, #expr, __FILE__, __LINE__); \
+  } while (0)
+
+int msrcg_cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+namespace msrcg {
+
+constexpr int kMaxLev = MSRCG_MAXLEV;
+constexpr int kThreads = 256;        // block size of the multi-CTA level kernels
+constexpr int kSmallThreads = 512;   // block size of the single-CTA solver
+constexpr int kMaxGrid = 4096;       // upper bound of blocks per multi-CTA launch
+
+// status bits written on the device (host maps them to MSRCG_E*)
+constexpr int kStBreakdown = 1;
+constexpr int kStNoConv = 2;
+constexpr int kStTimeout = 4;
+constexpr int kStNanInf = 8;
+
+// One level of the hierarchy as the kernels see it.  Face arrays: Tx has
+// (nx+1)*ny*nz entries (x fastest), Ty nx*(ny+1)*nz, Tz nx*ny*(nz+1).
+struct DevLevel {
+  int nx, ny, nz, dim;
+  long long n;
+  const void* T[3];      // smoother-precision transmissibilities (float or double)
+  const double* T64[3];  // FP64 transmissibilities
+  // prolongation tables of the transfer to level k+1, indexed by fine cell
+  // along each axis: coarse corners c0, c1 and the weight w of c1
+  const int* c0[3];
+  const int* c1[3];
+  const void* w[3];      // smoother precision
+  // restriction windows, indexed by coarse cell of level k+1 along each axis:
+  // the fine cells [lo, hi] that interpolate from it
+  const int* lo[3];
+  const int* hi[3];
+  // vectors: x, r, p, q in the level's vector type; z, t in smoother precision
+  void* x;
+  void* r;
+  void* p;
+  void* q;
+  void* z;
+  void* t;
+  double fk;             // f^k of the level test
+  int maxit;
+  int pad;
+};
+
+struct LevelState {
+  double rho, rho_old, pq, rr, bb, thr;
+  long long iters, calls;
+  int it, stop;
+};
+
+struct SolveState {
+  double eps2;           // eps^2 of the level test (Sec. 3)
+  double bb0;            // ||b||^2 of the caller's right-hand side
+  double tau2;
+  double inner_floor2;
+  int status;
+  int pad;
+  double rr_true;
+  LevelState lv[kMaxLev];
+  unsigned int ticket[kMaxLev];
+};
+
+// Everything one problem's single-CTA solve needs.
+struct ProblemDesc {
+  const DevLevel* L;     // device array, nlev entries
+  int nlev, m;
+  const double* Ainv;    // dense inverse of the coarsest operator, nc x nc
+  int nc;
+  int precision;
+  SolveState* S;
+  const double* b;       // caller right-hand side (level 0)
+  double* x;             // caller solution (level 0)
+  double tol;
+  long long work;        // scheduling weight (cells of level 0)
+};
+
+}  // namespace msrcg
+
+struct msrcg_hier {
+  int device = 0;
+  int dim = 2, nlev = 0, ks = 0;
+  int dims[MSRCG_MAXLEV][3] = {};
+  long long N[MSRCG_MAXLEV] = {};
+  double hsz[3] = {1.0, 1.0, 1.0};      // cell sizes of level 0
+  msrcg_opts o{};
+  size_t bytes = 0;
+  std::vector<void*> allocs;
+  double* T64[MSRCG_MAXLEV][3] = {};
+  void* TR[MSRCG_MAXLEV][3] = {};       // smoother precision copy (aliases T64 in FP64 mode)
+  msrcg::DevLevel hL[MSRCG_MAXLEV] = {};
+  msrcg::DevLevel* dL = nullptr;
+  double* Ainv = nullptr;
+  int nc = 0;
+  msrcg::SolveState* dS = nullptr;
+  double* partials = nullptr;           // kMaxLev * kMaxGrid doubles
+  double* b0 = nullptr;                 // internal right-hand side of the level-0 PCG
+  double* xs = nullptr;                 // accumulated solution across restarts
+  msrcg::ProblemDesc* dP = nullptr;     // device copy of this problem's descriptor
+  // level loop graph
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraph_t graph = nullptr;
+  int64_t last_iters[MSRCG_MAXLEV] = {};
+  int64_t last_calls[MSRCG_MAXLEV] = {};
+  int sms = 0;
+};
+
+// allocation helper: records the buffer in h->allocs
+int msrcg_alloc(msrcg_hier* h, void** p, size_t bytes);
+int msrcg_status_from_bits(int bits);

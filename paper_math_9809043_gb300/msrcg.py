@@ -1,0 +1,231 @@
+"""Python binding of libmsrcg (ctypes).
+
+Argument marshalling only: every step of the solver runs in the library's
+CUDA kernels.  PyTorch provides device memory and streams.  There is no CPU
+fallback: importing this module fails if the library is missing.
+
+Reference: Lackner & Menikoff, "Multi-scale linear solvers for very large
+systems derived from PDEs" (arXiv math/9809043), Sec. 2.3 (recursive
+multi-scale preconditioned CG) and Sec. 3 (porous-flow discretisation).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmsrcg.so")
+
+OK, EINVAL, ENOMEM, ENOCONV, EBREAKDOWN, ETIMEOUT, ENANINF, ECUDA = 0, -1, -2, -3, -4, -5, -6, -7
+MAXLEV = 16
+
+
+class Grid(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("h", C.c_double * 3)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("scale", C.c_int), ("m", C.c_int), ("f", C.c_double), ("coarsest_max_side", C.c_int),
+                ("precision", C.c_int), ("maxit_outer", C.c_int), ("maxit_inner", C.c_int),
+                ("timeout_ns", C.c_uint64), ("inner_floor", C.c_double), ("small_cells", C.c_int),
+                ("reserved", C.c_int * 7)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("levels", C.c_int), ("dims", (C.c_int * 3) * MAXLEV), ("iters", C.c_int64 * MAXLEV),
+                ("calls", C.c_int64 * MAXLEV), ("relres_recursive", C.c_double), ("relres_true", C.c_double),
+                ("status", C.c_int), ("restarts", C.c_int)]
+
+    def as_dict(self):
+        L = self.levels
+        return {"levels": L, "dims": [tuple(self.dims[k]) for k in range(L)],
+                "iters": [int(self.iters[k]) for k in range(L)], "calls": [int(self.calls[k]) for k in range(L)],
+                "relres_recursive": float(self.relres_recursive), "relres_true": float(self.relres_true),
+                "status": int(self.status), "restarts": int(self.restarts)}
+
+
+class MsrcgError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run paper_math_9809043_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        vp = C.c_void_p
+        L.msrcg_default_opts.argtypes = [C.POINTER(Opts)]
+        L.msrcg_build.argtypes = [C.POINTER(Grid), vp, C.c_int, vp, C.POINTER(Opts), vp, C.POINTER(vp)]
+        L.msrcg_lift_rhs.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.msrcg_solve.argtypes = [vp, vp, C.c_double, vp, C.POINTER(Stats), vp]
+        L.msrcg_batch_solve.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(vp), C.c_double, C.POINTER(vp),
+                                        C.POINTER(Stats), vp]
+        L.msrcg_level_info.argtypes = [vp, C.c_int, C.POINTER(C.c_int * 3), C.POINTER(C.c_int64),
+                                       C.POINTER(C.c_int64)]
+        L.msrcg_get_trans.argtypes = [vp, C.c_int, vp, vp, vp, vp]
+        L.msrcg_apply.argtypes = [vp, C.c_int, vp, vp, vp]
+        L.msrcg_num_levels.argtypes = [vp]
+        L.msrcg_device_bytes.argtypes = [vp]
+        L.msrcg_device_bytes.restype = C.c_size_t
+        L.msrcg_free.argtypes = [vp]
+        L.msrcg_free.restype = None
+        L.msrcg_strerror.argtypes = [C.c_int]
+        L.msrcg_strerror.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().msrcg_strerror(code).decode()
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    lib().msrcg_default_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def _dev(a, dtype, device):
+    if isinstance(a, torch.Tensor):
+        return a.to(device=device, dtype=dtype).contiguous()
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device=device)
+
+
+class Hierarchy:
+    """Level hierarchy of one problem, resident on the GPU (msrcg_build)."""
+
+    def __init__(self, dim, n, h, K, bc, opts: Opts | None = None, device="cuda", stream=None):
+        self.device = torch.device(device)
+        self.dim = dim
+        self.n = tuple(int(v) for v in n)
+        self.N = int(np.prod(self.n))
+        g = Grid()
+        g.dim = dim
+        for a in range(3):
+            g.n[a] = self.n[a] if a < dim else 1
+            g.h[a] = float(h[a]) if a < dim else 1.0
+        Kt = _dev(K, torch.float64, self.device).reshape(-1)
+        ncomp = Kt.numel() // max(self.N, 1)
+        bct = _dev(bc, torch.uint8, self.device)
+        self.opts = opts or default_opts()
+        hp = C.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = lib().msrcg_build(C.byref(g), _ptr(Kt), ncomp, _ptr(bct), C.byref(self.opts), _stream(stream),
+                                   C.byref(hp))
+        if rc != OK:
+            raise MsrcgError(rc, "msrcg_build")
+        self._h = hp
+        self.nlev = lib().msrcg_num_levels(self._h)
+
+    @classmethod
+    def from_problem(cls, prob, opts: Opts | None = None, device="cuda", stream=None):
+        return cls(prob.dim, prob.n, prob.h, prob.K, prob.bc, opts, device, stream)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().msrcg_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def device_bytes(self) -> int:
+        return int(lib().msrcg_device_bytes(self._h))
+
+    def dims(self, k):
+        d = (C.c_int * 3)()
+        it, ca = C.c_int64(), C.c_int64()
+        rc = lib().msrcg_level_info(self._h, k, C.byref(d), C.byref(it), C.byref(ca))
+        if rc != OK:
+            raise MsrcgError(rc, "msrcg_level_info")
+        return tuple(d), int(it.value), int(ca.value)
+
+    def lift_rhs(self, bc, gD, f, pbf, stream=None):
+        bct = _dev(bc, torch.uint8, self.device)
+        gDt = _dev(gD, torch.float64, self.device)
+        ft = _dev(f, torch.float64, self.device) if f is not None else None
+        pt = _dev(pbf, torch.float64, self.device)
+        b = torch.empty(self.N, dtype=torch.float64, device=self.device)
+        rc = lib().msrcg_lift_rhs(self._h, _ptr(bct), _ptr(gDt), _ptr(ft), _ptr(pt), _ptr(b), _stream(stream))
+        if rc != OK:
+            raise MsrcgError(rc, "msrcg_lift_rhs")
+        return b
+
+    def rhs_for(self, prob, stream=None):
+        """Device right-hand side of a generated problem (lifted or direct)."""
+        if prob.lifted:
+            return self.lift_rhs(prob.bc, prob.gD, prob.f, prob.pbf, stream)
+        return _dev(prob.b, torch.float64, self.device)
+
+    def solve(self, b, tol=1e-8, x=None, stats=True, stream=None, check=True):
+        b = _dev(b, torch.float64, self.device)
+        if x is None:
+            x = torch.empty(self.N, dtype=torch.float64, device=self.device)
+        st = Stats()
+        rc = lib().msrcg_solve(self._h, _ptr(b), float(tol), _ptr(x), C.byref(st) if stats else None,
+                               _stream(stream))
+        if check and rc != OK:
+            raise MsrcgError(rc, "msrcg_solve")
+        return x, (st.as_dict() if stats else {"status": rc})
+
+    def trans(self, k, stream=None):
+        d, _, _ = self.dims(k)
+        nx, ny, nz = d
+        Tx = torch.empty((nx + 1) * ny * nz, dtype=torch.float64, device=self.device)
+        Ty = torch.empty(nx * (ny + 1) * nz, dtype=torch.float64, device=self.device)
+        Tz = torch.empty(nx * ny * (nz + 1), dtype=torch.float64, device=self.device) if self.dim == 3 else None
+        rc = lib().msrcg_get_trans(self._h, k, _ptr(Tx), _ptr(Ty), _ptr(Tz), _stream(stream))
+        if rc != OK:
+            raise MsrcgError(rc, "msrcg_get_trans")
+        return Tx, Ty, Tz
+
+    def apply(self, k, x, stream=None):
+        x = _dev(x, torch.float64, self.device)
+        y = torch.empty_like(x)
+        rc = lib().msrcg_apply(self._h, k, _ptr(x), _ptr(y), _stream(stream))
+        if rc != OK:
+            raise MsrcgError(rc, "msrcg_apply")
+        return y
+
+
+def batch_solve(hs, bs, tol=1e-8, xs=None, stream=None, check=True):
+    """Solve independent problems in one persistent launch (msrcg_batch_solve)."""
+    n = len(hs)
+    if xs is None:
+        xs = [torch.empty(h.N, dtype=torch.float64, device=h.device) for h in hs]
+    H = (C.c_void_p * n)(*[h.handle.value for h in hs])
+    B = (C.c_void_p * n)(*[b.data_ptr() for b in bs])
+    X = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
+    st = (Stats * n)()
+    rc = lib().msrcg_batch_solve(n, H, B, float(tol), X, st, _stream(stream))
+    if check and rc != OK:
+        raise MsrcgError(rc, "msrcg_batch_solve")
+    return xs, [s.as_dict() for s in st]

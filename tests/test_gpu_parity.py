@@ -1,0 +1,222 @@
+"""GPU path vs the CPU oracle, through the C ABI (marked gpu).
+
+Bars: transmissibilities of every level bit-exact (integer overlap tables and
+explicitly rounded FP64 on both sides); operator and lifting within FP64
+rounding; solutions within 1e-6 relative error of the oracle at relative
+residual 1e-8 (the accuracy target of the method's GB300 build), per-level
+iteration counts equal in FP64 mode up to one iteration per call where a
+residual sits at a level threshold.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import oracle as O  # noqa: E402
+from paper_math_9809043_gb300 import problems as P  # noqa: E402
+
+SOL_RTOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def M():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_math_9809043_gb300 import build as B
+    B.build()
+    from paper_math_9809043_gb300 import msrcg
+    return msrcg
+
+
+def _prob_uniform(n, seed=5, span=2.0, lifted=True):
+    rng = np.random.default_rng(seed)
+    dim = len(n)
+    N = int(np.prod(n))
+    K = (10.0 ** rng.uniform(-span, span, N)).reshape(1, -1)
+    bc, gD = P.standard_bc(dim, n)
+    if lifted:
+        return P.Problem(dim=dim, n=tuple(n), h=tuple(1.0 / m for m in n), K=K, bc=bc, gD=gD,
+                         pbf=P.linear_lifting(dim, n), f=rng.standard_normal(N))
+    return P.Problem(dim=dim, n=tuple(n), h=tuple(1.0 / m for m in n), K=K, bc=bc, gD=gD,
+                     b=rng.standard_normal(N))
+
+
+def _counts_close(a, b, calls):
+    """Per-level iteration totals agree up to threshold flips: the GPU and
+    the oracle sum the residual norms in different orders, so a norm that
+    lands within rounding of a level's threshold can take one more or one
+    fewer iteration; allow 3% of the total (at least 1) per level."""
+    for k, (x, y) in enumerate(zip(a, b)):
+        assert abs(x - y) <= max(1, int(np.ceil(0.03 * y))), (k, a, b)
+
+
+# ---------------------------------------------------------------------------
+# build: transmissibilities, operator, lifting
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [(32, 32), (37, 23), (1, 1), (3, 2), (64, 4), (12, 10, 9), (7, 5, 3)])
+def test_transmissibility_bit_exact(M, n):
+    prob = _prob_uniform(n, span=4.5)
+    H = M.Hierarchy.from_problem(prob)
+    R = O.Hierarchy(prob)
+    assert H.nlev == R.nlev
+    for k in range(R.nlev):
+        got = [t.cpu().numpy() if t is not None else None for t in H.trans(k)]
+        ref = R.T(k)
+        for a in range(prob.dim):
+            assert np.array_equal(got[a], ref[a]), (k, a, np.max(np.abs(got[a] - ref[a])))
+
+
+def test_transmissibility_bit_exact_full_size(M):
+    prob = P.config_problem(1)  # 1024^2, 1e9 contrast
+    H = M.Hierarchy.from_problem(prob)
+    R = O.Hierarchy(prob)
+    for k in range(R.nlev):
+        got = H.trans(k)
+        ref = R.T(k)
+        for a in range(2):
+            assert np.array_equal(got[a].cpu().numpy(), ref[a]), (k, a)
+
+
+@pytest.mark.parametrize("n", [(32, 32), (37, 23), (9, 8, 7)])
+def test_apply_and_lift(M, n):
+    prob = _prob_uniform(n, span=4.5)
+    H = M.Hierarchy.from_problem(prob)
+    R = O.Hierarchy(prob)
+    rng = np.random.default_rng(1)
+    for k in range(R.nlev):
+        x = rng.standard_normal(R.ncells(k))
+        y = H.apply(k, torch.as_tensor(x, device="cuda")).cpu().numpy()
+        yr = R.apply(k, x)
+        assert np.max(np.abs(y - yr)) <= 1e-12 * np.max(np.abs(yr))
+    b = H.rhs_for(prob).cpu().numpy()
+    br = R.lift_rhs()
+    assert np.max(np.abs(b - br)) <= 1e-12 * np.max(np.abs(br))
+
+
+# ---------------------------------------------------------------------------
+# solve parity
+# ---------------------------------------------------------------------------
+CASES = [
+    ("cfg0", lambda: P.config_problem(0), 0),
+    ("ragged-37x23", lambda: _prob_uniform((37, 23)), 0),
+    ("ragged-37x23-wide", lambda: _prob_uniform((37, 23)), 64),
+    ("grf-128", lambda: P.config_problem(1, scale=128), 0),
+    ("grf-200x72-wide", lambda: P.grf_problem((200, 72), seed=21, ell=6.0, half_span=4.5), 256),
+    ("strip-64x4", lambda: _prob_uniform((64, 4)), 0),
+    ("tiny-3x2", lambda: _prob_uniform((3, 2)), 0),
+    ("direct-rhs-50x50", lambda: _prob_uniform((50, 50), lifted=False), 128),
+    ("chan3d-16", lambda: P.config_problem(2, scale=16), 0),
+    ("chan3d-24-wide", lambda: P.config_problem(2, scale=24), 256),
+    ("ragged3d-13x9x7", lambda: _prob_uniform((13, 9, 7)), 64),
+]
+
+
+@pytest.mark.parametrize("name,mk,small", CASES, ids=[c[0] for c in CASES])
+def test_solve_fp64_matches_oracle(M, name, mk, small):
+    prob = mk()
+    H = M.Hierarchy.from_problem(prob, M.default_opts(precision=0, small_cells=small))
+    b = H.rhs_for(prob)
+    x, st = H.solve(b, 1e-8)
+    R = O.Hierarchy(prob)
+    xr, sr = R.solve(R.lift_rhs(), 1e-8)
+    assert sr["status"] == 0 and st["status"] == 0, (st, sr)
+    assert st["relres_true"] < 1e-8
+    xg = x.cpu().numpy()
+    err = np.linalg.norm(xg - xr) / max(np.linalg.norm(xr), 1e-300)
+    assert err <= SOL_RTOL, err
+    _counts_close(st["iters"], sr["iters"], sr["calls"])
+    # bookkeeping invariant of the recursion: calls(k+1) = iterations(k)
+    for k in range(len(st["iters"]) - 1):
+        assert st["calls"][k + 1] == st["iters"][k]
+
+
+@pytest.mark.parametrize("name,mk,small", CASES, ids=[c[0] for c in CASES])
+def test_solve_fp32_precond_matches_oracle(M, name, mk, small):
+    prob = mk()
+    H = M.Hierarchy.from_problem(prob, M.default_opts(precision=1, small_cells=small, inner_floor=1e-6))
+    b = H.rhs_for(prob)
+    x, st = H.solve(b, 1e-8)
+    R = O.Hierarchy(prob)
+    xr, sr = R.solve(R.lift_rhs(), 1e-8)
+    assert st["status"] == 0, st
+    assert st["relres_true"] < 1e-8
+    err = np.linalg.norm(x.cpu().numpy() - xr) / max(np.linalg.norm(xr), 1e-300)
+    assert err <= SOL_RTOL, err
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_full_size_1024_matches_oracle(M, prec):
+    prob = P.config_problem(1)
+    H = M.Hierarchy.from_problem(prob, M.default_opts(precision=prec, inner_floor=1e-6 if prec else 0.0))
+    b = H.rhs_for(prob)
+    x, st = H.solve(b, 1e-8)
+    R = O.Hierarchy(prob)
+    xr, sr = R.solve(R.lift_rhs(), 1e-8)
+    assert st["status"] == 0 and st["relres_true"] < 1e-8, st
+    err = np.linalg.norm(x.cpu().numpy() - xr) / np.linalg.norm(xr)
+    assert err <= SOL_RTOL, err
+    if prec == 0:
+        _counts_close(st["iters"], sr["iters"], sr["calls"])
+
+
+def test_repeat_solves_identical(M):
+    """Deterministic reductions: two solves give the same bits."""
+    prob = P.config_problem(1, scale=256)
+    H = M.Hierarchy.from_problem(prob, M.default_opts(precision=1, inner_floor=1e-6))
+    b = H.rhs_for(prob)
+    x1, s1 = H.solve(b, 1e-8)
+    x2, s2 = H.solve(b, 1e-8)
+    assert torch.equal(x1, x2) and s1["iters"] == s2["iters"]
+
+
+# ---------------------------------------------------------------------------
+# degenerate inputs and errors
+# ---------------------------------------------------------------------------
+def test_zero_rhs(M):
+    prob = _prob_uniform((40, 40))
+    for small in (0, 64):
+        H = M.Hierarchy.from_problem(prob, M.default_opts(small_cells=small))
+        x, st = H.solve(torch.zeros(1600, dtype=torch.float64, device="cuda"), 1e-8)
+        assert st["status"] == 0 and torch.count_nonzero(x).item() == 0 and st["iters"][0] == 0
+
+
+def test_nan_rhs_reports_enaninf(M):
+    prob = _prob_uniform((40, 40))
+    for small in (0, 64):
+        H = M.Hierarchy.from_problem(prob, M.default_opts(small_cells=small))
+        b = torch.ones(1600, dtype=torch.float64, device="cuda")
+        b[7] = float("nan")
+        x, st = H.solve(b, 1e-8, check=False)
+        assert st["status"] == M.ENANINF
+
+
+def test_invalid_arguments(M):
+    prob = _prob_uniform((8, 8))
+    with pytest.raises(M.MsrcgError):
+        M.Hierarchy(2, (0, 8), (0.1, 0.1), prob.K, prob.bc)
+    with pytest.raises(M.MsrcgError):
+        M.Hierarchy(4, (8, 8), (0.1, 0.1), prob.K, prob.bc)
+    H = M.Hierarchy.from_problem(prob)
+    with pytest.raises(M.MsrcgError):
+        H.solve(torch.ones(64, dtype=torch.float64, device="cuda"), tol=-1.0)
+
+
+# ---------------------------------------------------------------------------
+# batched solve
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_matches_oracle(M, prec):
+    probs = [_prob_uniform((n, n), seed=100 + i, lifted=False) for i, n in enumerate([24, 40, 17, 64, 33, 9, 48, 30])]
+    opts = M.default_opts(precision=prec, inner_floor=1e-6 if prec else 0.0)
+    hs = [M.Hierarchy.from_problem(p, opts) for p in probs]
+    bs = [h.rhs_for(p) for h, p in zip(hs, probs)]
+    xs, sts = M.batch_solve(hs, bs, 1e-8)
+    for p, x, st in zip(probs, xs, sts):
+        R = O.Hierarchy(p)
+        xr, sr = R.solve(R.lift_rhs(), 1e-8)
+        assert st["status"] == 0 and st["relres_true"] < 1e-8
+        err = np.linalg.norm(x.cpu().numpy() - xr) / np.linalg.norm(xr)
+        assert err <= SOL_RTOL
+        if prec == 0:
+            _counts_close(st["iters"], sr["iters"], sr["calls"])
