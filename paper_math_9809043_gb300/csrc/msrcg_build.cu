@@ -75,7 +75,8 @@ int level_sides(int dim, const int n[3], int s, int limit, int out[][3]) {
 // the first coarse centre.  Outside [0, nc-1] the end value is held.
 struct Axis1D {
   std::vector<int> c0, c1, lo, hi;
-  std::vector<double> w;
+  std::vector<double> w, rw;  // rw: restriction weights, W per coarse cell
+  int W = 1;
 };
 
 Axis1D axis_tables(int nf, int nc) {
@@ -118,6 +119,16 @@ Axis1D axis_tables(int nf, int nc) {
       A.hi[cs[e]] = std::max(A.hi[cs[e]], i);
     }
   }
+  A.W = 1;
+  for (int I = 0; I < nc; ++I) A.W = std::max(A.W, A.hi[I] - A.lo[I] + 1);
+  A.rw.assign((size_t)nc * A.W, 0.0);
+  for (int I = 0; I < nc; ++I)
+    for (int i = A.lo[I]; i <= A.hi[I]; ++i) {
+      double v = 0.0;
+      if (A.c0[i] == I) v += 1.0 - A.w[i];
+      if (A.c1[i] == I) v += A.w[i];
+      A.rw[(size_t)I * A.W + (i - A.lo[I])] = v;
+    }
   return A;
 }
 
@@ -495,7 +506,8 @@ extern "C" int msrcg_build(const msrcg_grid* grid, const double* K, int ncomp, c
   h->nlev = level_sides(dim, n3, o.scale, o.coarsest_max_side, h->dims);
   if (h->nlev < 1) return fail(MSRCG_EINVAL);
   for (int k = 0; k < h->nlev; ++k) h->N[k] = (long long)h->dims[k][0] * h->dims[k][1] * h->dims[k][2];
-  if (h->N[h->nlev - 1] > 4096) return fail(MSRCG_EINVAL);
+  if ((long long)(n3[0] + 2) * (n3[1] + 2) * (n3[2] + 2) >= (1LL << 31)) return fail(MSRCG_EINVAL);
+  if (h->N[h->nlev - 1] > 1024) return fail(MSRCG_EINVAL);
   h->ks = h->nlev - 1;
   while (h->ks > 0 && h->N[h->ks - 1] <= o.small_cells) --h->ks;
 
@@ -558,6 +570,11 @@ extern "C" int msrcg_build(const msrcg_grid* grid, const double* K, int ncomp, c
     L.nz = h->dims[k][2];
     L.dim = dim;
     L.n = h->N[k];
+    L.px = L.nx + 2;
+    L.py = L.ny + 2;
+    L.plane = (long long)L.px * L.py;
+    L.off = 1 + L.px + (dim == 3 ? L.plane : 0);
+    L.npad = L.plane * (dim == 3 ? L.nz + 2 : 1);
     for (int a = 0; a < dim; ++a) {
       L.T[a] = h->TR[k][a];
       L.T64[a] = h->T64[k][a];
@@ -580,26 +597,41 @@ extern "C" int msrcg_build(const msrcg_grid* grid, const double* K, int ncomp, c
         if (f32) {
           std::vector<float> wf(ax.w.begin(), ax.w.end());
           if ((rc = upload(h, wf, &p))) return fail(rc);
+          L.w[a] = p;
+          std::vector<float> rf(ax.rw.begin(), ax.rw.end());
+          if ((rc = upload(h, rf, &p))) return fail(rc);
+          L.rw[a] = p;
         } else {
           if ((rc = upload(h, ax.w, &p))) return fail(rc);
+          L.w[a] = p;
+          if ((rc = upload(h, ax.rw, &p))) return fail(rc);
+          L.rw[a] = p;
         }
-        L.w[a] = p;
+        L.W[a] = ax.W;
       }
     }
+    // padded vectors; the ghost ring is zeroed here and never written
     const size_t vsz = k == 0 ? sizeof(double) : rsz;
     void* p;
-    if ((rc = msrcg_alloc(h, &p, vsz * L.n))) return fail(rc);
-    L.x = p;
-    if ((rc = msrcg_alloc(h, &p, vsz * L.n))) return fail(rc);
-    L.r = p;
-    if ((rc = msrcg_alloc(h, &p, vsz * L.n))) return fail(rc);
-    L.p = p;
-    if ((rc = msrcg_alloc(h, &p, vsz * L.n))) return fail(rc);
-    L.q = p;
-    if ((rc = msrcg_alloc(h, &p, rsz * L.n))) return fail(rc);
+    void** vv[4] = {&L.x, &L.r, &L.p, &L.q};
+    for (int v = 0; v < 4; ++v) {
+      if ((rc = msrcg_alloc(h, &p, vsz * L.npad))) return fail(rc);
+      MSRCG_CUDA_TRY(cudaMemsetAsync(p, 0, vsz * L.npad, st));
+      *vv[v] = p;
+    }
+    if ((rc = msrcg_alloc(h, &p, rsz * L.npad))) return fail(rc);
+    MSRCG_CUDA_TRY(cudaMemsetAsync(p, 0, rsz * L.npad, st));
     L.z = p;
-    if ((rc = msrcg_alloc(h, &p, rsz * L.n))) return fail(rc);
+    if ((rc = msrcg_alloc(h, &p, rsz * L.npad))) return fail(rc);
+    MSRCG_CUDA_TRY(cudaMemsetAsync(p, 0, rsz * L.npad, st));
     L.t = p;
+    if (vsz != rsz) {
+      if ((rc = msrcg_alloc(h, &p, rsz * L.npad))) return fail(rc);
+      MSRCG_CUDA_TRY(cudaMemsetAsync(p, 0, rsz * L.npad, st));
+      L.rp = p;
+    } else {
+      L.rp = L.r;
+    }
   }
   // ---- coarsest exact inverse (A3) ----
   {
@@ -631,9 +663,11 @@ extern "C" int msrcg_build(const msrcg_grid* grid, const double* K, int ncomp, c
     MSRCG_CUDA_TRY(cudaMemset(h->dS, 0, sizeof(SolveState)));
     if ((rc = msrcg_alloc(h, &p, sizeof(double) * kMaxLev * (size_t)std::max(gmax, kMaxGrid)))) return fail(rc);
     h->partials = (double*)p;
-    if ((rc = msrcg_alloc(h, &p, sizeof(double) * h->N[0]))) return fail(rc);
+    if ((rc = msrcg_alloc(h, &p, sizeof(double) * h->hL[0].npad))) return fail(rc);
+    MSRCG_CUDA_TRY(cudaMemsetAsync(p, 0, sizeof(double) * h->hL[0].npad, st));
     h->b0 = (double*)p;
-    if ((rc = msrcg_alloc(h, &p, sizeof(double) * h->N[0]))) return fail(rc);
+    if ((rc = msrcg_alloc(h, &p, sizeof(double) * h->hL[0].npad))) return fail(rc);
+    MSRCG_CUDA_TRY(cudaMemsetAsync(p, 0, sizeof(double) * h->hL[0].npad, st));
     h->xs = (double*)p;
     if ((rc = msrcg_alloc(h, &p, sizeof(ProblemDesc)))) return fail(rc);
     h->dP = (ProblemDesc*)p;

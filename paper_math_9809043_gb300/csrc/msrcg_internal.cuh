@@ -33,9 +33,16 @@ constexpr int kStNanInf = 8;
 
 // One level of the hierarchy as the kernels see it.  Face arrays: Tx has
 // (nx+1)*ny*nz entries (x fastest), Ty nx*(ny+1)*nz, Tz nx*ny*(nz+1).
+// Vectors are stored with a ring of ghost cells that stay zero: cell
+// (i, j, k) lives at off + i + px*j + plane*k with px = nx+2, plane =
+// px*(ny+2); npad is the padded length.  A zero ghost makes every boundary
+// face behave like the paper's boundary treatment without a branch: the
+// Gauss-Seidel sum gains T_b * 0 and the operator T_b (x_c - 0).
 struct DevLevel {
   int nx, ny, nz, dim;
   long long n;
+  int px, py;
+  long long plane, off, npad;
   const void* T[3];      // smoother-precision transmissibilities (float or double)
   const double* T64[3];  // FP64 transmissibilities
   // prolongation tables of the transfer to level k+1, indexed by fine cell
@@ -44,9 +51,12 @@ struct DevLevel {
   const int* c1[3];
   const void* w[3];      // smoother precision
   // restriction windows, indexed by coarse cell of level k+1 along each axis:
-  // the fine cells [lo, hi] that interpolate from it
+  // the fine cells [lo, hi] that interpolate from it, and their weights
+  // rw[I*W + t] (fine cell lo[I] + t), W = the longest window of the axis
   const int* lo[3];
   const int* hi[3];
+  const void* rw[3];     // smoother precision
+  int W[3];
   // vectors: x, r, p, q in the level's vector type; z, t in smoother precision
   void* x;
   void* r;
@@ -54,6 +64,7 @@ struct DevLevel {
   void* q;
   void* z;
   void* t;
+  void* rp;              // r in smoother precision (aliases r when the types agree)
   double fk;             // f^k of the level test
   int maxit;
   int pad;
@@ -61,6 +72,8 @@ struct DevLevel {
 
 struct LevelState {
   double rho, rho_old, pq, rr, bb, thr;
+  double alpha, beta;    // CG step scalars of the current iteration
+  float alpha_f, beta_f; // the same in FP32 for FP32 levels
   long long iters, calls;
   int it, stop;
 };
@@ -85,8 +98,9 @@ struct ProblemDesc {
   int nc;
   int precision;
   SolveState* S;
-  const double* b;       // caller right-hand side (level 0)
-  double* x;             // caller solution (level 0)
+  const double* b;       // caller right-hand side (level 0, unpadded)
+  double* x;             // caller solution (level 0, unpadded)
+  double* xs;            // padded FP64 accumulator of the level-0 solution
   double tol;
   long long work;        // scheduling weight (cells of level 0)
 };
@@ -116,6 +130,8 @@ struct msrcg_hier {
   // level loop graph
   cudaGraphExec_t gexec = nullptr;
   cudaGraph_t graph = nullptr;
+  size_t sub_smem = 0;                  // dynamic shared memory of the graph's single-CTA launch
+  bool dirty = false;                   // last solve failed: clear the vectors before the next
   int64_t last_iters[MSRCG_MAXLEV] = {};
   int64_t last_calls[MSRCG_MAXLEV] = {};
   int sms = 0;

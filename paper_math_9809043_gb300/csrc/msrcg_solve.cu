@@ -5,10 +5,13 @@
 // graph sequences; each level's PCG loop is a graph WHILE node whose
 // condition the last kernel of an iteration sets on the device, so no host
 // round trip decides anything.  Levels ks..kmax ("narrow" levels, few cells)
-// run inside one CTA that executes the whole remaining recursion: the level
-// stack is an explicit state machine over levels, with __syncthreads between
-// dependent steps.  The same single-CTA solver also runs complete problems,
-// one per CTA, for the batched entry point.
+// run inside one CTA that executes the whole remaining recursion from shared
+// memory: the level stack is an explicit state machine, with __syncthreads
+// between dependent steps.  The same single-CTA solver also runs complete
+// problems, one per CTA, for the batched entry point.
+//
+// Vectors use the padded layout of DevLevel (a zero ghost ring), so stencils
+// have no boundary branches, and threads map onto (column, row) directly.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -25,6 +28,8 @@ using namespace msrcg;
 
 namespace {
 
+constexpr int kMaxCoarse = 1024;  // largest coarsest level (cells) of the dense inverse
+
 // ---------------------------------------------------------------------------
 // small device helpers
 // ---------------------------------------------------------------------------
@@ -34,22 +39,36 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Deterministic block sum; every thread returns the total.  `sh` holds 33
-// doubles of shared memory.
-__device__ double block_sum(double v, double* sh) {
-  v = warp_sum(v);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  __syncthreads();
-  if (lane == 0) sh[wid] = v;
-  __syncthreads();
-  if (wid == 0) {
-    double t = lane < nw ? sh[lane] : 0.0;
-    t = warp_sum(t);
-    if (lane == 0) sh[32] = t;
-  }
-  __syncthreads();
-  return sh[32];
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
 }
+
+// The CTA as one team.  sum(): deterministic total in the value's own
+// precision with one barrier; warp sums go to one of two buffers
+// (alternating, so a buffer is rewritten only after a later barrier), then
+// every thread adds them in index order.  FP32 levels never touch the FP64
+// pipe, which is narrow on this GPU.
+struct BlockTeam {
+  double* shd;  // 64 doubles of shared memory
+  float* shf;   // 64 floats of shared memory
+  int par;
+  __device__ __forceinline__ void sync() { __syncthreads(); }
+  template <typename T>
+  __device__ __forceinline__ T sum(T v) {
+    v = warp_sum_t<T>(v);
+    T* b = (sizeof(T) == sizeof(double) ? (T*)shd : (T*)shf) + 32 * par;
+    par ^= 1;
+    if ((threadIdx.x & 31) == 0) b[threadIdx.x >> 5] = v;
+    __syncthreads();
+    T t = 0;
+    const int nw = blockDim.x >> 5;
+    for (int w = 0; w < nw; ++w) t += b[w];
+    return t;
+  }
+};
 
 template <typename V>
 __device__ __forceinline__ const V* Tvec(const DevLevel& L, int a);
@@ -62,156 +81,207 @@ __device__ __forceinline__ const float* Tvec<float>(const DevLevel& L, int a) {
   return (const float*)L.T[a];
 }
 
-struct Cell {
-  int i, j, k;
-  long long c;
+// Position and strides of a thread in the (column, row) plane of a level.
+struct Map {
+  int x0, dx, y0, dy;
 };
 
-__device__ __forceinline__ Cell cell_of(long long c, int nx, int ny) {
-  Cell q;
-  q.c = c;
-  q.i = (int)(c % nx);
-  long long rw = c / nx;
-  q.j = (int)(rw % ny);
-  q.k = (int)(rw / ny);
-  return q;
+// The CTA laid over rows of `width` columns: a power-of-two row width.
+__device__ __forceinline__ Map team_map(int width) {
+  int bx = 1;
+  while (bx < width && bx < (int)blockDim.x) bx <<= 1;
+  const int sh = __ffs(bx) - 1;
+  Map m;
+  m.x0 = threadIdx.x & (bx - 1);
+  m.dx = bx;
+  m.y0 = threadIdx.x >> sh;
+  m.dy = blockDim.x >> sh;
+  return m;
 }
 
-// Cell (i, j, k) of colour `colour` for pair index p (the colour's cells of a
-// row are i = 2*ii + ((j + k + colour) & 1)); returns false past the row end.
-__device__ __forceinline__ bool colour_cell(long long p, int colour, int nx, int ny, Cell& q) {
-  const int hx = (nx + 1) >> 1;
-  int ii = (int)(p % hx);
-  long long rw = p / hx;
-  q.j = (int)(rw % ny);
-  q.k = (int)(rw / ny);
-  q.i = 2 * ii + ((q.j + q.k + colour) & 1);
-  q.c = q.i + (long long)nx * rw;
-  return q.i < nx;
+// A 2D grid of 2D blocks laid over rows.
+__device__ __forceinline__ Map grid_map() {
+  Map m;
+  m.x0 = blockIdx.x * blockDim.x + threadIdx.x;
+  m.dx = gridDim.x * blockDim.x;
+  m.y0 = blockIdx.y * blockDim.y + threadIdx.y;
+  m.dy = gridDim.y * blockDim.y;
+  return m;
+}
+
+// Offsets of column 0 of one row (j, k) of a level: padded vector index and
+// the face-array indices.  Cell (i, j, k) of the row is at pc + i; its faces
+// are Tx[fx + i], Tx[fx + i + 1], Ty[fy + i], Ty[fy + i + nx], Tz[fz + i],
+// Tz[fz + i + nx*ny].  All level indices fit 32 bits (the build checks).
+struct Row {
+  int j, k, pc, fx, fy, fz;
+};
+
+template <int DIM>
+__device__ __forceinline__ Row make_row(const DevLevel& L, int row) {
+  Row r;
+  r.j = row;
+  r.k = 0;
+  if (DIM == 3) {
+    r.k = row / L.ny;
+    r.j = row - r.k * L.ny;
+  }
+  r.pc = (int)L.off + L.px * r.j + (int)L.plane * r.k;
+  r.fx = (L.nx + 1) * row;
+  r.fy = L.nx * (row + r.k);
+  r.fz = L.nx * row;
+  return r;
+}
+
+// Visit every cell of the level: f(i, row).
+template <int DIM, class F>
+__device__ __forceinline__ void for_cells(const Map& m, const DevLevel& L, F&& f) {
+  const int rows = L.ny * L.nz;
+  for (int row = m.y0; row < rows; row += m.dy) {
+    const Row r = make_row<DIM>(L, row);
+    for (int i = m.x0; i < L.nx; i += m.dx) f(i, r);
+  }
+}
+
+// Visit the cells of one colour ((i + j + k) & 1 == colour): in a row they
+// are i = 2*ii + ((j + k + colour) & 1).  f(i, i2, row) also gets the other
+// colour's cell at the same pair position (i2); either may be >= nx.
+template <int DIM, class F>
+__device__ __forceinline__ void for_colour(const Map& m, const DevLevel& L, int colour, F&& f) {
+  const int rows = L.ny * L.nz;
+  const int hx = (L.nx + 1) >> 1;
+  for (int row = m.y0; row < rows; row += m.dy) {
+    const Row r = make_row<DIM>(L, row);
+    const int s = (r.j + r.k + colour) & 1;
+    for (int ii = m.x0; ii < hx; ii += m.dx) f(2 * ii + s, 2 * ii + (s ^ 1), r);
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ R quot(R a, R b);
+template <>
+__device__ __forceinline__ float quot<float>(float a, float b) {
+  return __fdividef(a, b);
+}
+template <>
+__device__ __forceinline__ double quot<double>(double a, double b) {
+  return a / b;
 }
 
 // Sum of the face transmissibilities of a cell (the diagonal of A).
 template <int DIM, typename R>
-__device__ __forceinline__ R diag_of(const DevLevel& L, const R* Tx, const R* Ty, const R* Tz, const Cell& q) {
-  const long long row = q.j + (long long)L.ny * q.k, ky = q.c + (long long)L.nx * q.k;
-  R d = Tx[q.c + row];
-  d += Tx[q.c + row + 1];
-  d += Ty[ky];
-  d += Ty[ky + L.nx];
+__device__ __forceinline__ R diag_of(const DevLevel& L, const R* Tx, const R* Ty, const R* Tz, int i, const Row& r) {
+  R d = Tx[r.fx + i];
+  d += Tx[r.fx + i + 1];
+  d += Ty[r.fy + i];
+  d += Ty[r.fy + i + L.nx];
   if (DIM == 3) {
-    d += Tz[q.c];
-    d += Tz[q.c + (long long)L.nx * L.ny];
+    d += Tz[r.fz + i];
+    d += Tz[r.fz + i + L.nx * L.ny];
   }
   return d;
 }
 
 // Gauss-Seidel value of one cell: row c of A solved for x_c with the
-// neighbours held, x_c = (rhs_c + sum_f T_f x_nb) / sum_f T_f  (Sec. 3).
-template <int DIM, typename R, typename RB>
-__device__ __forceinline__ R gs_value(const DevLevel& L, const R* Tx, const R* Ty, const R* Tz, const RB* rhs,
-                                      const R* x, const Cell& q) {
-  const int nx = L.nx, ny = L.ny;
-  const long long c = q.c, row = q.j + (long long)ny * q.k, ky = c + (long long)nx * q.k;
-  R t = Tx[c + row], d = t, s = (R)rhs[c];
-  if (q.i > 0) s += t * x[c - 1];
-  t = Tx[c + row + 1];
-  d += t;
-  if (q.i < nx - 1) s += t * x[c + 1];
-  t = Ty[ky];
-  d += t;
-  if (q.j > 0) s += t * x[c - nx];
-  t = Ty[ky + nx];
-  d += t;
-  if (q.j < ny - 1) s += t * x[c + nx];
+// neighbours held, x_c = (rhs_c + sum_f T_f x_nb) / sum_f T_f  (Sec. 3); a
+// boundary face meets a zero ghost.  The FP32 smoother divides with the
+// fast hardware quotient; FP64 divides exactly.
+template <int DIM, typename R, typename RX>
+__device__ __forceinline__ R gs_value(const DevLevel& L, const R* Tx, const R* Ty, const R* Tz, R rhs, const RX* x,
+                                      int i, const Row& r) {
+  const int pc = r.pc + i;
+  const R tw = Tx[r.fx + i], te = Tx[r.fx + i + 1], ts = Ty[r.fy + i], tn = Ty[r.fy + i + L.nx];
+  R d = tw;
+  d += te;
+  d += ts;
+  d += tn;
+  R s = rhs;
+  s += tw * (R)x[pc - 1];
+  s += te * (R)x[pc + 1];
+  s += ts * (R)x[pc - L.px];
+  s += tn * (R)x[pc + L.px];
   if (DIM == 3) {
-    const long long pl = (long long)nx * ny;
-    t = Tz[c];
-    d += t;
-    if (q.k > 0) s += t * x[c - pl];
-    t = Tz[c + pl];
-    d += t;
-    if (q.k < L.nz - 1) s += t * x[c + pl];
+    const int pl = (int)L.plane;
+    const R tb = Tz[r.fz + i], tt = Tz[r.fz + i + L.nx * L.ny];
+    d += tb;
+    d += tt;
+    s += tb * (R)x[pc - pl];
+    s += tt * (R)x[pc + pl];
   }
-  return s / d;
+  return quot<R>(s, d);
 }
 
-// (A x)_c = sum_f T_f (x_c - x_nb), T_f x_c on boundary faces.
+// (A x)_c = sum_f T_f (x_c - x_nb); a boundary face gives T_f x_c.
 template <int DIM, typename R, typename RX>
-__device__ __forceinline__ R apply_value(const DevLevel& L, const R* Tx, const R* Ty, const R* Tz, const RX* x,
-                                         const Cell& q) {
-  const int nx = L.nx, ny = L.ny;
-  const long long c = q.c, row = q.j + (long long)ny * q.k, ky = c + (long long)nx * q.k;
-  const R xc = (R)x[c];
-  R s = 0, t;
-  t = Tx[c + row];
-  s += q.i > 0 ? t * (xc - (R)x[c - 1]) : t * xc;
-  t = Tx[c + row + 1];
-  s += q.i < nx - 1 ? t * (xc - (R)x[c + 1]) : t * xc;
-  t = Ty[ky];
-  s += q.j > 0 ? t * (xc - (R)x[c - nx]) : t * xc;
-  t = Ty[ky + nx];
-  s += q.j < ny - 1 ? t * (xc - (R)x[c + nx]) : t * xc;
+__device__ __forceinline__ R apply_value(const DevLevel& L, const R* Tx, const R* Ty, const R* Tz, const RX* x, int i,
+                                         const Row& r) {
+  const int pc = r.pc + i;
+  const R xc = (R)x[pc];
+  R s = Tx[r.fx + i] * (xc - (R)x[pc - 1]);
+  s += Tx[r.fx + i + 1] * (xc - (R)x[pc + 1]);
+  s += Ty[r.fy + i] * (xc - (R)x[pc - L.px]);
+  s += Ty[r.fy + i + L.nx] * (xc - (R)x[pc + L.px]);
   if (DIM == 3) {
-    const long long pl = (long long)nx * ny;
-    t = Tz[c];
-    s += q.k > 0 ? t * (xc - (R)x[c - pl]) : t * xc;
-    t = Tz[c + pl];
-    s += q.k < L.nz - 1 ? t * (xc - (R)x[c + pl]) : t * xc;
+    const int pl = (int)L.plane;
+    s += Tz[r.fz + i] * (xc - (R)x[pc - pl]);
+    s += Tz[r.fz + i + L.nx * L.ny] * (xc - (R)x[pc + pl]);
   }
   return s;
 }
 
-// Weight of fine index i on coarse index I in the 1-D interpolation table.
-template <typename R>
-__device__ __forceinline__ R tw(const int* c0, const int* c1, const R* w, int i, int I) {
-  R v = 0;
-  if (c0[i] == I) v += (R)1 - w[i];
-  if (c1[i] == I) v += w[i];
-  return v;
-}
-
 // (R t)_C = (E^T t)_C for coarse cell (I, J, K) of level k+1: a gather over
-// the fine cells whose interpolation uses it (Sec. 3, R = E^T).
+// the window of fine cells that interpolate from it, with the tabled weights
+// (Sec. 3, R = E^T).
 template <int DIM, typename R>
 __device__ __forceinline__ R restrict_value(const DevLevel& F, const R* t, int I, int J, int K) {
-  const R *wx = (const R*)F.w[0], *wy = (const R*)F.w[1];
+  const R* rwx = (const R*)F.rw[0] + (long long)I * F.W[0];
+  const R* rwy = (const R*)F.rw[1] + (long long)J * F.W[1];
+  const int ilo = __ldg(F.lo[0] + I), ihi = __ldg(F.hi[0] + I), jlo = __ldg(F.lo[1] + J), jhi = __ldg(F.hi[1] + J);
+  int klo = 0, khi = 0;
+  const R* rwz = nullptr;
+  if (DIM == 3) {
+    klo = __ldg(F.lo[2] + K);
+    khi = __ldg(F.hi[2] + K);
+    rwz = (const R*)F.rw[2] + (long long)K * F.W[2];
+  }
   R acc = 0;
-  const int klo = DIM == 3 ? F.lo[2][K] : 0, khi = DIM == 3 ? F.hi[2][K] : 0;
   for (int kk = klo; kk <= khi; ++kk) {
-    const R wz = DIM == 3 ? tw<R>(F.c0[2], F.c1[2], (const R*)F.w[2], kk, K) : (R)1;
     R accy = 0;
-    for (int jj = F.lo[1][J]; jj <= F.hi[1][J]; ++jj) {
-      const R wyv = tw<R>(F.c0[1], F.c1[1], wy, jj, J);
-      const R* row = t + (long long)F.nx * (jj + (long long)F.ny * kk);
+    for (int jj = jlo; jj <= jhi; ++jj) {
+      const R* row = t + ((int)F.off + F.px * jj + (int)F.plane * kk);
       R accx = 0;
-      for (int ii = F.lo[0][I]; ii <= F.hi[0][I]; ++ii) accx += tw<R>(F.c0[0], F.c1[0], wx, ii, I) * row[ii];
-      accy += wyv * accx;
+      for (int ii = ilo; ii <= ihi; ++ii) accx += __ldg(rwx + (ii - ilo)) * row[ii];
+      accy += __ldg(rwy + (jj - jlo)) * accx;
     }
-    acc += wz * accy;
+    acc += (DIM == 3 ? __ldg(rwz + (kk - klo)) : (R)1) * accy;
   }
   return acc;
 }
 
-// (E x_c)_c for fine cell q: tensor product of the 1-D linear interpolation
-// with zero slope at the boundary (Sec. 3).
-template <int DIM, typename R, typename RX>
-__device__ __forceinline__ R prolong_value(const DevLevel& F, const DevLevel& Cc, const RX* xc, const Cell& q) {
-  const R *wxp = (const R*)F.w[0], *wyp = (const R*)F.w[1];
-  const R wx = wxp[q.i], wy = wyp[q.j];
-  const int i0 = F.c0[0][q.i], i1 = F.c1[0][q.i], j0 = F.c0[1][q.j], j1 = F.c1[1][q.j];
-  const int cnx = Cc.nx, cny = Cc.ny;
+// (E x_c) at fine cell (i, j, k): tensor product of the 1-D linear
+// interpolation with zero slope at the boundary (Sec. 3).
+template <int DIM, typename R>
+__device__ __forceinline__ R prolong_value(const DevLevel& F, const DevLevel& C, const R* xc, int i, int j, int k) {
+  const int coff = (int)C.off, cpl = (int)C.plane;
+  const R wx = __ldg((const R*)F.w[0] + i), wy = __ldg((const R*)F.w[1] + j);
+  const int i0 = __ldg(F.c0[0] + i), i1 = __ldg(F.c1[0] + i), j0 = __ldg(F.c0[1] + j), j1 = __ldg(F.c1[1] + j);
   if (DIM == 2) {
-    const R a = ((R)1 - wx) * (R)xc[i0 + (long long)cnx * j0] + wx * (R)xc[i1 + (long long)cnx * j0];
-    const R b = ((R)1 - wx) * (R)xc[i0 + (long long)cnx * j1] + wx * (R)xc[i1 + (long long)cnx * j1];
+    const R* r0 = xc + (coff + C.px * j0);
+    const R* r1 = xc + (coff + C.px * j1);
+    const R a = ((R)1 - wx) * r0[i0] + wx * r0[i1];
+    const R b = ((R)1 - wx) * r1[i0] + wx * r1[i1];
     return ((R)1 - wy) * a + wy * b;
   } else {
-    const R wz = ((const R*)F.w[2])[q.k];
-    const int k0 = F.c0[2][q.k], k1 = F.c1[2][q.k];
-    const long long p0 = (long long)cnx * ((long long)cny * k0), p1 = (long long)cnx * ((long long)cny * k1);
-    const R a0 = ((R)1 - wx) * (R)xc[p0 + i0 + (long long)cnx * j0] + wx * (R)xc[p0 + i1 + (long long)cnx * j0];
-    const R b0 = ((R)1 - wx) * (R)xc[p0 + i0 + (long long)cnx * j1] + wx * (R)xc[p0 + i1 + (long long)cnx * j1];
-    const R a1 = ((R)1 - wx) * (R)xc[p1 + i0 + (long long)cnx * j0] + wx * (R)xc[p1 + i1 + (long long)cnx * j0];
-    const R b1 = ((R)1 - wx) * (R)xc[p1 + i0 + (long long)cnx * j1] + wx * (R)xc[p1 + i1 + (long long)cnx * j1];
+    const R wz = __ldg((const R*)F.w[2] + k);
+    const int k0 = __ldg(F.c0[2] + k), k1 = __ldg(F.c1[2] + k);
+    const R* r00 = xc + (coff + C.px * j0 + cpl * k0);
+    const R* r10 = xc + (coff + C.px * j1 + cpl * k0);
+    const R* r01 = xc + (coff + C.px * j0 + cpl * k1);
+    const R* r11 = xc + (coff + C.px * j1 + cpl * k1);
+    const R a0 = ((R)1 - wx) * r00[i0] + wx * r00[i1];
+    const R b0 = ((R)1 - wx) * r10[i0] + wx * r10[i1];
+    const R a1 = ((R)1 - wx) * r01[i0] + wx * r01[i1];
+    const R b1 = ((R)1 - wx) * r11[i0] + wx * r11[i1];
     return ((R)1 - wz) * (((R)1 - wy) * a0 + wy * b0) + wz * (((R)1 - wy) * a1 + wy * b1);
   }
 }
@@ -219,227 +289,283 @@ __device__ __forceinline__ R prolong_value(const DevLevel& F, const DevLevel& Cc
 // ===========================================================================
 // Single-CTA solver
 // ===========================================================================
-struct BlkShared {
-  double red[33];
-};
 
-// One red-black half-sweep of the level (all threads of the CTA).  With
-// `zero`, the iterate starts from x = 0: cells of `colour` get rhs/D and the
-// other colour is cleared.
-template <int DIM, typename RP, typename RB>
-__device__ void b_sweep(const DevLevel& L, int colour, const RB* rhs, RP* z, bool zero) {
-  const RP *Tx = (const RP*)L.T[0], *Ty = (const RP*)L.T[1], *Tz = (const RP*)L.T[2];
-  if (zero) {
-    for (long long c = threadIdx.x; c < L.n; c += blockDim.x) {
-      Cell q = cell_of(c, L.nx, L.ny);
-      z[c] = ((q.i + q.j + q.k) & 1) == colour ? (RP)rhs[c] / diag_of<DIM, RP>(L, Tx, Ty, Tz, q) : (RP)0;
-    }
-  } else {
-    const long long np = (long long)((L.nx + 1) >> 1) * L.ny * L.nz;
-    for (long long p = threadIdx.x; p < np; p += blockDim.x) {
-      Cell q;
-      if (colour_cell(p, colour, L.nx, L.ny, q)) z[q.c] = gs_value<DIM, RP, RB>(L, Tx, Ty, Tz, rhs, z, q);
-    }
-  }
-  __syncthreads();
-}
+// One red-black half-sweep of colour `colour` by the CTA, with right-hand
+// side rp (smoother precision).  Modes:
+//  kZero: the iterate starts from x = 0: cells of `colour` get rhs/D, the
+//         other colour is cleared; when the level's vectors are wider than
+//         the smoother type, r is first rounded into rp at every cell.
+//  kNormal: Gauss-Seidel update of the colour's cells.
+//  kDot: as kNormal, and returns this thread's share of r . z over all cells
+//        (r in the level's vector type; the other colour is final already).
+enum : int { kNormal = 0, kZero = 1, kDot = 2 };
 
-// m symmetric Gauss-Seidel steps in red-black order (eq. 2.10's (P^-1 Q)^m
-// terms): forward red, black, backward black, red; the repeated black sweep
-// reproduces the same values, so m steps are the 2m+1 half-sweeps
-// red (black red)^m.
-template <int DIM, typename RP, typename RB>
-__device__ void b_smooth(const DevLevel& L, int m, const RB* rhs, RP* z, bool from_zero) {
-  b_sweep<DIM, RP, RB>(L, 0, rhs, z, from_zero);
-  for (int s = 0; s < m; ++s) {
-    b_sweep<DIM, RP, RB>(L, 1, rhs, z, false);
-    b_sweep<DIM, RP, RB>(L, 0, rhs, z, false);
-  }
-}
-
-// t = r - A z, then r_{k+1} = R t.
 template <int DIM, typename RP, typename V>
-__device__ void b_residual_restrict(const DevLevel& L, const DevLevel& C, const V* r, const RP* z, RP* t, RP* rc) {
+__device__ __forceinline__ V t_sweep(const DevLevel& L, int colour, const V* r, RP* rp, RP* z, int mode) {
   const RP *Tx = (const RP*)L.T[0], *Ty = (const RP*)L.T[1], *Tz = (const RP*)L.T[2];
-  for (long long c = threadIdx.x; c < L.n; c += blockDim.x) {
-    Cell q = cell_of(c, L.nx, L.ny);
-    t[c] = (RP)r[c] - apply_value<DIM, RP, RP>(L, Tx, Ty, Tz, z, q);
-  }
-  __syncthreads();
-  for (long long c = threadIdx.x; c < C.n; c += blockDim.x) {
-    Cell q = cell_of(c, C.nx, C.ny);
-    rc[c] = restrict_value<DIM, RP>(L, t, q.i, q.j, q.k);
-  }
-  __syncthreads();
-}
-
-template <int DIM, typename RP>
-__device__ void b_prolong(const DevLevel& L, const DevLevel& C, const RP* xc, RP* z) {
-  for (long long c = threadIdx.x; c < L.n; c += blockDim.x) {
-    Cell q = cell_of(c, L.nx, L.ny);
-    z[c] += prolong_value<DIM, RP, RP>(L, C, xc, q);
-  }
-  __syncthreads();
-}
-
-template <typename V>
-__device__ double b_zero_dot(V* x, const V* r, long long n, double* sh) {
   V acc = 0;
-  for (long long c = threadIdx.x; c < n; c += blockDim.x) {
-    x[c] = 0;
-    acc += r[c] * r[c];
+  if (mode == kZero) {
+    for_cells<DIM>(team_map(L.nx), L, [&](int i, const Row& rw) {
+      const int pc = rw.pc + i;
+      RP rhs;
+      if (sizeof(V) != sizeof(RP)) {
+        rhs = (RP)r[pc];
+        rp[pc] = rhs;
+      } else {
+        rhs = rp[pc];
+      }
+      z[pc] = ((i + rw.j + rw.k) & 1) == colour ? quot<RP>(rhs, diag_of<DIM, RP>(L, Tx, Ty, Tz, i, rw)) : (RP)0;
+    });
+  } else {
+    const bool dot = mode == kDot;
+    for_colour<DIM>(team_map((L.nx + 1) >> 1), L, colour, [&](int i, int i2, const Row& rw) {
+      const int base = rw.pc;
+      if (i < L.nx) {
+        const RP v = gs_value<DIM, RP, RP>(L, Tx, Ty, Tz, rp[base + i], z, i, rw);
+        z[base + i] = v;
+        if (dot) acc += r[base + i] * (V)v;
+      }
+      if (dot && i2 < L.nx) acc += r[base + i2] * (V)z[base + i2];
+    });
   }
-  return block_sum((double)acc, sh);
+  return acc;
 }
 
-template <typename V, typename RP>
-__device__ double b_dot(const V* a, const RP* b, long long n, double* sh) {
-  V acc = 0;
-  for (long long c = threadIdx.x; c < n; c += blockDim.x) acc += a[c] * (V)b[c];
-  return block_sum((double)acc, sh);
-}
-
-template <typename V, typename RP>
-__device__ void b_direction(V* p, const RP* z, long long n, bool first, V beta) {
-  for (long long c = threadIdx.x; c < n; c += blockDim.x) p[c] = first ? (V)z[c] : (V)z[c] + beta * p[c];
-  __syncthreads();
-}
-
-template <int DIM, typename V>
-__device__ double b_apply_dot(const DevLevel& L, const V* p, V* q, double* sh) {
-  const V *Tx = Tvec<V>(L, 0), *Ty = Tvec<V>(L, 1), *Tz = DIM == 3 ? Tvec<V>(L, 2) : nullptr;
-  V acc = 0;
-  for (long long c = threadIdx.x; c < L.n; c += blockDim.x) {
-    Cell cq = cell_of(c, L.nx, L.ny);
-    V v = apply_value<DIM, V, V>(L, Tx, Ty, Tz, p, cq);
-    q[c] = v;
-    acc += p[c] * v;
+// m symmetric Gauss-Seidel steps (the smoothing factors of eq. 2.10):
+// forward red, black, backward black, red; the repeated black half-sweep
+// reproduces the same values, so m steps are the 2m+1 half-sweeps
+// red (black red)^m.  Returns r . z after the last half-sweep when `dot`.
+template <int DIM, typename RP, typename V>
+__device__ V t_smooth(BlockTeam& tm, const DevLevel& L, int m, bool from_zero, bool dot) {
+  const V* r = (const V*)L.r;
+  RP* rp = (RP*)L.rp;
+  RP* z = (RP*)L.z;
+  t_sweep<DIM, RP, V>(L, 0, r, rp, z, from_zero ? kZero : kNormal);
+  tm.sync();
+  for (int s = 0; s < m; ++s) {
+    t_sweep<DIM, RP, V>(L, 1, r, rp, z, kNormal);
+    tm.sync();
+    const bool last = s == m - 1;
+    const V d = t_sweep<DIM, RP, V>(L, 0, r, rp, z, dot && last ? kDot : kNormal);
+    if (dot && last) return tm.sum<V>(d);
+    tm.sync();
   }
-  return block_sum((double)acc, sh);
+  return (V)0;
 }
 
-template <typename V>
-__device__ double b_update(V* x, V* r, const V* p, const V* q, long long n, V alpha, double* sh) {
-  V acc = 0;
-  for (long long c = threadIdx.x; c < n; c += blockDim.x) {
-    x[c] += alpha * p[c];
-    V rv = r[c] - alpha * q[c];
-    r[c] = rv;
-    acc += rv * rv;
-  }
-  return block_sum((double)acc, sh);
-}
-
-// Coarsest level: z = A^-1 r with the FP64 explicit inverse (Sec. 2.2, the
-// recursion ends with the exact inverse).
-template <typename V, typename RP>
-__device__ void b_coarsest(const double* Ainv, int nc, const V* r, RP* z) {
-  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+// Coarsest level: z = A^-1 r with the FP64 explicit inverse (the recursion
+// ends with the exact inverse, Sec. 2.2).  rc: compact shared scratch.
+template <int DIM, typename V, typename RP>
+__device__ void t_coarsest(BlockTeam& tm, const DevLevel& L, const double* Ainv, int nc, const V* r, RP* z, double* rc) {
+  for_cells<DIM>(team_map(L.nx), L, [&](int i, const Row& rw) {
+    rc[i + L.nx * (rw.j + L.ny * rw.k)] = (double)r[rw.pc + i];
+  });
+  tm.sync();
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) {
     double s = 0.0;
-    const double* row = Ainv + (long long)i * nc;
-    for (int j = 0; j < nc; ++j) s += row[j] * (double)r[j];
-    z[i] = (RP)s;
+    const double* row = Ainv + (long long)c * nc;
+    for (int j = 0; j < nc; ++j) s += __ldg(row + j) * rc[j];
+    const int i = c % L.nx, rw = c / L.nx, jj = rw % L.ny, kk = rw / L.ny;
+    z[(int)L.off + i + L.px * jj + (int)L.plane * kk] = (RP)s;
   }
-  __syncthreads();
+  tm.sync();
 }
 
-// Per-level control of the single-CTA state machine.
+// Control of one level of the single-CTA state machine.  Scalars are kept
+// in both precisions so that an FP32 level never converts.
 struct LvlCtl {
-  double rho_old, thr, rho;
+  double rho_d, rho_old_d, thrN_d;
+  float rho_f, rho_old_f, thrN_f;
   int it, phase;
 };
 enum : int { kStart = 0, kIterate = 1, kAfterCoarse = 2, kPrecondDone = 3, kReturn = 4 };
 
-// Ops of one level with its vector type V (double at level 0 of a full
-// solve, the smoother type RP elsewhere).
-template <int DIM, typename V, typename RP>
-struct LevelOps {
-  // PCG entry: x = 0, r holds b_k; returns ||b_k||^2
-  static __device__ double enter(const DevLevel& L, double* sh) { return b_zero_dot<V>((V*)L.x, (const V*)L.r, L.n, sh); }
-  static __device__ void presmooth_restrict(const DevLevel& L, const DevLevel& C, int m) {
-    b_smooth<DIM, RP, V>(L, m, (const V*)L.r, (RP*)L.z, true);
-    b_residual_restrict<DIM, RP, V>(L, C, (const V*)L.r, (const RP*)L.z, (RP*)L.t, (RP*)C.r);
-  }
-  static __device__ void coarsest(const DevLevel& L, const double* Ainv, int nc) {
-    b_coarsest<V, RP>(Ainv, nc, (const V*)L.r, (RP*)L.z);
-  }
-  static __device__ void postsmooth(const DevLevel& L, int m) { b_smooth<DIM, RP, V>(L, m, (const V*)L.r, (RP*)L.z, false); }
-  // rho = r.z, p = z + beta p, q = A p, alpha, x += alpha p, r -= alpha q.
-  // Returns ||r||^2, or -1 on breakdown.
-  static __device__ double cg_step(const DevLevel& L, LvlCtl& ct, double* sh) {
-    const double rho = b_dot<V, RP>((const V*)L.r, (const RP*)L.z, L.n, sh);
-    const bool first = ct.it == 0;
-    b_direction<V, RP>((V*)L.p, (const RP*)L.z, L.n, first, first ? (V)0 : (V)(rho / ct.rho_old));
-    const double pq = b_apply_dot<DIM, V>(L, (const V*)L.p, (V*)L.q, sh);
-    if (!(pq > 0.0) || !isfinite(pq) || !isfinite(rho)) return -1.0;
-    const V alpha = (V)(rho / pq);
-    ct.rho = rho;
-    return b_update<V>((V*)L.x, (V*)L.r, (const V*)L.p, (const V*)L.q, L.n, alpha, sh);
+template <typename V>
+struct Scal;
+template <>
+struct Scal<double> {
+  static __device__ __forceinline__ double& rho(LvlCtl& c) { return c.rho_d; }
+  static __device__ __forceinline__ double& rho_old(LvlCtl& c) { return c.rho_old_d; }
+  // the level test ||r||^2 / N_k < thr, as ||r||^2 < thr N_k
+  static __device__ __forceinline__ bool below(const LvlCtl& c, double rr) { return rr < c.thrN_d; }
+};
+template <>
+struct Scal<float> {
+  static __device__ __forceinline__ float& rho(LvlCtl& c) { return c.rho_f; }
+  static __device__ __forceinline__ float& rho_old(LvlCtl& c) { return c.rho_old_f; }
+  static __device__ __forceinline__ bool below(const LvlCtl& c, float rr) {
+    // thr N_k below the normal FP32 range: decide in FP64
+    return c.thrN_f > 1e-30f ? rr < c.thrN_f : (double)rr < c.thrN_d;
   }
 };
 
-// The recursion of eq. (2.10) from level ks down to kmax, run by one CTA.
-// On entry level ks's r holds its right-hand side; on exit its x holds the
-// PCG result.  sL: the levels in shared memory.  top_double: level 0 (if ks
-// is 0) keeps FP64 vectors while the preconditioner runs in RP.
+struct RecArgs {
+  int kmax, m, nc;
+  const double* Ainv;
+  double eps2, floor2;
+  SolveState* S;
+  bool top_double;  // level 0 keeps FP64 vectors
+  double* rc;       // shared scratch of the coarsest solve
+};
+
+// Steps of one level with vector type V (double at level 0 of a full solve,
+// the smoother type RP elsewhere).
+template <int DIM, typename V, typename RP>
+struct Ops {
+  // PCG entry (x = 0; r holds b_k): ||b_k||^2
+  static __device__ V enter(BlockTeam& tm, const DevLevel& L) {
+    V* x = (V*)L.x;
+    const V* r = (const V*)L.r;
+    V acc = 0;
+    for (int c = threadIdx.x; c < (int)L.npad; c += blockDim.x) {
+      x[c] = 0;
+      acc += r[c] * r[c];
+    }
+    return tm.sum<V>(acc);
+  }
+  // pre-smoothing from zero, t = r - A z, r_{k+1} = R t
+  static __device__ void presmooth_restrict(BlockTeam& tm, const DevLevel& L, const DevLevel& C, int m) {
+    t_smooth<DIM, RP, V>(tm, L, m, true, false);
+    const RP* rp = (const RP*)L.rp;
+    const RP* z = (const RP*)L.z;
+    RP* t = (RP*)L.t;
+    const RP *Tx = (const RP*)L.T[0], *Ty = (const RP*)L.T[1], *Tz = (const RP*)L.T[2];
+    for_cells<DIM>(team_map(L.nx), L, [&](int i, const Row& rw) {
+      t[rw.pc + i] = rp[rw.pc + i] - apply_value<DIM, RP, RP>(L, Tx, Ty, Tz, z, i, rw);
+    });
+    tm.sync();
+    RP* rc = (RP*)C.r;
+    for_cells<DIM>(team_map(C.nx), C, [&](int i, const Row& rw) {
+      rc[rw.pc + i] = restrict_value<DIM, RP>(L, t, i, rw.j, rw.k);
+    });
+    tm.sync();
+  }
+  // z += E x_c on the black cells only: the first post-smoothing half-sweep
+  // recomputes every red cell from its black neighbours, so a red cell's
+  // prolonged value would never be read.  Then post-smoothing; returns r.z.
+  static __device__ V prolong_postsmooth(BlockTeam& tm, const DevLevel& L, const DevLevel& C, int m) {
+    RP* z = (RP*)L.z;
+    const RP* xc = (const RP*)C.x;
+    for_colour<DIM>(team_map((L.nx + 1) >> 1), L, 1, [&](int i, int, const Row& rw) {
+      if (i < L.nx) z[rw.pc + i] += prolong_value<DIM, RP>(L, C, xc, i, rw.j, rw.k);
+    });
+    tm.sync();
+    return t_smooth<DIM, RP, V>(tm, L, m, false, true);
+  }
+  static __device__ V coarsest(BlockTeam& tm, const DevLevel& L, const RecArgs& a) {
+    t_coarsest<DIM, V, RP>(tm, L, a.Ainv, a.nc, (const V*)L.r, (RP*)L.z, a.rc);
+    const V* r = (const V*)L.r;
+    const RP* z = (const RP*)L.z;
+    V acc = 0;
+    for (int c = threadIdx.x; c < (int)L.npad; c += blockDim.x) acc += r[c] * (V)z[c];
+    return tm.sum<V>(acc);
+  }
+  // p = z + beta p, q = A p, alpha = rho / p.q, x += alpha p, r -= alpha q.
+  // Returns ||r||^2 (false on breakdown).
+  static __device__ bool cg_step(BlockTeam& tm, const DevLevel& L, LvlCtl& ct, V& rr_out) {
+    const V rho = Scal<V>::rho(ct);
+    const bool first = ct.it == 0;
+    const V beta = first ? (V)0 : rho / Scal<V>::rho_old(ct);
+    V* p = (V*)L.p;
+    V* q = (V*)L.q;
+    const RP* z = (const RP*)L.z;
+    for (int c = threadIdx.x; c < (int)L.npad; c += blockDim.x) p[c] = first ? (V)z[c] : (V)z[c] + beta * p[c];
+    tm.sync();
+    const V *Tx = Tvec<V>(L, 0), *Ty = Tvec<V>(L, 1), *Tz = DIM == 3 ? Tvec<V>(L, 2) : nullptr;
+    V acc = 0;
+    for_cells<DIM>(team_map(L.nx), L, [&](int i, const Row& rw) {
+      const V v = apply_value<DIM, V, V>(L, Tx, Ty, Tz, p, i, rw);
+      q[rw.pc + i] = v;
+      acc += p[rw.pc + i] * v;
+    });
+    const V pq = tm.sum<V>(acc);
+    if (!(pq > (V)0) || !isfinite(pq) || !isfinite(rho)) return false;
+    const V alpha = rho / pq;
+    V* x = (V*)L.x;
+    V* r = (V*)L.r;
+    V acc2 = 0;
+    for (int c = threadIdx.x; c < (int)L.npad; c += blockDim.x) {
+      x[c] += alpha * p[c];
+      const V rv = r[c] - alpha * q[c];
+      r[c] = rv;
+      acc2 += rv * rv;
+    }
+    rr_out = tm.sum<V>(acc2);
+    return true;
+  }
+  // one CG step and the level test; returns 0 = continue, 1 = converged,
+  // 2 = breakdown
+  static __device__ int iterate(BlockTeam& tm, const DevLevel& L, LvlCtl& c, SolveState* S, int k) {
+    V rr;
+    if (!cg_step(tm, L, c, rr)) return 2;
+    if (threadIdx.x == 0) {
+      S->lv[k].iters++;
+      if (k == 0) S->lv[0].rr = (double)rr;
+    }
+    return Scal<V>::below(c, rr) ? 1 : 0;
+  }
+};
+
+// The recursion of eq. (2.10) from level ks down to kmax, run by the CTA.
+// On entry r_ks holds the level's right-hand side; on exit x_ks holds the
+// PCG result.
 template <int DIM, typename RP>
-__device__ void small_recursion(const DevLevel* sL, int ks, int kmax, int m, const double* Ainv, int nc, double eps2,
-                                double floor2, SolveState* S, double* sh) {
+__device__ void recursion(BlockTeam& tm, const DevLevel* sL, int ks, const RecArgs& a) {
   LvlCtl ct[kMaxLev];
   int k = ks;
   ct[k].phase = kStart;
-  const bool top_double = ks == 0;
+  SolveState* S = a.S;
   for (;;) {
     const DevLevel& L = sL[k];
     LvlCtl& c = ct[k];
-    const bool dbl = top_double && k == 0;
+    const bool dbl = a.top_double && k == 0;
     if (c.phase == kStart) {
       if (threadIdx.x == 0) S->lv[k].calls++;
-      const double bb = dbl ? LevelOps<DIM, double, RP>::enter(L, sh) : LevelOps<DIM, RP, RP>::enter(L, sh);
-      if (bb == 0.0) {
+      const double bb = dbl ? (double)Ops<DIM, double, RP>::enter(tm, L) : (double)Ops<DIM, RP, RP>::enter(tm, L);
+      if (!(bb > 0.0)) {
         c.phase = kReturn;
         continue;
       }
-      double thr = L.fk * eps2;
-      if (k > 0 && floor2 > 0.0) thr = fmax(thr, floor2 * bb / (double)L.n);
-      c.thr = thr;
+      // level test of Sec. 3: ||r||^2 / N_k < f^k eps^2 (inner levels may
+      // also stop at a floor relative to ||b_k||)
+      double thr = L.fk * a.eps2;
+      if (k > 0 && a.floor2 > 0.0) thr = fmax(thr, a.floor2 * bb / (double)L.n);
+      c.thrN_d = thr * (double)L.n;
+      c.thrN_f = (float)c.thrN_d;
       c.it = 0;
-      c.rho_old = 0.0;
+      c.rho_old_d = 0.0;
+      c.rho_old_f = 0.f;
       c.phase = kIterate;
     } else if (c.phase == kIterate) {
-      if (k == kmax) {
-        if (dbl) LevelOps<DIM, double, RP>::coarsest(L, Ainv, nc);
-        else LevelOps<DIM, RP, RP>::coarsest(L, Ainv, nc);
+      if (k == a.kmax) {
+        if (dbl) c.rho_d = Ops<DIM, double, RP>::coarsest(tm, L, a);
+        else Scal<RP>::rho(c) = Ops<DIM, RP, RP>::coarsest(tm, L, a);
         c.phase = kPrecondDone;
       } else {
-        if (dbl) LevelOps<DIM, double, RP>::presmooth_restrict(L, sL[k + 1], m);
-        else LevelOps<DIM, RP, RP>::presmooth_restrict(L, sL[k + 1], m);
+        if (dbl) Ops<DIM, double, RP>::presmooth_restrict(tm, L, sL[k + 1], a.m);
+        else Ops<DIM, RP, RP>::presmooth_restrict(tm, L, sL[k + 1], a.m);
         c.phase = kAfterCoarse;
         ++k;
         ct[k].phase = kStart;
       }
     } else if (c.phase == kAfterCoarse) {
-      b_prolong<DIM, RP>(L, sL[k + 1], (const RP*)sL[k + 1].x, (RP*)L.z);
-      if (dbl) LevelOps<DIM, double, RP>::postsmooth(L, m);
-      else LevelOps<DIM, RP, RP>::postsmooth(L, m);
+      if (dbl) c.rho_d = Ops<DIM, double, RP>::prolong_postsmooth(tm, L, sL[k + 1], a.m);
+      else Scal<RP>::rho(c) = Ops<DIM, RP, RP>::prolong_postsmooth(tm, L, sL[k + 1], a.m);
       c.phase = kPrecondDone;
     } else if (c.phase == kPrecondDone) {
-      const double rr = dbl ? LevelOps<DIM, double, RP>::cg_step(L, c, sh) : LevelOps<DIM, RP, RP>::cg_step(L, c, sh);
-      if (rr < 0.0) {
+      const int st = dbl ? Ops<DIM, double, RP>::iterate(tm, L, c, S, k) : Ops<DIM, RP, RP>::iterate(tm, L, c, S, k);
+      c.it++;
+      if (st == 2) {
         if (threadIdx.x == 0) atomicOr(&S->status, kStBreakdown);
         c.phase = kReturn;
-        continue;
-      }
-      if (threadIdx.x == 0) S->lv[k].iters++;
-      c.it++;
-      if (k == 0 && threadIdx.x == 0) S->lv[0].rr = rr;
-      if (rr / (double)L.n < c.thr) {
+      } else if (st == 1) {
         c.phase = kReturn;
       } else if (c.it >= L.maxit) {
         if (threadIdx.x == 0) atomicOr(&S->status, kStNoConv);
         c.phase = kReturn;
       } else {
-        c.rho_old = c.rho;
+        c.rho_old_d = c.rho_d;
+        c.rho_old_f = c.rho_f;
         c.phase = kIterate;
       }
     } else {  // kReturn
@@ -447,24 +573,112 @@ __device__ void small_recursion(const DevLevel* sL, int ks, int kmax, int m, con
       --k;
     }
   }
+  tm.sync();
+}
+
+__host__ __device__ __forceinline__ size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+// Shared-memory bytes of level L's arrays when it runs from shared memory:
+// x, r, p, q in the level's vector type, z in RP, the residual t and the
+// rounded right-hand side rp in RP (t shares q's and rp shares r's storage
+// when the types agree), the face transmissibilities.
+__host__ __device__ __forceinline__ size_t level_smem_bytes(const DevLevel& L, size_t vsz, size_t rsz, int dim) {
+  const long long n = L.npad;
+  size_t b = 4 * align16(n * vsz) + align16(n * rsz);
+  if (vsz != rsz) b += 2 * align16(n * rsz);
+  b += align16((size_t)(L.nx + 1) * L.ny * L.nz * rsz) + align16((size_t)L.nx * (L.ny + 1) * L.nz * rsz);
+  if (dim == 3) b += align16((size_t)L.nx * L.ny * (L.nz + 1) * rsz);
+  return b;
+}
+
+// Place levels lo..kmax that fit (from the coarsest up) in the dynamic shared
+// memory: rewrite their pointers in sL, zero their vectors (ghosts included)
+// and copy their transmissibilities.  Returns the first level placed.
+template <int DIM, typename RP>
+__device__ int place_levels(DevLevel* sL, const DevLevel* gL, int lo, int kmax, bool top_double, unsigned char* dsm,
+                            size_t budget) {
+  __shared__ int s_ksm;
+  __shared__ size_t s_vec_bytes;
+  if (threadIdx.x == 0) {
+    size_t off = 0;
+    int ksm = kmax + 1;
+    for (int k = kmax; k >= lo; --k) {
+      const size_t vsz = (top_double && k == 0) ? sizeof(double) : sizeof(RP);
+      const size_t need = level_smem_bytes(sL[k], vsz, sizeof(RP), DIM);
+      if (off + need > budget) break;
+      off += need;
+      ksm = k;
+    }
+    off = 0;
+    // vectors of all placed levels first (one contiguous block to zero)
+    for (int k = ksm; k <= kmax; ++k) {
+      DevLevel& L = sL[k];
+      const size_t vsz = (top_double && k == 0) ? sizeof(double) : sizeof(RP);
+      void** vec[4] = {&L.x, &L.r, &L.p, &L.q};
+      for (int v = 0; v < 4; ++v) {
+        *vec[v] = dsm + off;
+        off += align16(L.npad * vsz);
+      }
+      L.z = dsm + off;
+      off += align16(L.npad * sizeof(RP));
+      if (vsz != sizeof(RP)) {
+        L.t = dsm + off;
+        off += align16(L.npad * sizeof(RP));
+        L.rp = dsm + off;
+        off += align16(L.npad * sizeof(RP));
+      } else {
+        L.t = L.q;
+        L.rp = L.r;
+      }
+    }
+    s_vec_bytes = off;
+    for (int k = ksm; k <= kmax; ++k) {
+      DevLevel& L = sL[k];
+      for (int ax = 0; ax < DIM; ++ax) {
+        const size_t nf = (size_t)(L.nx + (ax == 0)) * (L.ny + (ax == 1)) * (L.nz + (ax == 2));
+        L.T[ax] = dsm + off;
+        if (sizeof(RP) == sizeof(double)) L.T64[ax] = (const double*)(dsm + off);
+        off += align16(nf * sizeof(RP));
+      }
+    }
+    s_ksm = ksm;
+  }
   __syncthreads();
+  const int ksm = s_ksm;
+  for (size_t e = threadIdx.x; e < s_vec_bytes / 16; e += blockDim.x) ((float4*)dsm)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int k = ksm; k <= kmax; ++k) {
+    for (int ax = 0; ax < DIM; ++ax) {
+      const DevLevel& L = sL[k];
+      const size_t nf = (size_t)(L.nx + (ax == 0)) * (L.ny + (ax == 1)) * (L.nz + (ax == 2));
+      const RP* src = (const RP*)gL[k].T[ax];
+      RP* dst = (RP*)L.T[ax];
+      for (size_t e = threadIdx.x; e < nf; e += blockDim.x) dst[e] = __ldg(src + e);
+    }
+  }
+  __syncthreads();
+  return ksm;
 }
 
 // Single-CTA kernel.
-//  mode 0: solve levels ks..kmax of problem P[0]; its r_ks already holds b_ks
-//          and eps^2 comes from the problem's state (the wide levels set it).
+//  mode 0: solve levels ks..kmax of problem P[0]; its r_ks (global) holds
+//          b_ks and eps^2 comes from the problem state (set for the wide
+//          levels); x_ks is written back to global memory.
 //  mode 1: full solves of problems P[order[i]]; CTAs take the next problem
-//          index from *next (problems are sorted largest first).
+//          index from *next (problems sorted largest first).
 //  mode 2: full solve of problem P[0] by CTA 0.
-// A full solve copies b into r_0, computes eps^2 = tol^2 ||b||^2 / N_0, runs
-// the recursion from level 0 with FP64 level-0 vectors, adds the result to
-// x, forms the true residual b - A x in FP64 and, if that misses tol, runs
-// the recursion again on it (at most 3 restarts).
+// A full solve copies b into r_0, sets eps^2 = tol^2 ||b||^2 / N_0 (Sec. 3),
+// runs the recursion from level 0 with FP64 level-0 vectors, adds the result
+// to xs, forms the true residual b - A xs in FP64 and, if that misses tol,
+// runs the recursion again on it (at most 3 restarts); x = xs at the end.
 template <int DIM, typename RP>
-__global__ void __launch_bounds__(kSmallThreads) k_small(const ProblemDesc* __restrict__ P, const int* __restrict__ order,
-                                                         int nprob, int ks, int mode, int* next) {
+__global__ void __launch_bounds__(kSmallThreads, 1) k_small(const ProblemDesc* __restrict__ P,
+                                                            const int* __restrict__ order, int nprob, int ks, int mode,
+                                                            int* next, size_t smem_budget) {
+  extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ DevLevel sL[kMaxLev];
-  __shared__ double sh[33];
+  __shared__ double shd[64];
+  __shared__ float shf[64];
+  __shared__ double s_rc[kMaxCoarse];
   __shared__ int s_pid;
   for (int round = 0;; ++round) {
     if (threadIdx.x == 0) s_pid = mode == 1 ? atomicAdd(next, 1) : (round == 0 && blockIdx.x == 0 ? 0 : nprob);
@@ -478,21 +692,52 @@ __global__ void __launch_bounds__(kSmallThreads) k_small(const ProblemDesc* __re
     __syncthreads();
     SolveState* S = pd.S;
     const int kmax = pd.nlev - 1;
-    if (mode == 0) {
-      small_recursion<DIM, RP>(sL, ks, kmax, pd.m, pd.Ainv, pd.nc, S->eps2, S->inner_floor2, S, sh);
+    const bool full = mode != 0;
+    const int lo = full ? 0 : ks;
+    place_levels<DIM, RP>(sL, pd.L, lo, kmax, full, dsm, smem_budget);
+    RecArgs a;
+    a.kmax = kmax;
+    a.m = pd.m;
+    a.nc = pd.nc;
+    a.Ainv = pd.Ainv;
+    a.floor2 = S->inner_floor2;
+    a.S = S;
+    a.top_double = full;
+    a.rc = s_rc;
+    BlockTeam bt;
+    bt.shd = shd;
+    bt.shf = shf;
+    bt.par = 0;
+    if (!full) {
+      // level ks's right-hand side into its (shared-memory) r
+      const DevLevel& G = pd.L[ks];
+      const RP* gr = (const RP*)G.r;
+      RP* sr = (RP*)sL[ks].r;
+      if (sr != gr)
+        for (int c = threadIdx.x; c < (int)G.npad; c += blockDim.x) sr[c] = gr[c];
+      __syncthreads();
+      a.eps2 = S->eps2;
+      recursion<DIM, RP>(bt, sL, ks, a);
+      RP* gx = (RP*)G.x;
+      const RP* sx = (const RP*)sL[ks].x;
+      if (sx != gx)
+        for (int c = threadIdx.x; c < (int)G.npad; c += blockDim.x) gx[c] = sx[c];
+      __syncthreads();
       continue;
     }
     const DevLevel& L0 = sL[0];
+    const DevLevel& G0 = pd.L[0];
     double* r0 = (double*)L0.r;
-    double* x0 = (double*)L0.x;
+    const double* x0 = (const double*)L0.x;
+    double* xs = pd.xs;
     double bbl = 0.0;
-    for (long long c = threadIdx.x; c < L0.n; c += blockDim.x) {
-      const double v = pd.b[c];
-      r0[c] = v;
-      pd.x[c] = 0.0;
+    for_cells<DIM>(team_map(L0.nx), L0, [&](int i, const Row& rw) {
+      const double v = pd.b[i + L0.nx * (rw.j + L0.ny * rw.k)];
+      r0[rw.pc + i] = v;
       bbl += v * v;
-    }
-    const double bb = block_sum(bbl, sh);
+    });
+    for (int c = threadIdx.x; c < (int)L0.npad; c += blockDim.x) xs[c] = 0.0;
+    const double bb = bt.sum<double>(bbl);
     const double eps2 = pd.tol * pd.tol * (bb / (double)L0.n);
     if (threadIdx.x == 0) {
       S->bb0 = bb;
@@ -508,25 +753,30 @@ __global__ void __launch_bounds__(kSmallThreads) k_small(const ProblemDesc* __re
       S->rr_true = bb;
     }
     __syncthreads();
-    if (!(bb > 0.0) || !isfinite(bb)) continue;
-    const double floor2 = S->inner_floor2;
-    for (int pass = 0; pass < 4; ++pass) {
-      small_recursion<DIM, RP>(sL, 0, kmax, pd.m, pd.Ainv, pd.nc, eps2, floor2, S, sh);
-      for (long long c = threadIdx.x; c < L0.n; c += blockDim.x) pd.x[c] += x0[c];
-      __syncthreads();
-      double rl = 0.0;
-      for (long long c = threadIdx.x; c < L0.n; c += blockDim.x) {
-        Cell q = cell_of(c, L0.nx, L0.ny);
-        const double v =
-            pd.b[c] - apply_value<DIM, double, double>(L0, L0.T64[0], L0.T64[1], DIM == 3 ? L0.T64[2] : nullptr, pd.x, q);
-        r0[c] = v;
-        rl += v * v;
+    a.eps2 = eps2;
+    if (bb > 0.0 && isfinite(bb)) {
+      for (int pass = 0; pass < 4; ++pass) {
+        recursion<DIM, RP>(bt, sL, 0, a);
+        for (int c = threadIdx.x; c < (int)L0.npad; c += blockDim.x) xs[c] += x0[c];
+        __syncthreads();
+        double rl = 0.0;
+        for_cells<DIM>(team_map(L0.nx), L0, [&](int i, const Row& rw) {
+          const double v = pd.b[i + L0.nx * (rw.j + L0.ny * rw.k)] -
+                           apply_value<DIM, double, double>(G0, G0.T64[0], G0.T64[1], DIM == 3 ? G0.T64[2] : nullptr, xs,
+                                                            i, rw);
+          r0[rw.pc + i] = v;
+          rl += v * v;
+        });
+        const double rt = bt.sum<double>(rl);
+        if (threadIdx.x == 0) S->rr_true = rt;
+        __syncthreads();
+        if (S->status != 0 || rt < pd.tol * pd.tol * bb) break;
       }
-      const double rt = block_sum(rl, sh);
-      if (threadIdx.x == 0) S->rr_true = rt;
-      __syncthreads();
-      if (S->status != 0 || rt < pd.tol * pd.tol * bb) break;
     }
+    for_cells<DIM>(team_map(L0.nx), L0, [&](int i, const Row& rw) {
+      pd.x[i + L0.nx * (rw.j + L0.ny * rw.k)] = xs[rw.pc + i];
+    });
+    __syncthreads();
   }
 }
 
@@ -536,45 +786,55 @@ __global__ void __launch_bounds__(kSmallThreads) k_small(const ProblemDesc* __re
 
 // Reduction across the CTAs of one launch: each CTA writes its partial, the
 // last CTA to arrive (ticket) sums the partials in index order and calls fin
-// with the total.  Deterministic for a given grid size.
-template <class Fin>
-__device__ void grid_total(double v, double* partials, unsigned int* ticket, double* sh, Fin fin) {
-  const double bs = block_sum(v, sh);
+// with the total.  Deterministic for a given launch shape.
+template <typename T, class Fin>
+__device__ void grid_total(T v, double* partials, unsigned int* ticket, Fin fin) {
+  __shared__ T sh[32];
   __shared__ bool last;
-  if (threadIdx.x == 0) {
-    partials[blockIdx.x] = bs;
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nt = blockDim.x * blockDim.y;
+  const unsigned nb = gridDim.x * gridDim.y, bid = blockIdx.x + gridDim.x * blockIdx.y;
+  v = warp_sum_t<T>(v);
+  if ((tid & 31) == 0) sh[tid >> 5] = v;
+  __syncthreads();
+  if (tid == 0) {
+    T s = 0;
+    for (int w = 0; w < (nt >> 5); ++w) s += sh[w];
+    partials[bid] = (double)s;
     __threadfence();
     const unsigned t = atomicAdd(ticket, 1u);
-    last = t == gridDim.x - 1;
+    last = t == nb - 1;
   }
   __syncthreads();
-  if (last) {
+  if (last && tid < 32) {
     __threadfence();
     double s = 0.0;
-    if (threadIdx.x < 32) {
-      for (int i = threadIdx.x; i < (int)gridDim.x; i += 32) s += __ldcg(partials + i);
-      s = warp_sum(s);
-      if (threadIdx.x == 0) {
-        *ticket = 0u;
-        fin(s);
-      }
+    for (unsigned i = tid; i < nb; i += 32) s += __ldcg(partials + i);
+    s = warp_sum(s);
+    if (tid == 0) {
+      *ticket = 0u;
+      fin(s);
     }
   }
 }
 
-__device__ __forceinline__ long long gtid() { return blockIdx.x * (long long)blockDim.x + threadIdx.x; }
-__device__ __forceinline__ long long gstride() { return (long long)gridDim.x * blockDim.x; }
+__device__ __forceinline__ long long lin_tid() {
+  return (long long)(blockIdx.x + gridDim.x * blockIdx.y) * (blockDim.x * blockDim.y) + threadIdx.x +
+         blockDim.x * threadIdx.y;
+}
+__device__ __forceinline__ long long lin_stride() {
+  return (long long)gridDim.x * gridDim.y * blockDim.x * blockDim.y;
+}
 
 // PCG entry on a wide level: x = 0 (level 0: r = b0), ||b_k||^2, threshold,
 // counters, and the WHILE condition of the level's loop.
 template <typename V>
-__global__ void __launch_bounds__(kThreads) k_init(DevLevel L, int k, SolveState* S, const double* b0, double* partials,
-                                                   cudaGraphConditionalHandle hcond) {
-  __shared__ double sh[33];
+__global__ void k_init(DevLevel L, int k, SolveState* S, const double* b0, double* partials,
+                       cudaGraphConditionalHandle hcond) {
   V* x = (V*)L.x;
   V* r = (V*)L.r;
   V acc = 0;
-  for (long long c = gtid(); c < L.n; c += gstride()) {
+  for (long long c = lin_tid(); c < L.npad; c += lin_stride()) {
     x[c] = 0;
     V v;
     if (b0) {
@@ -585,7 +845,7 @@ __global__ void __launch_bounds__(kThreads) k_init(DevLevel L, int k, SolveState
     }
     acc += v * v;
   }
-  grid_total((double)acc, partials, &S->ticket[k], sh, [&](double bb) {
+  grid_total(acc, partials, &S->ticket[k], [&](double bb) {
     LevelState& ls = S->lv[k];
     ls.bb = bb;
     double thr = L.fk * S->eps2;
@@ -600,131 +860,177 @@ __global__ void __launch_bounds__(kThreads) k_init(DevLevel L, int k, SolveState
   });
 }
 
-// One red-black half-sweep over a wide level (see b_sweep).
-template <int DIM, typename RP, typename RB>
-__global__ void __launch_bounds__(kThreads) k_sweep(DevLevel L, int colour, int zero) {
+template <typename V>
+__device__ __forceinline__ V beta_of(const LevelState& ls);
+template <>
+__device__ __forceinline__ double beta_of<double>(const LevelState& ls) {
+  return ls.beta;
+}
+template <>
+__device__ __forceinline__ float beta_of<float>(const LevelState& ls) {
+  return ls.beta_f;
+}
+template <typename V>
+__device__ __forceinline__ V alpha_of(const LevelState& ls);
+template <>
+__device__ __forceinline__ double alpha_of<double>(const LevelState& ls) {
+  return ls.alpha;
+}
+template <>
+__device__ __forceinline__ float alpha_of<float>(const LevelState& ls) {
+  return ls.alpha_f;
+}
+
+// One red-black half-sweep over a wide level (see t_sweep).  With `zero`
+// the iterate starts from x = 0 and, when the level's vectors are wider than
+// the smoother type, r is rounded into rp on the way.
+template <int DIM, typename RP, typename V>
+__global__ void k_sweep(DevLevel L, int colour, int zero) {
   const RP *Tx = (const RP*)L.T[0], *Ty = (const RP*)L.T[1], *Tz = (const RP*)L.T[2];
-  const RB* rhs = (const RB*)L.r;
+  const V* r = (const V*)L.r;
+  RP* rp = (RP*)L.rp;
   RP* z = (RP*)L.z;
   if (zero) {
-    for (long long c = gtid(); c < L.n; c += gstride()) {
-      Cell q = cell_of(c, L.nx, L.ny);
-      z[c] = ((q.i + q.j + q.k) & 1) == colour ? (RP)rhs[c] / diag_of<DIM, RP>(L, Tx, Ty, Tz, q) : (RP)0;
-    }
+    for_cells<DIM>(grid_map(), L, [&](int i, const Row& rw) {
+      const int pc = rw.pc + i;
+      RP rhs;
+      if (sizeof(V) != sizeof(RP)) {
+        rhs = (RP)r[pc];
+        rp[pc] = rhs;
+      } else {
+        rhs = rp[pc];
+      }
+      z[pc] = ((i + rw.j + rw.k) & 1) == colour ? quot<RP>(rhs, diag_of<DIM, RP>(L, Tx, Ty, Tz, i, rw)) : (RP)0;
+    });
   } else {
-    const long long np = (long long)((L.nx + 1) >> 1) * L.ny * L.nz;
-    for (long long p = gtid(); p < np; p += gstride()) {
-      Cell q;
-      if (colour_cell(p, colour, L.nx, L.ny, q)) z[q.c] = gs_value<DIM, RP, RB>(L, Tx, Ty, Tz, rhs, z, q);
-    }
+    for_colour<DIM>(grid_map(), L, colour, [&](int i, int, const Row& rw) {
+      if (i < L.nx) z[rw.pc + i] = gs_value<DIM, RP, RP>(L, Tx, Ty, Tz, rp[rw.pc + i], z, i, rw);
+    });
   }
 }
 
+// The last red half-sweep of post-smoothing, with rho = r . z over all cells
+// and the CG direction factor beta = rho / rho_old.
 template <int DIM, typename RP, typename V>
-__global__ void __launch_bounds__(kThreads) k_residual(DevLevel L) {
+__global__ void k_sweep_rho(DevLevel L, int k, SolveState* S, double* partials) {
   const RP *Tx = (const RP*)L.T[0], *Ty = (const RP*)L.T[1], *Tz = (const RP*)L.T[2];
   const V* r = (const V*)L.r;
+  const RP* rp = (const RP*)L.rp;
+  RP* z = (RP*)L.z;
+  V acc = 0;
+  for_colour<DIM>(grid_map(), L, 0, [&](int i, int i2, const Row& rw) {
+    if (i < L.nx) {
+      const RP v = gs_value<DIM, RP, RP>(L, Tx, Ty, Tz, rp[rw.pc + i], z, i, rw);
+      z[rw.pc + i] = v;
+      acc += r[rw.pc + i] * (V)v;
+    }
+    if (i2 < L.nx) acc += r[rw.pc + i2] * (V)z[rw.pc + i2];
+  });
+  grid_total(acc, partials, &S->ticket[k], [&](double rho) {
+    LevelState& ls = S->lv[k];
+    ls.rho = rho;
+    ls.beta = ls.it == 0 ? 0.0 : rho / ls.rho_old;
+    ls.beta_f = (float)ls.beta;
+  });
+}
+
+template <int DIM, typename RP>
+__global__ void k_residual(DevLevel L) {
+  const RP *Tx = (const RP*)L.T[0], *Ty = (const RP*)L.T[1], *Tz = (const RP*)L.T[2];
+  const RP* rp = (const RP*)L.rp;
   const RP* z = (const RP*)L.z;
   RP* t = (RP*)L.t;
-  for (long long c = gtid(); c < L.n; c += gstride()) {
-    Cell q = cell_of(c, L.nx, L.ny);
-    t[c] = (RP)r[c] - apply_value<DIM, RP, RP>(L, Tx, Ty, Tz, z, q);
-  }
+  for_cells<DIM>(grid_map(), L, [&](int i, const Row& rw) {
+    t[rw.pc + i] = rp[rw.pc + i] - apply_value<DIM, RP, RP>(L, Tx, Ty, Tz, z, i, rw);
+  });
 }
 
 template <int DIM, typename RP>
-__global__ void __launch_bounds__(kThreads) k_restrict(DevLevel L, DevLevel C) {
+__global__ void k_restrict(DevLevel L, DevLevel C) {
   const RP* t = (const RP*)L.t;
   RP* rc = (RP*)C.r;
-  for (long long c = gtid(); c < C.n; c += gstride()) {
-    Cell q = cell_of(c, C.nx, C.ny);
-    rc[c] = restrict_value<DIM, RP>(L, t, q.i, q.j, q.k);
-  }
+  for_cells<DIM>(grid_map(), C, [&](int i, const Row& rw) {
+      const int pc = rw.pc + i;
+      const int j = rw.j, k = rw.k;
+      (void)j;
+      (void)k; rc[pc] = restrict_value<DIM, RP>(L, t, i, j, k); });
 }
 
+// z += E x_c on the black cells (see Ops::prolong_postsmooth)
 template <int DIM, typename RP>
-__global__ void __launch_bounds__(kThreads) k_prolong(DevLevel L, DevLevel C) {
+__global__ void k_prolong_black(DevLevel L, DevLevel C) {
   const RP* xc = (const RP*)C.x;
   RP* z = (RP*)L.z;
-  for (long long c = gtid(); c < L.n; c += gstride()) {
-    Cell q = cell_of(c, L.nx, L.ny);
-    z[c] += prolong_value<DIM, RP, RP>(L, C, xc, q);
-  }
+  for_colour<DIM>(grid_map(), L, 1, [&](int i, int, const Row& rw) {
+      const int base = rw.pc;
+      const int j = rw.j, k = rw.k;
+      (void)j;
+      (void)k;
+    if (i < L.nx) z[base + i] += prolong_value<DIM, RP>(L, C, xc, i, j, k);
+  });
 }
 
-// rho = r . z
+// p = z (first iteration) or z + beta p
 template <typename V, typename RP>
-__global__ void __launch_bounds__(kThreads) k_rho(DevLevel L, int k, SolveState* S, double* partials) {
-  __shared__ double sh[33];
-  if (S->lv[k].stop) return;
-  const V* r = (const V*)L.r;
-  const RP* z = (const RP*)L.z;
-  V acc = 0;
-  for (long long c = gtid(); c < L.n; c += gstride()) acc += r[c] * (V)z[c];
-  grid_total((double)acc, partials, &S->ticket[k], sh, [&](double rho) { S->lv[k].rho = rho; });
-}
-
-// p = z (first iteration) or z + (rho/rho_old) p
-template <typename V, typename RP>
-__global__ void __launch_bounds__(kThreads) k_direction(DevLevel L, int k, SolveState* S) {
+__global__ void k_direction(DevLevel L, int k, SolveState* S) {
   const LevelState& ls = S->lv[k];
   if (ls.stop) return;
   const bool first = ls.it == 0;
-  const V beta = first ? (V)0 : (V)(ls.rho / ls.rho_old);
+  const V beta = beta_of<V>(ls);
   V* p = (V*)L.p;
   const RP* z = (const RP*)L.z;
-  for (long long c = gtid(); c < L.n; c += gstride()) p[c] = first ? (V)z[c] : (V)z[c] + beta * p[c];
+  const int n = (int)L.npad;
+  for (int c = (int)lin_tid(); c < n; c += (int)lin_stride()) p[c] = first ? (V)z[c] : (V)z[c] + beta * p[c];
 }
 
-// q = A p, pq = p . q; breakdown check
+// q = A p, pq = p . q, alpha = rho / pq; breakdown check
 template <int DIM, typename V>
-__global__ void __launch_bounds__(kThreads) k_apply_dot(DevLevel L, int k, SolveState* S, double* partials) {
-  __shared__ double sh[33];
+__global__ void k_apply_dot(DevLevel L, int k, SolveState* S, double* partials) {
   if (S->lv[k].stop) return;
   const V *Tx = Tvec<V>(L, 0), *Ty = Tvec<V>(L, 1), *Tz = DIM == 3 ? Tvec<V>(L, 2) : nullptr;
   const V* p = (const V*)L.p;
   V* q = (V*)L.q;
   V acc = 0;
-  for (long long c = gtid(); c < L.n; c += gstride()) {
-    Cell cq = cell_of(c, L.nx, L.ny);
-    const V v = apply_value<DIM, V, V>(L, Tx, Ty, Tz, p, cq);
-    q[c] = v;
-    acc += p[c] * v;
-  }
-  grid_total((double)acc, partials, &S->ticket[k], sh, [&](double pq) {
+  for_cells<DIM>(grid_map(), L, [&](int i, const Row& rw) {
+    const V v = apply_value<DIM, V, V>(L, Tx, Ty, Tz, p, i, rw);
+    q[rw.pc + i] = v;
+    acc += p[rw.pc + i] * v;
+  });
+  grid_total(acc, partials, &S->ticket[k], [&](double pq) {
     LevelState& ls = S->lv[k];
     ls.pq = pq;
     if (!(pq > 0.0) || !isfinite(pq) || !isfinite(ls.rho)) {
       ls.stop = 1;
       atomicOr(&S->status, kStBreakdown);
     }
+    ls.alpha = ls.rho / pq;
+    ls.alpha_f = (float)ls.alpha;
   });
 }
 
 // x += alpha p, r -= alpha q, ||r||^2, the level test of Sec. 3 and the
 // WHILE condition of the level's loop.
 template <typename V>
-__global__ void __launch_bounds__(kThreads) k_update(DevLevel L, int k, SolveState* S, double* partials,
-                                                     cudaGraphConditionalHandle hcond) {
-  __shared__ double sh[33];
+__global__ void k_update(DevLevel L, int k, SolveState* S, double* partials, cudaGraphConditionalHandle hcond) {
   const LevelState& ls = S->lv[k];
   if (ls.stop) {
-    if (gtid() == 0) cudaGraphSetConditional(hcond, 0u);
+    if (lin_tid() == 0) cudaGraphSetConditional(hcond, 0u);
     return;
   }
-  const V alpha = (V)(ls.rho / ls.pq);
+  const V alpha = alpha_of<V>(ls);
   V* x = (V*)L.x;
   V* r = (V*)L.r;
   const V* p = (const V*)L.p;
   const V* q = (const V*)L.q;
   V acc = 0;
-  for (long long c = gtid(); c < L.n; c += gstride()) {
+  const int n = (int)L.npad;
+  for (int c = (int)lin_tid(); c < n; c += (int)lin_stride()) {
     x[c] += alpha * p[c];
     const V rv = r[c] - alpha * q[c];
     r[c] = rv;
     acc += rv * rv;
   }
-  grid_total((double)acc, partials, &S->ticket[k], sh, [&](double rr) {
+  grid_total(acc, partials, &S->ticket[k], [&](double rr) {
     LevelState& w = S->lv[k];
     w.rr = rr;
     w.iters++;
@@ -742,22 +1048,25 @@ __global__ void __launch_bounds__(kThreads) k_update(DevLevel L, int k, SolveSta
   });
 }
 
-// Before a solve: b0 = b, ||b||^2, eps^2 = tol^2 ||b||^2 / N_0 (Sec. 3), x = 0,
-// counters cleared.
-__global__ void __launch_bounds__(kThreads) k_prepare(const double* b, double* b0, double* xs, long long n, double tol,
-                                                      SolveState* S, int nlev, double* partials) {
-  __shared__ double sh[33];
+// Before a solve: b0 = b (padded), ||b||^2, eps^2 = tol^2 ||b||^2 / N_0
+// (Sec. 3), counters cleared.  xs is zeroed by the caller.
+template <int DIM>
+__global__ void k_prepare(DevLevel L0, const double* b, double* b0, double tol, SolveState* S, int nlev,
+                          double* partials) {
   double acc = 0.0;
-  for (long long c = gtid(); c < n; c += gstride()) {
-    const double v = b[c];
-    b0[c] = v;
-    xs[c] = 0.0;
+  for_cells<DIM>(grid_map(), L0, [&](int i, const Row& rw) {
+      const int pc = rw.pc + i;
+      const int j = rw.j, k = rw.k;
+      (void)j;
+      (void)k;
+    const double v = b[i + (long long)L0.nx * (j + (long long)L0.ny * k)];
+    b0[pc] = v;
     acc += v * v;
-  }
-  grid_total(acc, partials, &S->ticket[kMaxLev - 1], sh, [&](double bb) {
+  });
+  grid_total(acc, partials, &S->ticket[kMaxLev - 1], [&](double bb) {
     S->bb0 = bb;
     S->tau2 = tol * tol;
-    S->eps2 = tol * tol * (bb / (double)n);
+    S->eps2 = tol * tol * (bb / (double)L0.n);
     S->status = isfinite(bb) ? 0 : kStNanInf;
     S->rr_true = bb;
     for (int k = 0; k < nlev; ++k) {
@@ -769,36 +1078,80 @@ __global__ void __launch_bounds__(kThreads) k_prepare(const double* b, double* b
   });
 }
 
-// After the level-0 PCG: xs += x_0.  The true residual b - A xs needs the
-// neighbours of every cell, so it is taken by the next kernel.
-__global__ void __launch_bounds__(kThreads) k_accumulate(const double* __restrict__ x0, double* __restrict__ xs, long long n) {
-  for (long long c = gtid(); c < n; c += gstride()) xs[c] += x0[c];
+// After the level-0 PCG: xs += x_0.
+__global__ void k_accumulate(const double* __restrict__ x0, double* __restrict__ xs, long long n) {
+  for (long long c = lin_tid(); c < n; c += lin_stride()) xs[c] += x0[c];
+}
+
+// True residual b - A xs in FP64 into b0 (the right-hand side of a restart).
+template <int DIM>
+__global__ void k_true_residual(DevLevel L0, const double* b, double* b0, const double* xs, SolveState* S,
+                                double* partials) {
+  const double *Tx = L0.T64[0], *Ty = L0.T64[1], *Tz = DIM == 3 ? L0.T64[2] : nullptr;
+  double acc = 0.0;
+  for_cells<DIM>(grid_map(), L0, [&](int i, const Row& rw) {
+      const int pc = rw.pc + i;
+      const int j = rw.j, k = rw.k;
+      (void)j;
+      (void)k;
+    const double v = b[i + (long long)L0.nx * (j + (long long)L0.ny * k)] -
+                     apply_value<DIM, double, double>(L0, Tx, Ty, Tz, xs, i, rw);
+    b0[pc] = v;
+    acc += v * v;
+  });
+  grid_total(acc, partials, &S->ticket[kMaxLev - 1], [&](double rt) { S->rr_true = rt; });
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(kThreads) k_true_residual(DevLevel L0, const double* b, double* b0, const double* xs,
-                                                            SolveState* S, double* partials) {
-  __shared__ double sh[33];
-  const double *Tx = L0.T64[0], *Ty = L0.T64[1], *Tz = DIM == 3 ? L0.T64[2] : nullptr;
-  double acc = 0.0;
-  for (long long c = gtid(); c < L0.n; c += gstride()) {
-    Cell q = cell_of(c, L0.nx, L0.ny);
-    const double v = b[c] - apply_value<DIM, double, double>(L0, Tx, Ty, Tz, xs, q);
-    b0[c] = v;
-    acc += v * v;
-  }
-  grid_total(acc, partials, &S->ticket[kMaxLev - 1], sh, [&](double rt) { S->rr_true = rt; });
+__global__ void k_copy_out(DevLevel L0, const double* xs, double* x) {
+  for_cells<DIM>(grid_map(), L0, [&](int i, const Row& rw) {
+      const int pc = rw.pc + i;
+      const int j = rw.j, k = rw.k;
+      (void)j;
+      (void)k;
+    x[i + (long long)L0.nx * (j + (long long)L0.ny * k)] = xs[pc];
+  });
 }
 
 // ===========================================================================
 // Host side
 // ===========================================================================
-int grid_for(long long n, int threads, int maxblocks) {
-  long long g = (n + threads - 1) / threads;
-  if (g < 1) g = 1;
-  if (g > maxblocks) g = maxblocks;
-  return (int)g;
+struct Launch {
+  dim3 grid, block;
+};
+
+// 2D launch over rows of `width` columns (width = pair positions or cells):
+// a power-of-two block width, 256 threads per block, at most gmax blocks.
+Launch rows_launch(int width, long long rows, int gmax) {
+  int bx = 1;
+  while (bx < width && bx < kThreads) bx <<= 1;
+  const int by = kThreads / bx;
+  Launch l;
+  l.block = dim3(bx, by, 1);
+  long long gx = (width + bx - 1) / bx;
+  long long gy = (rows + by - 1) / by;
+  if (gx > gmax) gx = gmax;
+  long long cap = std::max(1LL, (long long)gmax / gx);
+  if (gy > cap) gy = cap;
+  if (gy > 65535) gy = 65535;
+  l.grid = dim3((unsigned)gx, (unsigned)std::max(1LL, gy), 1);
+  return l;
 }
+
+Launch lin_launch(long long n, int gmax) {
+  Launch l;
+  l.block = dim3(kThreads, 1, 1);
+  long long g = (n + kThreads - 1) / kThreads;
+  if (g < 1) g = 1;
+  if (g > gmax) g = gmax;
+  l.grid = dim3((unsigned)g, 1, 1);
+  return l;
+}
+
+Launch cells_launch(const DevLevel& L, int gmax) { return rows_launch(L.nx, (long long)L.ny * L.nz, gmax); }
+Launch pairs_launch(const DevLevel& L, int gmax) { return rows_launch((L.nx + 1) >> 1, (long long)L.ny * L.nz, gmax); }
+
+size_t levels_smem(const msrcg_hier* h, int lo, bool top_double);
 
 struct Emit {
   msrcg_hier* h;
@@ -809,53 +1162,44 @@ struct Emit {
 template <int DIM, typename RP>
 void emit_pcg(Emit& E, int k, cudaStream_t s);
 
+template <int DIM, typename RP, typename V>
+void emit_smooth(const DevLevel& L, int m, bool from_zero, bool with_rho, int k, msrcg_hier* h, int gmax, cudaStream_t s) {
+  const Launch lp = pairs_launch(L, gmax), lc = cells_launch(L, gmax);
+  if (from_zero) k_sweep<DIM, RP, V><<<lc.grid, lc.block, 0, s>>>(L, 0, 1);
+  else k_sweep<DIM, RP, V><<<lp.grid, lp.block, 0, s>>>(L, 0, 0);
+  for (int i = 0; i < m; ++i) {
+    k_sweep<DIM, RP, V><<<lp.grid, lp.block, 0, s>>>(L, 1, 0);
+    if (with_rho && i == m - 1)
+      k_sweep_rho<DIM, RP, V><<<lp.grid, lp.block, 0, s>>>(L, k, h->dS, h->partials + (size_t)k * kMaxGrid);
+    else
+      k_sweep<DIM, RP, V><<<lp.grid, lp.block, 0, s>>>(L, 0, 0);
+  }
+}
+
 template <int DIM, typename RP>
 void emit_precond(Emit& E, int k, cudaStream_t s) {
   msrcg_hier* h = E.h;
   const DevLevel& L = h->hL[k];
   const DevLevel& C = h->hL[k + 1];
   const int gmax = std::min(h->sms * 8, kMaxGrid);
-  const long long npairs = (long long)((L.nx + 1) >> 1) * L.ny * L.nz;
-  const int gp = grid_for(npairs, kThreads, gmax), gc = grid_for(L.n, kThreads, gmax);
+  const Launch lc = cells_launch(L, gmax), lp = pairs_launch(L, gmax), lcc = cells_launch(C, gmax);
   const int m = h->o.m;
-  // pre-smoothing from zero: red (black red)^m
+  // pre-smoothing from zero, residual, restriction
   if (k == 0) {
-    k_sweep<DIM, RP, double><<<gc, kThreads, 0, s>>>(L, 0, 1);
-    for (int i = 0; i < m; ++i) {
-      k_sweep<DIM, RP, double><<<gp, kThreads, 0, s>>>(L, 1, 0);
-      k_sweep<DIM, RP, double><<<gp, kThreads, 0, s>>>(L, 0, 0);
-    }
-    k_residual<DIM, RP, double><<<gc, kThreads, 0, s>>>(L);
+    emit_smooth<DIM, RP, double>(L, m, true, false, k, h, gmax, s);
+    k_residual<DIM, RP><<<lc.grid, lc.block, 0, s>>>(L);
   } else {
-    k_sweep<DIM, RP, RP><<<gc, kThreads, 0, s>>>(L, 0, 1);
-    for (int i = 0; i < m; ++i) {
-      k_sweep<DIM, RP, RP><<<gp, kThreads, 0, s>>>(L, 1, 0);
-      k_sweep<DIM, RP, RP><<<gp, kThreads, 0, s>>>(L, 0, 0);
-    }
-    k_residual<DIM, RP, RP><<<gc, kThreads, 0, s>>>(L);
+    emit_smooth<DIM, RP, RP>(L, m, true, false, k, h, gmax, s);
+    k_residual<DIM, RP><<<lc.grid, lc.block, 0, s>>>(L);
   }
-  k_restrict<DIM, RP><<<grid_for(C.n, kThreads, gmax), kThreads, 0, s>>>(L, C);
-  // coarse solve, A_c^-1 applied by the PCG one level down (Sec. 2.3)
-  if (k + 1 < h->ks) {
-    emit_pcg<DIM, RP>(E, k + 1, s);
-  } else {
-    k_small<DIM, RP><<<1, kSmallThreads, 0, s>>>(h->dP, nullptr, 1, k + 1, 0, nullptr);
-  }
-  k_prolong<DIM, RP><<<gc, kThreads, 0, s>>>(L, C);
-  // post-smoothing: red (black red)^m
-  if (k == 0) {
-    k_sweep<DIM, RP, double><<<gp, kThreads, 0, s>>>(L, 0, 0);
-    for (int i = 0; i < m; ++i) {
-      k_sweep<DIM, RP, double><<<gp, kThreads, 0, s>>>(L, 1, 0);
-      k_sweep<DIM, RP, double><<<gp, kThreads, 0, s>>>(L, 0, 0);
-    }
-  } else {
-    k_sweep<DIM, RP, RP><<<gp, kThreads, 0, s>>>(L, 0, 0);
-    for (int i = 0; i < m; ++i) {
-      k_sweep<DIM, RP, RP><<<gp, kThreads, 0, s>>>(L, 1, 0);
-      k_sweep<DIM, RP, RP><<<gp, kThreads, 0, s>>>(L, 0, 0);
-    }
-  }
+  k_restrict<DIM, RP><<<lcc.grid, lcc.block, 0, s>>>(L, C);
+  // coarse solve: A_c^-1 applied by the PCG one level down (Sec. 2.3)
+  if (k + 1 < h->ks) emit_pcg<DIM, RP>(E, k + 1, s);
+  else k_small<DIM, RP><<<1, kSmallThreads, h->sub_smem, s>>>(h->dP, nullptr, 1, k + 1, 0, nullptr, h->sub_smem);
+  // prolongation (black cells) and post-smoothing with rho = r . z
+  k_prolong_black<DIM, RP><<<lp.grid, lp.block, 0, s>>>(L, C);
+  if (k == 0) emit_smooth<DIM, RP, double>(L, m, false, true, k, h, gmax, s);
+  else emit_smooth<DIM, RP, RP>(L, m, false, true, k, h, gmax, s);
 }
 
 template <int DIM, typename RP>
@@ -863,7 +1207,7 @@ void emit_pcg(Emit& E, int k, cudaStream_t s) {
   msrcg_hier* h = E.h;
   const DevLevel& L = h->hL[k];
   const int gmax = std::min(h->sms * 8, kMaxGrid);
-  const int gc = grid_for(L.n, kThreads, gmax);
+  const Launch ll = lin_launch(L.npad, gmax), lc = cells_launch(L, gmax);
   double* part = h->partials + (size_t)k * kMaxGrid;
   cudaStreamCaptureStatus cst;
   cudaGraph_t cg;
@@ -880,8 +1224,8 @@ void emit_pcg(Emit& E, int k, cudaStream_t s) {
     E.err = 2;
     return;
   }
-  if (k == 0) k_init<double><<<gc, kThreads, 0, s>>>(L, k, h->dS, h->b0, part, hc);
-  else k_init<RP><<<gc, kThreads, 0, s>>>(L, k, h->dS, nullptr, part, hc);
+  if (k == 0) k_init<double><<<ll.grid, ll.block, 0, s>>>(L, k, h->dS, h->b0, part, hc);
+  else k_init<RP><<<ll.grid, ll.block, 0, s>>>(L, k, h->dS, nullptr, part, hc);
   if (cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, &deps, &edata, &ndeps) != cudaSuccess) {
     E.err = 3;
     return;
@@ -908,15 +1252,13 @@ void emit_pcg(Emit& E, int k, cudaStream_t s) {
   }
   emit_precond<DIM, RP>(E, k, b);
   if (k == 0) {
-    k_rho<double, RP><<<gc, kThreads, 0, b>>>(L, k, h->dS, part);
-    k_direction<double, RP><<<gc, kThreads, 0, b>>>(L, k, h->dS);
-    k_apply_dot<DIM, double><<<gc, kThreads, 0, b>>>(L, k, h->dS, part);
-    k_update<double><<<gc, kThreads, 0, b>>>(L, k, h->dS, part, hc);
+    k_direction<double, RP><<<ll.grid, ll.block, 0, b>>>(L, k, h->dS);
+    k_apply_dot<DIM, double><<<lc.grid, lc.block, 0, b>>>(L, k, h->dS, part);
+    k_update<double><<<ll.grid, ll.block, 0, b>>>(L, k, h->dS, part, hc);
   } else {
-    k_rho<RP, RP><<<gc, kThreads, 0, b>>>(L, k, h->dS, part);
-    k_direction<RP, RP><<<gc, kThreads, 0, b>>>(L, k, h->dS);
-    k_apply_dot<DIM, RP><<<gc, kThreads, 0, b>>>(L, k, h->dS, part);
-    k_update<RP><<<gc, kThreads, 0, b>>>(L, k, h->dS, part, hc);
+    k_direction<RP, RP><<<ll.grid, ll.block, 0, b>>>(L, k, h->dS);
+    k_apply_dot<DIM, RP><<<lc.grid, lc.block, 0, b>>>(L, k, h->dS, part);
+    k_update<RP><<<ll.grid, ll.block, 0, b>>>(L, k, h->dS, part, hc);
   }
   cudaGraph_t out;
   if (cudaStreamEndCapture(b, &out) != cudaSuccess) E.err = 7;
@@ -943,32 +1285,73 @@ int build_graph_t(msrcg_hier* h) {
   if (!rc) h->graph = g;
   else if (g) cudaGraphDestroy(g);
   for (int i = 0; i < kMaxLev + 2; ++i) cudaStreamDestroy(E.cs[i]);
-  if (rc && getenv("MSRCG_DEBUG")) fprintf(stderr, "msrcg: graph build failed (step %d): %s\n", E.err,
-                                           cudaGetErrorString(cudaGetLastError()));
+  if (rc && getenv("MSRCG_DEBUG"))
+    fprintf(stderr, "msrcg: graph build failed (step %d): %s\n", E.err, cudaGetErrorString(cudaGetLastError()));
   (void)cudaGetLastError();
   return rc;
 }
 
 int build_graph(msrcg_hier* h) {
   const bool f32 = h->o.precision == 1;
+  h->sub_smem = levels_smem(h, h->ks, false);
   if (h->dim == 2) return f32 ? build_graph_t<2, float>(h) : build_graph_t<2, double>(h);
   return f32 ? build_graph_t<3, float>(h) : build_graph_t<3, double>(h);
 }
 
+// Largest dynamic shared memory a single-CTA launch may use, after the
+// kernel's static shared memory; sets the attribute the launch needs.
 template <int DIM, typename RP>
-void launch_small(const ProblemDesc* P, const int* order, int nprob, int ks, int mode, int* next, int grid, cudaStream_t s) {
-  k_small<DIM, RP><<<grid, kSmallThreads, 0, s>>>(P, order, nprob, ks, mode, next);
+size_t small_smem_limit() {
+  static size_t lim = 0;
+  if (!lim) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    cudaFuncGetAttributes(&fa, k_small<DIM, RP>);
+    size_t l = (size_t)optin > fa.sharedSizeBytes + 1024 ? (size_t)optin - fa.sharedSizeBytes - 1024 : 0;
+    cudaFuncSetAttribute(k_small<DIM, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l);
+    (void)cudaGetLastError();
+    lim = l;
+  }
+  return lim;
+}
+
+size_t small_smem_limit_any(int dim, bool f32) {
+  if (dim == 2) return f32 ? small_smem_limit<2, float>() : small_smem_limit<2, double>();
+  return f32 ? small_smem_limit<3, float>() : small_smem_limit<3, double>();
+}
+
+template <int DIM, typename RP>
+void launch_small(const ProblemDesc* P, const int* order, int nprob, int ks, int mode, int* next, int grid,
+                  size_t smem, cudaStream_t s) {
+  k_small<DIM, RP><<<grid, kSmallThreads, smem, s>>>(P, order, nprob, ks, mode, next, smem);
 }
 
 void launch_small_any(int dim, bool f32, const ProblemDesc* P, const int* order, int nprob, int ks, int mode, int* next,
-                      int grid, cudaStream_t s) {
+                      int grid, size_t smem, cudaStream_t s) {
   if (dim == 2) {
-    if (f32) launch_small<2, float>(P, order, nprob, ks, mode, next, grid, s);
-    else launch_small<2, double>(P, order, nprob, ks, mode, next, grid, s);
+    if (f32) launch_small<2, float>(P, order, nprob, ks, mode, next, grid, smem, s);
+    else launch_small<2, double>(P, order, nprob, ks, mode, next, grid, smem, s);
   } else {
-    if (f32) launch_small<3, float>(P, order, nprob, ks, mode, next, grid, s);
-    else launch_small<3, double>(P, order, nprob, ks, mode, next, grid, s);
+    if (f32) launch_small<3, float>(P, order, nprob, ks, mode, next, grid, smem, s);
+    else launch_small<3, double>(P, order, nprob, ks, mode, next, grid, smem, s);
   }
+}
+
+// Shared memory that levels lo..kmax of hierarchy h need (from the coarsest
+// up, as many as fit under the per-CTA limit).
+size_t levels_smem(const msrcg_hier* h, int lo, bool top_double) {
+  const bool f32 = h->o.precision == 1;
+  const size_t rsz = f32 ? sizeof(float) : sizeof(double), lim = small_smem_limit_any(h->dim, f32);
+  size_t tot = 0;
+  for (int k = h->nlev - 1; k >= lo; --k) {
+    const size_t vsz = (top_double && k == 0) ? sizeof(double) : rsz;
+    const size_t b = level_smem_bytes(h->hL[k], vsz, rsz, h->dim);
+    if (tot + b > lim) break;
+    tot += b;
+  }
+  return tot;
 }
 
 ProblemDesc make_desc(msrcg_hier* h, const double* b, double* x, double tol) {
@@ -983,6 +1366,7 @@ ProblemDesc make_desc(msrcg_hier* h, const double* b, double* x, double tol) {
   pd.S = h->dS;
   pd.b = b;
   pd.x = x;
+  pd.xs = h->xs;
   pd.tol = tol;
   pd.work = h->N[0];
   return pd;
@@ -1002,6 +1386,22 @@ void fill_stats(const msrcg_hier* h, const SolveState& S, msrcg_stats* st, int r
   st->status = msrcg_status_from_bits(S.status);
 }
 
+// After a failed solve, vectors may hold non-finite values (their ghosts
+// included); clear every level's vectors so that the hierarchy is reusable.
+int scrub(msrcg_hier* h, cudaStream_t s) {
+  const size_t rsz = h->o.precision == 1 ? sizeof(float) : sizeof(double);
+  for (int k = 0; k < h->nlev; ++k) {
+    const DevLevel& L = h->hL[k];
+    const size_t vsz = k == 0 ? sizeof(double) : rsz;
+    void* v4[4] = {L.x, L.r, L.p, L.q};
+    for (int v = 0; v < 4; ++v) MSRCG_CUDA_TRY(cudaMemsetAsync(v4[v], 0, vsz * L.npad, s));
+    MSRCG_CUDA_TRY(cudaMemsetAsync(L.z, 0, rsz * L.npad, s));
+    MSRCG_CUDA_TRY(cudaMemsetAsync(L.t, 0, rsz * L.npad, s));
+  }
+  MSRCG_CUDA_TRY(cudaMemsetAsync(h->b0, 0, sizeof(double) * h->hL[0].npad, s));
+  return MSRCG_OK;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -1016,6 +1416,11 @@ extern "C" int msrcg_solve(msrcg_hier* h, const double* b, double tol, double* x
     int rc = build_graph(h);
     if (rc) return rc;
   }
+  if (h->dirty) {
+    int rc = scrub(h, s);
+    if (rc) return rc;
+    h->dirty = false;
+  }
   {
     ProblemDesc pd = make_desc(h, b, x, tol);
     MSRCG_CUDA_TRY(cudaMemcpyAsync(h->dP, &pd, sizeof(pd), cudaMemcpyHostToDevice, s));
@@ -1026,19 +1431,22 @@ extern "C" int msrcg_solve(msrcg_hier* h, const double* b, double tol, double* x
   int restarts = 0;
   if (h->ks == 0) {
     // every level fits one CTA: one launch runs the whole solve
-    launch_small_any(dim, f32, h->dP, nullptr, 1, 0, 2, nullptr, 1, s);
+    launch_small_any(dim, f32, h->dP, nullptr, 1, 0, 2, nullptr, 1, levels_smem(h, 0, true), s);
     MSRCG_CUDA_TRY(cudaGetLastError());
   } else {
     const int gmax = std::min(h->sms * 8, kMaxGrid);
     double* part = h->partials + (size_t)(kMaxLev - 1) * kMaxGrid;
-    const int g0 = grid_for(h->N[0], kThreads, gmax);
-    k_prepare<<<g0, kThreads, 0, s>>>(b, h->b0, h->xs, h->N[0], tol, h->dS, h->nlev, part);
+    const DevLevel& L0 = h->hL[0];
+    const Launch lc = cells_launch(L0, gmax), ll = lin_launch(L0.npad, gmax);
+    MSRCG_CUDA_TRY(cudaMemsetAsync(h->xs, 0, sizeof(double) * L0.npad, s));
+    if (dim == 2) k_prepare<2><<<lc.grid, lc.block, 0, s>>>(L0, b, h->b0, tol, h->dS, h->nlev, part);
+    else k_prepare<3><<<lc.grid, lc.block, 0, s>>>(L0, b, h->b0, tol, h->dS, h->nlev, part);
     MSRCG_CUDA_TRY(cudaGetLastError());
     for (;;) {
       MSRCG_CUDA_TRY(cudaGraphLaunch(h->gexec, s));
-      k_accumulate<<<g0, kThreads, 0, s>>>((const double*)h->hL[0].x, h->xs, h->N[0]);
-      if (dim == 2) k_true_residual<2><<<g0, kThreads, 0, s>>>(h->hL[0], b, h->b0, h->xs, h->dS, part);
-      else k_true_residual<3><<<g0, kThreads, 0, s>>>(h->hL[0], b, h->b0, h->xs, h->dS, part);
+      k_accumulate<<<ll.grid, ll.block, 0, s>>>((const double*)L0.x, h->xs, L0.npad);
+      if (dim == 2) k_true_residual<2><<<lc.grid, lc.block, 0, s>>>(L0, b, h->b0, h->xs, h->dS, part);
+      else k_true_residual<3><<<lc.grid, lc.block, 0, s>>>(L0, b, h->b0, h->xs, h->dS, part);
       MSRCG_CUDA_TRY(cudaGetLastError());
       if (!stats) break;
       MSRCG_CUDA_TRY(cudaMemcpyAsync(&hs, h->dS, sizeof(hs), cudaMemcpyDeviceToHost, s));
@@ -1046,7 +1454,9 @@ extern "C" int msrcg_solve(msrcg_hier* h, const double* b, double tol, double* x
       if (hs.status != 0 || hs.rr_true < hs.tau2 * hs.bb0 || restarts >= 3 || !(hs.bb0 > 0)) break;
       ++restarts;
     }
-    MSRCG_CUDA_TRY(cudaMemcpyAsync(x, h->xs, sizeof(double) * h->N[0], cudaMemcpyDeviceToDevice, s));
+    if (dim == 2) k_copy_out<2><<<lc.grid, lc.block, 0, s>>>(L0, h->xs, x);
+    else k_copy_out<3><<<lc.grid, lc.block, 0, s>>>(L0, h->xs, x);
+    MSRCG_CUDA_TRY(cudaGetLastError());
   }
   if (stats) {
     MSRCG_CUDA_TRY(cudaMemcpyAsync(&hs, h->dS, sizeof(hs), cudaMemcpyDeviceToHost, s));
@@ -1056,6 +1466,7 @@ extern "C" int msrcg_solve(msrcg_hier* h, const double* b, double tol, double* x
       h->last_iters[k] = stats->iters[k];
       h->last_calls[k] = stats->calls[k];
     }
+    if (stats->status != MSRCG_OK) h->dirty = true;
     return stats->status;
   }
   return MSRCG_OK;
@@ -1063,13 +1474,22 @@ extern "C" int msrcg_solve(msrcg_hier* h, const double* b, double tol, double* x
 
 extern "C" int msrcg_batch_solve(int count, msrcg_hier* const* hs, const double* const* b, double tol, double* const* x,
                                  msrcg_stats* stats, void* stream) {
-  if (count < 0 || (count > 0 && (!hs || !b || !x)) || !(tol > 0.0)) return MSRCG_EINVAL;
+  if (count < 0 || (count > 0 && (!hs || !b || !x)) || !(tol > 0.0) || !isfinite(tol)) return MSRCG_EINVAL;
   if (count == 0) return MSRCG_OK;
   cudaStream_t s = (cudaStream_t)stream;
   const int dim = hs[0]->dim, prec = hs[0]->o.precision;
   std::vector<ProblemDesc> pds(count);
   for (int i = 0; i < count; ++i) {
     if (!hs[i] || !b[i] || !x[i] || hs[i]->dim != dim || hs[i]->o.precision != prec) return MSRCG_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return MSRCG_EINVAL;
+  }
+  for (int i = 0; i < count; ++i) {
+    if (hs[i]->dirty) {
+      int rc = scrub(hs[i], s);
+      if (rc) return rc;
+      hs[i]->dirty = false;
+    }
     pds[i] = make_desc(hs[i], b[i], x[i], tol);
     const double floor2 = prec == 1 ? hs[i]->o.inner_floor * hs[i]->o.inner_floor : 0.0;
     MSRCG_CUDA_TRY(cudaMemcpyAsync(&hs[i]->dS->inner_floor2, &floor2, sizeof(double), cudaMemcpyHostToDevice, s));
@@ -1084,16 +1504,19 @@ extern "C" int msrcg_batch_solve(int count, msrcg_hier* const* hs, const double*
   MSRCG_CUDA_TRY(cudaMemcpyAsync(dp, pds.data(), sizeof(ProblemDesc) * count, cudaMemcpyHostToDevice, s));
   MSRCG_CUDA_TRY(cudaMemcpyAsync(dord, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s));
   MSRCG_CUDA_TRY(cudaMemsetAsync(dnext, 0, sizeof(int), s));
+  // shared memory per CTA: what the largest problem's coarse levels need
+  size_t smem = 0;
+  for (int i = 0; i < count; ++i) smem = std::max(smem, levels_smem(hs[i], 0, true));
   int sms = hs[0]->sms, per = 0;
   if (dim == 2) {
-    if (prec) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_small<2, float>, kSmallThreads, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_small<2, double>, kSmallThreads, 0);
+    if (prec) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_small<2, float>, kSmallThreads, smem);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_small<2, double>, kSmallThreads, smem);
   } else {
-    if (prec) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_small<3, float>, kSmallThreads, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_small<3, double>, kSmallThreads, 0);
+    if (prec) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_small<3, float>, kSmallThreads, smem);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_small<3, double>, kSmallThreads, smem);
   }
   int grid = std::max(1, std::min(count, sms * std::max(per, 1)));
-  launch_small_any(dim, prec == 1, (const ProblemDesc*)dp, (const int*)dord, count, 0, 1, (int*)dnext, grid, s);
+  launch_small_any(dim, prec == 1, (const ProblemDesc*)dp, (const int*)dord, count, 0, 1, (int*)dnext, grid, smem, s);
   MSRCG_CUDA_TRY(cudaGetLastError());
   int rc = MSRCG_OK;
   std::vector<SolveState> st(count);
@@ -1111,7 +1534,10 @@ extern "C" int msrcg_batch_solve(int count, msrcg_hier* const* hs, const double*
       hs[i]->last_iters[k] = one.iters[k];
       hs[i]->last_calls[k] = one.calls[k];
     }
-    if (one.status && !rc) rc = one.status;
+    if (one.status) {
+      hs[i]->dirty = true;
+      if (!rc) rc = one.status;
+    }
   }
   return rc;
 }

@@ -123,8 +123,8 @@ class Hierarchy:
         g = Grid()
         g.dim = dim
         for a in range(3):
-            g.n[a] = self.n[a] if a < dim else 1
-            g.h[a] = float(h[a]) if a < dim else 1.0
+            g.n[a] = self.n[a] if a < min(dim, len(self.n)) else 1
+            g.h[a] = float(h[a]) if a < min(dim, len(h)) else 1.0
         Kt = _dev(K, torch.float64, self.device).reshape(-1)
         ncomp = Kt.numel() // max(self.N, 1)
         bct = _dev(bc, torch.uint8, self.device)
