@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Benchmark of the recursive multi-scale PCG (Lackner & Menikoff) on GB300.
+
+Workload: 2D 1024x1024 cell-centred 5-point porous flow, log10 K a seeded
+Gaussian random field (correlation length 16 cells) spanning [-4.5, 4.5]
+(1e9 contrast), N(0,1) source, Dirichlet p=1 / p=0 on the x faces and no
+flow on the y faces (lifted), relative residual 1e-8.
+
+A step solves a batch of B independent such problems (own hierarchy, own
+right-hand side) in one persistent launch of the library's batched entry
+point; `value` is solves/s over the whole job with inputs resident in HBM.
+The JSON line also carries the plain-FP64 solver on the same batch, the
+latency of single solves, an end-to-end number through the C ABI with host
+buffers, the roofline of the dominant kernel, sampled clocks and the CPU
+oracle timed on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solves/s to 1e-8 rel. residual at 1024² (FP32-precond vs plain FP64); p99 ms"
+UNIT = "solves/s"
+WORKLOAD = ("2D 1024x1024 5-point -div(K grad p) = f; log10 K Gaussian random field (corr. length 16 cells) "
+            "in [-4.5, 4.5] (1e9 contrast); N(0,1) source; Dirichlet x / no-flow y (lifted); tol 1e-8 relative residual")
+TOL = 1e-8
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=0, help="problems per step per GPU (0 = one per SM)")
+    ap.add_argument("--size", type=int, default=1024)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes (fused schedule) and residency in shared memory
+# ---------------------------------------------------------------------------
+def level_bytes_per_iter(k, dims, prec, dim=2, s=4):
+    """Algorithmic DRAM bytes of one PCG iteration on level k: per cell the
+    fused schedule reads/writes (3d + 15 + 2/s^d) words (transmissibilities
+    d words; residual, iterate, direction, A p, solution; the coarse vector
+    share 2/s^d).  Level 0 of the FP32-preconditioner mode keeps its CG
+    vectors in FP64 and the smoother in FP32: 140 bytes per cell."""
+    n = dims[0] * dims[1] * dims[2]
+    words = 3 * dim + 15 + 2.0 / s ** dim
+    if prec == 1 and k == 0:
+        return 140.0 * n
+    return words * (4 if prec == 1 else 8) * n
+
+
+def smem_resident_levels(dims, prec, dim=2, budget=None):
+    """Levels that the single-CTA solver keeps in shared memory (counted from
+    the coarsest up while their arrays fit the per-CTA budget)."""
+    if budget is None:
+        budget = 232448 - 14368 - 1024
+    rsz = 4 if prec == 1 else 8
+    res, tot = set(), 0
+    for k in range(len(dims) - 1, -1, -1):
+        nx, ny, nz = dims[k]
+        npad = (nx + 2) * (ny + 2) * ((nz + 2) if dim == 3 else 1)
+        vsz = 8 if k == 0 else rsz
+        al = lambda b: (b + 15) // 16 * 16
+        b = 4 * al(npad * vsz) + al(npad * rsz) + (2 * al(npad * rsz) if vsz != rsz else 0)
+        b += al((nx + 1) * ny * nz * rsz) + al(nx * (ny + 1) * nz * rsz)
+        if dim == 3:
+            b += al(nx * ny * (nz + 1) * rsz)
+        if tot + b > budget:
+            break
+        tot += b
+        res.add(k)
+    return res
+
+
+def hbm_bytes_of_solve(stats, prec):
+    dims = [tuple(d) for d in stats["dims"]]
+    res = smem_resident_levels(dims, prec)
+    return sum(stats["iters"][k] * level_bytes_per_iter(k, dims[k], prec) for k in range(len(dims)) if k not in res)
+
+
+def traffic_from_profile(kernel_src):
+    """DRAM traffic per launch from the committed ncu summary, valid only
+    while the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    try:
+        d = json.load(open(path))
+        sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+        if d.get("source_sha256") == sha:
+            return d
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    from paper_math_9809043_gb300 import problems as P
+    prob = P.config_problem(1, scale=args.size)
+    H = O.Hierarchy(prob)
+    b = H.lift_rhs()
+    for _ in range(args.warmup):
+        H.solve(b, TOL)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        x, st = H.solve(b, TOL)
+        ts.append(time.perf_counter() - t0)
+    tot = sum(ts)
+    val = args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "size": args.size, "solver": "CPU oracle (plain C, FP64, 1 thread)"},
+            "iters": st["iters"],
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} full solves of the {args.size}^2 problem"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as tdist
+
+    from paper_math_9809043_gb300 import build as B
+    from paper_math_9809043_gb300 import dist as D
+    from paper_math_9809043_gb300 import problems as P
+
+    rank, world, local = D.env_rank_world()
+    if world > 1:
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if rank == 0 or not os.path.exists(B.LIB):
+        B.build()
+    D.barrier(dev)
+    from paper_math_9809043_gb300 import msrcg as M
+
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    nb = args.batch or sms
+    base = P.config_problem(1, scale=args.size)
+    stream = torch.cuda.current_stream(dev)
+
+    def make_batch(prec):
+        opts = M.default_opts(precision=prec, inner_floor=1e-6 if prec else 0.0)
+        hs, bs = [], []
+        for j in range(nb):
+            # problem j of this rank: the shared permeability field with its own
+            # seeded N(0,1) source
+            rng = np.random.default_rng(1001 * 1000 + rank * nb + j)
+            prob = P.Problem(dim=2, n=base.n, h=base.h, K=base.K, bc=base.bc, gD=base.gD,
+                             f=rng.standard_normal(base.N), pbf=base.pbf)
+            h = M.Hierarchy.from_problem(prob, opts, device=dev)
+            hs.append(h)
+            bs.append(h.rhs_for(prob))
+        xs = [torch.empty(base.N, dtype=torch.float64, device=dev) for _ in range(nb)]
+        return hs, bs, xs
+
+    def timed_steps(hs, bs, xs, steps, warmup, clocks=None):
+        for _ in range(warmup):
+            M.batch_solve(hs, bs, TOL, xs, stream=stream)
+        torch.cuda.synchronize(dev)
+        D.barrier(dev)
+        torch.cuda.synchronize(dev)
+        if clocks:
+            clocks.start()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        sts = None
+        for (e0, e1) in evs:
+            e0.record(stream)
+            _, sts = M.batch_solve(hs, bs, TOL, xs, stream=stream)
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        D.barrier(dev)
+        torch.cuda.synchronize(dev)
+        ck = clocks.stop() if clocks else None
+        per = [e0.elapsed_time(e1) for (e0, e1) in evs]
+        return per, sts, ck
+
+    # ---- FP32 preconditioner (headline) ----
+    hs, bs, xs = make_batch(1)
+    clocks = Clocks(dev.index) if rank == 0 else None
+    per, sts, ck = timed_steps(hs, bs, xs, args.steps, args.warmup, clocks)
+    tot_ms = D.max_over_ranks(sum(per), dev)
+    value = world * nb * args.steps / (tot_ms / 1e3)
+    statuses = sorted({s["status"] for s in sts})
+    relres = max(s["relres_true"] for s in sts)
+
+    # roofline of the dominant kernel: one persistent launch per step
+    prec = 1
+    alg_bytes = sum(hbm_bytes_of_solve(s, prec) for s in sts)
+    launch_s = statistics.mean(per) / 1e3
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    peak = peak or 6800.0
+    achieved = alg_bytes / launch_s / 1e9
+    tr = traffic_from_profile(os.path.join(ROOT, "paper_math_9809043_gb300", "csrc", "msrcg_solve.cu"))
+    traffic = None
+    if tr and tr.get("batch") and tr.get("size") == args.size:
+        traffic = tr["dram_bytes_per_problem"] * nb
+    roofline = {"kernel": "k_small (persistent batched solve, one CTA per problem)", "bound": "hbm",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": peak_src, "traffic": traffic,
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "launch_ms": launch_s * 1e3}
+
+    # ---- latency of single solves (graph path) ----
+    lat = []
+    h0 = hs[0]
+    x0 = torch.empty(base.N, dtype=torch.float64, device=dev)
+    h0.solve(bs[0], TOL, x0, stats=False, stream=stream)
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h0.solve(bs[0], TOL, x0, stats=False, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        lat.append(e0.elapsed_time(e1))
+    lat.sort()
+    latency = {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+               "samples": len(lat), "mode": "one solve at a time (wide levels as graph kernels)"}
+
+    # ---- end to end through the C ABI with host buffers ----
+    hb = [b.cpu().pin_memory() for b in bs]
+    hx = [torch.empty(base.N, dtype=torch.float64).pin_memory() for _ in range(nb)]
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize(dev)
+    D.barrier(dev)
+    t_e2e = []
+    for _ in range(e2e_steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for j in range(nb):
+            bs[j].copy_(hb[j], non_blocking=True)
+        M.batch_solve(hs, bs, TOL, xs, stream=stream)
+        for j in range(nb):
+            hx[j].copy_(xs[j], non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        t_e2e.append(e0.elapsed_time(e1))
+    e2e_ms = D.max_over_ranks(sum(t_e2e), dev)
+    e2e = {"value": world * nb * e2e_steps / (e2e_ms / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": nb * base.N * 8, "d2h_bytes_per_step": nb * base.N * 8}
+    del hs, bs, xs, hb, hx
+    torch.cuda.empty_cache()
+
+    # ---- plain FP64 solver on the same batch ----
+    fp64 = None
+    if not args.no_fp64:
+        hs, bs, xs = make_batch(0)
+        per64, sts64, _ = timed_steps(hs, bs, xs, max(1, min(args.steps, 2)), 1)
+        t64 = D.max_over_ranks(sum(per64), dev)
+        fp64 = {"value": world * nb * len(per64) / (t64 / 1e3), "unit": UNIT, "ms_per_step": t64 / len(per64),
+                "iters": sts64[0]["iters"], "relres_true_max": max(s["relres_true"] for s in sts64)}
+        del hs, bs, xs
+        torch.cuda.empty_cache()
+
+    # ---- CPU oracle on the host cores (rank 0, N = 1 only) ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        from oracle import oracle as O
+        R = O.Hierarchy(base)
+        rb = R.lift_rhs()
+        n_done, t0 = 0, time.perf_counter()
+        while True:
+            R.solve(rb, TOL)
+            n_done += 1
+            if time.perf_counter() - t0 >= args.cpu_seconds:
+                break
+        el = time.perf_counter() - t0
+        cpu = {"value": n_done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{n_done} full FP64 solves of the {args.size}^2 problem ({el:.1f} s)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "size": args.size, "concurrent_solves_per_gpu": nb,
+                           "precision": "FP32 preconditioner (smoother, transfers, inner PCG) in FP64 outer PCG",
+                           "l2": "inputs larger than L2 (each problem's hierarchy ~70 MB resident in HBM)",
+                           "parallelism": f"independent problems, {world} GPU(s)"},
+                "status": statuses, "relres_true_max": relres, "iters": sts[0]["iters"],
+                "latency_ms": latency, "fp64_plain": fp64, "e2e": e2e, "roofline": roofline,
+                "cpu_baseline": cpu, "clocks": ck, "gpu_launches": args.steps}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        tdist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
