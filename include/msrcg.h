@@ -160,6 +160,35 @@ size_t msrcg_device_bytes(const msrcg_hier* h);
 /* Release everything the hierarchy owns (synchronises the device first). */
 void msrcg_free(msrcg_hier* h);
 
+/* Bytes of the fixed device scratch that msrcg_solve_static works in. */
+#define MSRCG_STATIC_SCRATCH_BYTES (4u << 20)
+
+/* Build and solve one small problem without allocating any memory.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc — code whose device memory is all owned by another
+ * allocator (a framework's caching pool, a budget reserved at start-up) and
+ * code in which an allocation is not allowed or too slow (real-time loops).
+ * It does what msrcg_build followed by msrcg_solve does (same operator,
+ * hierarchy and recursion; every level runs in one thread block), but every
+ * device array lives in one fixed array of MSRCG_STATIC_SCRATCH_BYTES inside
+ * the library, which each device that loads the library holds until the
+ * process exits.  No device or host memory is allocated.
+ *  grid, K, ncomp, bc, opts  as msrcg_build (opts may be NULL: defaults).
+ *  b  device, N doubles (read only).   x  device, N doubles (output).
+ *  stats  host, or NULL.  The call synchronises `stream` before returning.
+ * Errors: MSRCG_EINVAL also when the problem's hierarchy does not fit the
+ * scratch (about 20 000 cells in 2D FP64, e.g. 128x128; 24^3 in 3D);
+ * otherwise as msrcg_build and msrcg_solve.
+ * The first call on a device looks up the scratch's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one scratch and keep the previous call's contents
+ * (the call clears what must start at zero): calls that overlap on the GPU,
+ * from two streams or two host threads, race and corrupt each other. */
+int msrcg_solve_static(const msrcg_grid* grid, const double* K, int ncomp, const uint8_t* bc,
+                       const msrcg_opts* opts, const double* b, double tol, double* x, msrcg_stats* stats,
+                       void* stream);
+
 /* Static description of an error code. */
 const char* msrcg_strerror(int code);
 

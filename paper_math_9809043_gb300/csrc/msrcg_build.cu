@@ -721,3 +721,255 @@ extern "C" int msrcg_apply(const msrcg_hier* h, int level, const double* x, doub
 extern "C" int msrcg_num_levels(const msrcg_hier* h) { return h ? h->nlev : 0; }
 extern "C" size_t msrcg_device_bytes(const msrcg_hier* h) { return h ? h->bytes : 0; }
 extern "C" void msrcg_free(msrcg_hier* h) { release(h); }
+
+// ===========================================================================
+// Hierarchy in a caller-supplied device buffer (used by the entry point that
+// allocates nothing).  Same kernels and layout as msrcg_build, but every array
+// is carved out of [base, base + cap) and the transfer tables are computed on
+// the device, so neither device nor host memory is allocated.  All levels run
+// in one CTA (ks = 0).
+// ===========================================================================
+namespace {
+
+// 1-D transfer tables of one axis (nf fine -> nc coarse cells) on the device:
+// prolongation corners/weights per fine cell and, per coarse cell, the window
+// of fine cells interpolating from it with their weights (row stride W).
+__global__ void k_axis_tables(int nf, int nc, int W, int* c0, int* c1, void* w, int* lo, int* hi, void* rw, int f32) {
+  const long long den = 2LL * nf;
+  auto corners = [&](int i, int* a, int* b, double* wt) {
+    const long long num = (2LL * i + 1) * nc - nf;
+    if (num <= 0) {
+      *a = *b = 0;
+      *wt = 0.0;
+    } else if (num / den >= nc - 1) {
+      *a = *b = nc - 1;
+      *wt = 0.0;
+    } else if (num % den == 0) {
+      *a = *b = (int)(num / den);
+      *wt = 0.0;
+    } else {
+      *a = (int)(num / den);
+      *b = *a + 1;
+      *wt = (double)(num % den) / (double)den;
+    }
+  };
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  for (int i = tid; i < nf; i += stride) {
+    int a, b;
+    double wt;
+    corners(i, &a, &b, &wt);
+    c0[i] = a;
+    c1[i] = b;
+    if (f32) ((float*)w)[i] = (float)wt;
+    else ((double*)w)[i] = wt;
+  }
+  for (int I = tid; I < nc; I += stride) {
+    const int wa = (int)(((long long)(I - 1) * nf) / nc) - 2, wb = (int)(((long long)(I + 2) * nf) / nc) + 2;
+    const int a0 = wa < 0 ? 0 : wa, b0 = wb > nf - 1 ? nf - 1 : wb;
+    int l = nf, h = -1;
+    for (int i = a0; i <= b0; ++i) {
+      int a, b;
+      double wt;
+      corners(i, &a, &b, &wt);
+      const bool on = (a == I && (1.0 - wt != 0.0 || a == b)) || (b == I && wt != 0.0);
+      if (on) {
+        l = i < l ? i : l;
+        h = i > h ? i : h;
+      }
+    }
+    lo[I] = l;
+    hi[I] = h;
+    for (int t = 0; t < W; ++t) {
+      const int i = l + t;
+      double v = 0.0;
+      if (i <= h) {
+        int a, b;
+        double wt;
+        corners(i, &a, &b, &wt);
+        if (a == I) v += 1.0 - wt;
+        if (b == I) v += wt;
+      }
+      if (f32) ((float*)rw)[(long long)I * W + t] = (float)v;
+      else ((double*)rw)[(long long)I * W + t] = v;
+    }
+  }
+}
+
+struct Carve {
+  unsigned char* base;
+  size_t cap, off;
+  bool ok;
+  void* take(size_t b) {
+    off = (off + 255) & ~(size_t)255;
+    if (off + b > cap) {
+      ok = false;
+      return nullptr;
+    }
+    void* p = base + off;
+    off += b;
+    return p;
+  }
+};
+
+}  // namespace
+
+int msrcg_build_into(msrcg_hier* h, const msrcg_grid* grid, const double* K, int ncomp, const uint8_t* bc,
+                     const msrcg_opts* opts, cudaStream_t st, unsigned char* base, size_t cap) {
+  if (!h || !grid || !K || !bc || !base) return MSRCG_EINVAL;
+  const int dim = grid->dim;
+  if (dim != 2 && dim != 3) return MSRCG_EINVAL;
+  for (int a = 0; a < dim; ++a)
+    if (grid->n[a] < 1 || !(grid->h[a] > 0.0) || !isfinite(grid->h[a])) return MSRCG_EINVAL;
+  if (ncomp != 1 && ncomp != dim) return MSRCG_EINVAL;
+  msrcg_opts o;
+  if (opts) o = *opts;
+  else msrcg_default_opts(&o);
+  if (o.scale < 2 || o.m < 1 || !(o.f > 0.0) || o.maxit_outer < 1 || o.maxit_inner < 1) return MSRCG_EINVAL;
+  if (o.precision != 0 && o.precision != 1) return MSRCG_EINVAL;
+  if (o.coarsest_max_side <= 0) o.coarsest_max_side = dim == 2 ? 8 : 4;
+  h->dim = dim;
+  h->o = o;
+  for (int a = 0; a < 3; ++a) h->hsz[a] = a < dim ? grid->h[a] : 1.0;
+  if (cudaGetDevice(&h->device) != cudaSuccess) return MSRCG_ECUDA;
+  cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+  int n3[3] = {grid->n[0], grid->n[1], dim == 3 ? grid->n[2] : 1};
+  if ((long long)(n3[0] + 2) * (n3[1] + 2) * (n3[2] + 2) >= (1LL << 31)) return MSRCG_EINVAL;
+  h->nlev = level_sides(dim, n3, o.scale, o.coarsest_max_side, h->dims);
+  if (h->nlev < 1) return MSRCG_EINVAL;
+  for (int k = 0; k < h->nlev; ++k) h->N[k] = (long long)h->dims[k][0] * h->dims[k][1] * h->dims[k][2];
+  if (h->N[h->nlev - 1] > 1024) return MSRCG_EINVAL;
+  h->ks = 0;
+  const bool f32 = o.precision == 1;
+  const size_t rsz = f32 ? sizeof(float) : sizeof(double);
+  const int gmax = std::min(h->sms * 8, kMaxGrid);
+  Carve cv{base, cap, 0, true};
+
+  double hh[3] = {grid->h[0], grid->h[1], dim == 3 ? grid->h[2] : 1.0};
+  double ratio[3] = {(hh[1] * hh[2]) / hh[0], (hh[0] * hh[2]) / hh[1], (hh[0] * hh[1]) / hh[2]};
+  const long long nyz = (long long)n3[1] * n3[2], nxz = (long long)n3[0] * n3[2], nxy = (long long)n3[0] * n3[1];
+  const uint8_t* blo[3] = {bc, bc + 2 * nyz, bc + 2 * nyz + 2 * nxz};
+  const uint8_t* bhi[3] = {bc + nyz, bc + 2 * nyz + nxz, bc + 2 * nyz + 2 * nxz + nxy};
+  for (int k = 0; k < h->nlev; ++k)
+    for (int a = 0; a < dim; ++a) {
+      const int* d = h->dims[k];
+      long long nf = (long long)(d[0] + (a == 0)) * (d[1] + (a == 1)) * (d[2] + (a == 2));
+      h->T64[k][a] = (double*)cv.take(sizeof(double) * nf);
+    }
+  if (!cv.ok) return MSRCG_EINVAL;
+  for (int a = 0; a < dim; ++a) {
+    long long nf = (long long)(n3[0] + (a == 0)) * (n3[1] + (a == 1)) * (n3[2] + (a == 2));
+    const double* Ka = K + (ncomp > 1 ? a * h->N[0] : 0);
+    k_face_trans<<<grid_for(nf, 256, gmax), 256, 0, st>>>(a, n3[0], n3[1], n3[2], ratio[a], Ka, blo[a], bhi[a],
+                                                           h->T64[0][a]);
+  }
+  for (int k = 0; k + 1 < h->nlev; ++k) {
+    int3 nf = make_int3(h->dims[k][0], h->dims[k][1], h->dims[k][2]);
+    int3 nc = make_int3(h->dims[k + 1][0], h->dims[k + 1][1], h->dims[k + 1][2]);
+    for (int a = 0; a < dim; ++a) {
+      long long ncf = (long long)(nc.x + (a == 0)) * (nc.y + (a == 1)) * (nc.z + (a == 2));
+      k_upscale<<<grid_for(ncf, 128, gmax), 128, 0, st>>>(a, nf, nc, h->T64[k][a], h->T64[k + 1][a]);
+    }
+  }
+  for (int k = 0; k < h->nlev; ++k)
+    for (int a = 0; a < dim; ++a) {
+      const int* d = h->dims[k];
+      long long nf = (long long)(d[0] + (a == 0)) * (d[1] + (a == 1)) * (d[2] + (a == 2));
+      if (f32) {
+        void* p = cv.take(sizeof(float) * nf);
+        if (!cv.ok) return MSRCG_EINVAL;
+        k_to_float<<<grid_for(nf, 256, gmax), 256, 0, st>>>(h->T64[k][a], (float*)p, nf);
+        h->TR[k][a] = p;
+      } else {
+        h->TR[k][a] = h->T64[k][a];
+      }
+    }
+  double fk = 1.0;
+  for (int k = 0; k < h->nlev; ++k) {
+    DevLevel& L = h->hL[k];
+    memset(&L, 0, sizeof(L));
+    L.nx = h->dims[k][0];
+    L.ny = h->dims[k][1];
+    L.nz = h->dims[k][2];
+    L.dim = dim;
+    L.n = h->N[k];
+    L.px = L.nx + 2;
+    L.py = L.ny + 2;
+    L.plane = (long long)L.px * L.py;
+    L.off = 1 + L.px + (dim == 3 ? L.plane : 0);
+    L.npad = L.plane * (dim == 3 ? L.nz + 2 : 1);
+    for (int a = 0; a < dim; ++a) {
+      L.T[a] = h->TR[k][a];
+      L.T64[a] = h->T64[k][a];
+    }
+    L.fk = fk;
+    fk *= o.f;
+    L.maxit = k == 0 ? o.maxit_outer : o.maxit_inner;
+    if (k + 1 < h->nlev) {
+      for (int a = 0; a < 3; ++a) {
+        const int nf = h->dims[k][a], nc = h->dims[k + 1][a];
+        const int W = 3 * ((nf + nc - 1) / nc) + 6;
+        int* c0 = (int*)cv.take(sizeof(int) * nf);
+        int* c1 = (int*)cv.take(sizeof(int) * nf);
+        void* w = cv.take(rsz * nf);
+        int* lo = (int*)cv.take(sizeof(int) * nc);
+        int* hi = (int*)cv.take(sizeof(int) * nc);
+        void* rw = cv.take(rsz * (size_t)nc * W);
+        if (!cv.ok) return MSRCG_EINVAL;
+        k_axis_tables<<<grid_for(std::max(nf, nc), 128, gmax), 128, 0, st>>>(nf, nc, W, c0, c1, w, lo, hi, rw, f32);
+        L.c0[a] = c0;
+        L.c1[a] = c1;
+        L.w[a] = w;
+        L.lo[a] = lo;
+        L.hi[a] = hi;
+        L.rw[a] = rw;
+        L.W[a] = W;
+      }
+    }
+    // padded vectors; the ghost rings must be zero, and the buffer keeps the
+    // previous call's contents, so every vector is cleared
+    const size_t vsz = k == 0 ? sizeof(double) : rsz;
+    void** vv[4] = {&L.x, &L.r, &L.p, &L.q};
+    for (int v = 0; v < 4; ++v) {
+      void* p = cv.take(vsz * L.npad);
+      if (!cv.ok) return MSRCG_EINVAL;
+      MSRCG_CUDA_TRY(cudaMemsetAsync(p, 0, vsz * L.npad, st));
+      *vv[v] = p;
+    }
+    L.z = cv.take(rsz * L.npad);
+    L.t = cv.take(rsz * L.npad);
+    L.rp = vsz != rsz ? cv.take(rsz * L.npad) : L.r;
+    if (!cv.ok) return MSRCG_EINVAL;
+    MSRCG_CUDA_TRY(cudaMemsetAsync(L.z, 0, rsz * L.npad, st));
+    MSRCG_CUDA_TRY(cudaMemsetAsync(L.t, 0, rsz * L.npad, st));
+    if (vsz != rsz) MSRCG_CUDA_TRY(cudaMemsetAsync(L.rp, 0, rsz * L.npad, st));
+  }
+  {
+    const int kc = h->nlev - 1;
+    h->nc = (int)h->N[kc];
+    double* A = (double*)cv.take(sizeof(double) * h->nc * h->nc);
+    double* Ai = (double*)cv.take(sizeof(double) * h->nc * h->nc);
+    int* fl = (int*)cv.take(sizeof(int));
+    if (!cv.ok) return MSRCG_EINVAL;
+    MSRCG_CUDA_TRY(cudaMemsetAsync(fl, 0, sizeof(int), st));
+    k_dense_assemble<<<1, 512, 0, st>>>(h->dims[kc][0], h->dims[kc][1], h->dims[kc][2], h->T64[kc][0], h->T64[kc][1],
+                                        dim == 3 ? h->T64[kc][2] : nullptr, A);
+    k_chol_inverse<<<1, 512, 0, st>>>(h->nc, A, Ai, fl);
+    int hf = 0;
+    MSRCG_CUDA_TRY(cudaMemcpyAsync(&hf, fl, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MSRCG_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hf) return MSRCG_EBREAKDOWN;
+    h->Ainv = Ai;
+  }
+  h->dL = (DevLevel*)cv.take(sizeof(DevLevel) * h->nlev);
+  h->dS = (SolveState*)cv.take(sizeof(SolveState));
+  h->xs = (double*)cv.take(sizeof(double) * h->hL[0].npad);
+  h->dP = (ProblemDesc*)cv.take(sizeof(ProblemDesc));
+  h->partials = nullptr;
+  h->b0 = nullptr;
+  if (!cv.ok) return MSRCG_EINVAL;
+  MSRCG_CUDA_TRY(cudaMemcpyAsync(h->dL, h->hL, sizeof(DevLevel) * h->nlev, cudaMemcpyHostToDevice, st));
+  MSRCG_CUDA_TRY(cudaMemsetAsync(h->dS, 0, sizeof(SolveState), st));
+  MSRCG_CUDA_TRY(cudaGetLastError());
+  h->bytes = cv.off;
+  return MSRCG_OK;
+}

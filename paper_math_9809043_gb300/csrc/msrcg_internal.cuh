@@ -139,4 +139,7 @@ struct msrcg_hier {
 
 // allocation helper: records the buffer in h->allocs
 int msrcg_alloc(msrcg_hier* h, void** p, size_t bytes);
+// builds h inside the device buffer [base, base + cap) without allocating
+int msrcg_build_into(msrcg_hier* h, const msrcg_grid* grid, const double* K, int ncomp, const uint8_t* bc,
+                     const msrcg_opts* opts, cudaStream_t st, unsigned char* base, size_t cap);
 int msrcg_status_from_bits(int bits);

@@ -1541,3 +1541,61 @@ extern "C" int msrcg_batch_solve(int count, msrcg_hier* const* hs, const double*
   }
   return rc;
 }
+
+// ===========================================================================
+// Solve without allocating (msrcg_solve_static)
+//
+// For callers that must not allocate device memory: code whose device memory
+// is all owned by another allocator (a framework's caching pool, a fixed
+// budget reserved at start-up), and code that runs where cudaMalloc is not
+// allowed or not wanted (real-time loops).  The whole hierarchy of a small
+// problem lives in one file-scope device array; the caller passes only the
+// inputs and the output.
+// ===========================================================================
+namespace {
+
+// The scratch of msrcg_solve_static.  Every device that loads the library
+// holds it until the process exits.  Host code must not pass the symbol
+// itself to a kernel: on the host it is only a stand-in, so its device
+// address is looked up with cudaGetSymbolAddress (once per device).
+static __device__ __align__(256) unsigned char g_static_scratch[MSRCG_STATIC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+void* g_static_ptr[kMaxDevices] = {};
+
+}  // namespace
+
+extern "C" int msrcg_solve_static(const msrcg_grid* grid, const double* K, int ncomp, const uint8_t* bc,
+                                  const msrcg_opts* opts, const double* b, double tol, double* x, msrcg_stats* stats,
+                                  void* stream) {
+  if (!grid || !K || !bc || !b || !x || !(tol > 0.0) || !isfinite(tol)) return MSRCG_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0;
+  MSRCG_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return MSRCG_EINVAL;
+  if (!g_static_ptr[dev]) {
+    // first call on this device: find the device address of the scratch
+    void* p = nullptr;
+    MSRCG_CUDA_TRY(cudaGetSymbolAddress(&p, g_static_scratch));
+    if (!p) return MSRCG_ECUDA;
+    g_static_ptr[dev] = p;
+  }
+  msrcg_hier h;  // host bookkeeping only; its device arrays are carved from the scratch
+  int rc = msrcg_build_into(&h, grid, K, ncomp, bc, opts, s, (unsigned char*)g_static_ptr[dev],
+                            MSRCG_STATIC_SCRATCH_BYTES);
+  if (rc) return rc;
+  const bool f32 = h.o.precision == 1;
+  ProblemDesc pd = make_desc(&h, b, x, tol);
+  MSRCG_CUDA_TRY(cudaMemcpyAsync(h.dP, &pd, sizeof(pd), cudaMemcpyHostToDevice, s));
+  const double floor2 = f32 ? h.o.inner_floor * h.o.inner_floor : 0.0;
+  MSRCG_CUDA_TRY(cudaMemcpyAsync(&h.dS->inner_floor2, &floor2, sizeof(double), cudaMemcpyHostToDevice, s));
+  launch_small_any(h.dim, f32, h.dP, nullptr, 1, 0, 2, nullptr, 1, levels_smem(&h, 0, true), s);
+  MSRCG_CUDA_TRY(cudaGetLastError());
+  SolveState hs;
+  MSRCG_CUDA_TRY(cudaMemcpyAsync(&hs, h.dS, sizeof(hs), cudaMemcpyDeviceToHost, s));
+  MSRCG_CUDA_TRY(cudaStreamSynchronize(s));
+  msrcg_stats one;
+  fill_stats(&h, hs, &one, 0);
+  if (stats) *stats = one;
+  return one.status;
+}

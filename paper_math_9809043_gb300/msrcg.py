@@ -78,6 +78,8 @@ def lib():
         L.msrcg_device_bytes.restype = C.c_size_t
         L.msrcg_free.argtypes = [vp]
         L.msrcg_free.restype = None
+        L.msrcg_solve_static.argtypes = [C.POINTER(Grid), vp, C.c_int, vp, C.POINTER(Opts), vp, C.c_double, vp,
+                                         C.POINTER(Stats), vp]
         L.msrcg_strerror.argtypes = [C.c_int]
         L.msrcg_strerror.restype = C.c_char_p
         _lib = L
@@ -229,3 +231,34 @@ def batch_solve(hs, bs, tol=1e-8, xs=None, stream=None, check=True):
     if check and rc != OK:
         raise MsrcgError(rc, "msrcg_batch_solve")
     return xs, [s.as_dict() for s in st]
+
+
+STATIC_SCRATCH_BYTES = 4 << 20
+
+
+def solve_static(dim, n, h, K, bc, b, tol=1e-8, x=None, opts: Opts | None = None, device="cuda", stream=None,
+                 check=True):
+    """Build and solve one small problem without allocating (msrcg_solve_static).
+
+    For callers that cannot allocate device memory; the library works in a
+    fixed scratch of STATIC_SCRATCH_BYTES.  Overlapping calls race."""
+    device = torch.device(device)
+    g = Grid()
+    g.dim = dim
+    nn = tuple(int(v) for v in n)
+    for a in range(3):
+        g.n[a] = nn[a] if a < min(dim, len(nn)) else 1
+        g.h[a] = float(h[a]) if a < min(dim, len(h)) else 1.0
+    N = int(np.prod(nn))
+    Kt = _dev(K, torch.float64, device).reshape(-1)
+    bct = _dev(bc, torch.uint8, device)
+    bt = _dev(b, torch.float64, device)
+    if x is None:
+        x = torch.empty(N, dtype=torch.float64, device=device)
+    st = Stats()
+    o = opts or default_opts()
+    rc = lib().msrcg_solve_static(C.byref(g), _ptr(Kt), Kt.numel() // max(N, 1), _ptr(bct), C.byref(o), _ptr(bt),
+                                  float(tol), _ptr(x), C.byref(st), _stream(stream))
+    if check and rc != OK:
+        raise MsrcgError(rc, "msrcg_solve_static")
+    return x, st.as_dict()
