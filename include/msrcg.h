@@ -160,6 +160,49 @@ size_t msrcg_device_bytes(const msrcg_hier* h);
 /* Release everything the hierarchy owns (synchronises the device first). */
 void msrcg_free(msrcg_hier* h);
 
+/* ---- serving: continuous batching of independent solves ----------------
+ * A server admits requests while their estimated device memory (hierarchy,
+ * right-hand side, solution) fits `budget_bytes`, builds each admitted
+ * request's hierarchy on a build stream with stream-ordered allocation, and
+ * on every progress call launches the requests built since the last launch
+ * as one batched wave (one thread block per request, msrcg_batch_solve's
+ * kernel) on a stream of its own; waves overlap on the device, so requests
+ * arriving while others run start as soon as they are built.  A finished
+ * wave's requests get their solution copied to the caller's buffer and
+ * their memory released, which admits waiting requests.  One host thread
+ * drives a server; the calls are not thread safe. */
+typedef struct msrcg_server msrcg_server;
+
+/* max_waves: streams for concurrent waves (0 = 8).  opts as msrcg_build
+ * (NULL = defaults).  Errors: MSRCG_EINVAL, MSRCG_ECUDA. */
+int msrcg_server_create(size_t budget_bytes, int max_waves, const msrcg_opts* opts, msrcg_server** out);
+
+/* Queue one request.  K (ncomp*N doubles), bc (boundary mask) and b (N
+ * doubles) are host arrays read when the request is admitted; x (N doubles,
+ * host) receives the solution when the request finishes.  All four stay
+ * valid until msrcg_server_poll reports the request done.  *id identifies
+ * it.  Runs one progress step.  Errors: MSRCG_EINVAL, MSRCG_ENOMEM (the
+ * request alone exceeds the budget), MSRCG_ECUDA. */
+int msrcg_server_submit(msrcg_server* sv, const msrcg_grid* grid, const double* K, int ncomp, const uint8_t* bc,
+                        const double* b, double tol, double* x, int64_t* id);
+
+/* Retire finished waves, admit waiting requests, launch built ones.
+ * Returns the number of requests not yet done, or a negative error. */
+int msrcg_server_progress(msrcg_server* sv);
+
+/* 1 when request `id` is done (x written, *stats filled if non-NULL; the id
+ * is then forgotten), 0 while pending, a negative code if it failed. */
+int msrcg_server_poll(msrcg_server* sv, int64_t id, msrcg_stats* stats);
+
+/* Progress until every submitted request is done. */
+int msrcg_server_drain(msrcg_server* sv);
+
+/* Device bytes currently charged to admitted requests. */
+size_t msrcg_server_bytes_in_use(const msrcg_server* sv);
+
+/* Wait for the device, release everything the server holds. */
+void msrcg_server_destroy(msrcg_server* sv);
+
 /* Bytes of the fixed device scratch that msrcg_solve_static works in. */
 #define MSRCG_STATIC_SCRATCH_BYTES (4u << 20)
 

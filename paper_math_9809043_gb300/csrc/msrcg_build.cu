@@ -28,7 +28,9 @@ int msrcg_cuda_fail(cudaError_t e, const char* what, const char* file, int line)
 int msrcg_alloc(msrcg_hier* h, void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(p, bytes);
+  // stream-ordered when the hierarchy has an allocation stream (the server),
+  // plain cudaMalloc otherwise
+  cudaError_t e = h->alloc_stream ? cudaMallocAsync(p, bytes, h->alloc_stream) : cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
     *p = nullptr;
@@ -416,22 +418,29 @@ int grid_for(long long n, int threads, int maxblocks) {
   return (int)g;
 }
 
+// Upload a host table on the build stream (the pageable source is consumed
+// before the call returns).
 template <typename T>
-int upload(msrcg_hier* h, const std::vector<T>& v, const void** out) {
+int upload(msrcg_hier* h, const std::vector<T>& v, const void** out, cudaStream_t st) {
   void* p;
   int rc = msrcg_alloc(h, &p, sizeof(T) * v.size());
   if (rc) return rc;
-  MSRCG_CUDA_TRY(cudaMemcpy(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+  MSRCG_CUDA_TRY(cudaMemcpyAsync(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st));
   *out = p;
   return MSRCG_OK;
 }
 
 void release(msrcg_hier* h) {
   if (!h) return;
-  cudaDeviceSynchronize();
+  if (h->alloc_stream) {
+    // stream-ordered: freed after the work already queued on that stream
+    for (void* p : h->allocs) cudaFreeAsync(p, h->alloc_stream);
+  } else {
+    cudaDeviceSynchronize();
+    for (void* p : h->allocs) cudaFree(p);
+  }
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->graph) cudaGraphDestroy(h->graph);
-  for (void* p : h->allocs) cudaFree(p);
   (void)cudaGetLastError();
   delete h;
 }
@@ -473,6 +482,11 @@ extern "C" const char* msrcg_strerror(int code) {
 
 extern "C" int msrcg_build(const msrcg_grid* grid, const double* K, int ncomp, const uint8_t* bc,
                            const msrcg_opts* opts, void* stream, msrcg_hier** out) {
+  return msrcg_build_ex(grid, K, ncomp, bc, opts, (cudaStream_t)stream, nullptr, out);
+}
+
+int msrcg_build_ex(const msrcg_grid* grid, const double* K, int ncomp, const uint8_t* bc, const msrcg_opts* opts,
+                   cudaStream_t stream, cudaStream_t alloc_stream, msrcg_hier** out) {
   if (!out) return MSRCG_EINVAL;
   *out = nullptr;
   if (!grid || !K || !bc) return MSRCG_EINVAL;
@@ -492,6 +506,7 @@ extern "C" int msrcg_build(const msrcg_grid* grid, const double* K, int ncomp, c
   cudaStream_t st = (cudaStream_t)stream;
 
   msrcg_hier* h = new msrcg_hier();
+  h->alloc_stream = alloc_stream;
   h->dim = dim;
   h->o = o;
   for (int a = 0; a < 3; ++a) h->hsz[a] = a < dim ? grid->h[a] : 1.0;
@@ -586,25 +601,25 @@ extern "C" int msrcg_build(const msrcg_grid* grid, const double* K, int ncomp, c
       for (int a = 0; a < 3; ++a) {
         Axis1D ax = axis_tables(h->dims[k][a], h->dims[k + 1][a]);
         const void* p;
-        if ((rc = upload(h, ax.c0, &p))) return fail(rc);
+        if ((rc = upload(h, ax.c0, &p, st))) return fail(rc);
         L.c0[a] = (const int*)p;
-        if ((rc = upload(h, ax.c1, &p))) return fail(rc);
+        if ((rc = upload(h, ax.c1, &p, st))) return fail(rc);
         L.c1[a] = (const int*)p;
-        if ((rc = upload(h, ax.lo, &p))) return fail(rc);
+        if ((rc = upload(h, ax.lo, &p, st))) return fail(rc);
         L.lo[a] = (const int*)p;
-        if ((rc = upload(h, ax.hi, &p))) return fail(rc);
+        if ((rc = upload(h, ax.hi, &p, st))) return fail(rc);
         L.hi[a] = (const int*)p;
         if (f32) {
           std::vector<float> wf(ax.w.begin(), ax.w.end());
-          if ((rc = upload(h, wf, &p))) return fail(rc);
+          if ((rc = upload(h, wf, &p, st))) return fail(rc);
           L.w[a] = p;
           std::vector<float> rf(ax.rw.begin(), ax.rw.end());
-          if ((rc = upload(h, rf, &p))) return fail(rc);
+          if ((rc = upload(h, rf, &p, st))) return fail(rc);
           L.rw[a] = p;
         } else {
-          if ((rc = upload(h, ax.w, &p))) return fail(rc);
+          if ((rc = upload(h, ax.w, &p, st))) return fail(rc);
           L.w[a] = p;
-          if ((rc = upload(h, ax.rw, &p))) return fail(rc);
+          if ((rc = upload(h, ax.rw, &p, st))) return fail(rc);
           L.rw[a] = p;
         }
         L.W[a] = ax.W;
@@ -657,10 +672,10 @@ extern "C" int msrcg_build(const msrcg_grid* grid, const double* K, int ncomp, c
     void* p;
     if ((rc = msrcg_alloc(h, &p, sizeof(DevLevel) * h->nlev))) return fail(rc);
     h->dL = (DevLevel*)p;
-    MSRCG_CUDA_TRY(cudaMemcpy(h->dL, h->hL, sizeof(DevLevel) * h->nlev, cudaMemcpyHostToDevice));
+    MSRCG_CUDA_TRY(cudaMemcpyAsync(h->dL, h->hL, sizeof(DevLevel) * h->nlev, cudaMemcpyHostToDevice, st));
     if ((rc = msrcg_alloc(h, &p, sizeof(SolveState)))) return fail(rc);
     h->dS = (SolveState*)p;
-    MSRCG_CUDA_TRY(cudaMemset(h->dS, 0, sizeof(SolveState)));
+    MSRCG_CUDA_TRY(cudaMemsetAsync(h->dS, 0, sizeof(SolveState), st));
     if ((rc = msrcg_alloc(h, &p, sizeof(double) * kMaxLev * (size_t)std::max(gmax, kMaxGrid)))) return fail(rc);
     h->partials = (double*)p;
     if ((rc = msrcg_alloc(h, &p, sizeof(double) * h->hL[0].npad))) return fail(rc);

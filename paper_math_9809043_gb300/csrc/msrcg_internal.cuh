@@ -132,6 +132,7 @@ struct msrcg_hier {
   cudaGraph_t graph = nullptr;
   size_t sub_smem = 0;                  // dynamic shared memory of the graph's single-CTA launch
   bool dirty = false;                   // last solve failed: clear the vectors before the next
+  cudaStream_t alloc_stream = nullptr;  // set: allocations are stream ordered on it
   int64_t last_iters[MSRCG_MAXLEV] = {};
   int64_t last_calls[MSRCG_MAXLEV] = {};
   int sms = 0;
@@ -139,6 +140,14 @@ struct msrcg_hier {
 
 // allocation helper: records the buffer in h->allocs
 int msrcg_alloc(msrcg_hier* h, void** p, size_t bytes);
+// msrcg_build with an optional stream for stream-ordered allocation
+int msrcg_build_ex(const msrcg_grid* grid, const double* K, int ncomp, const uint8_t* bc, const msrcg_opts* opts,
+                   cudaStream_t stream, cudaStream_t alloc_stream, msrcg_hier** out);
+// batched solve split in two: enqueue everything on s (states copied into
+// host_states), then, once s has passed the work, turn states into stats
+int msrcg_batch_enqueue(int count, msrcg_hier* const* hs, const double* const* b, double tol, double* const* x,
+                        cudaStream_t s, msrcg::SolveState* host_states);
+int msrcg_batch_finish(int count, msrcg_hier* const* hs, const msrcg::SolveState* host_states, msrcg_stats* stats);
 // builds h inside the device buffer [base, base + cap) without allocating
 int msrcg_build_into(msrcg_hier* h, const msrcg_grid* grid, const double* K, int ncomp, const uint8_t* bc,
                      const msrcg_opts* opts, cudaStream_t st, unsigned char* base, size_t cap);

@@ -1472,11 +1472,11 @@ extern "C" int msrcg_solve(msrcg_hier* h, const double* b, double tol, double* x
   return MSRCG_OK;
 }
 
-extern "C" int msrcg_batch_solve(int count, msrcg_hier* const* hs, const double* const* b, double tol, double* const* x,
-                                 msrcg_stats* stats, void* stream) {
-  if (count < 0 || (count > 0 && (!hs || !b || !x)) || !(tol > 0.0) || !isfinite(tol)) return MSRCG_EINVAL;
+int msrcg_batch_enqueue(int count, msrcg_hier* const* hs, const double* const* b, double tol, double* const* x,
+                        cudaStream_t s, SolveState* host_states) {
+  if (count < 0 || (count > 0 && (!hs || !b || !x || !host_states)) || !(tol > 0.0) || !isfinite(tol))
+    return MSRCG_EINVAL;
   if (count == 0) return MSRCG_OK;
-  cudaStream_t s = (cudaStream_t)stream;
   const int dim = hs[0]->dim, prec = hs[0]->o.precision;
   std::vector<ProblemDesc> pds(count);
   for (int i = 0; i < count; ++i) {
@@ -1518,17 +1518,19 @@ extern "C" int msrcg_batch_solve(int count, msrcg_hier* const* hs, const double*
   int grid = std::max(1, std::min(count, sms * std::max(per, 1)));
   launch_small_any(dim, prec == 1, (const ProblemDesc*)dp, (const int*)dord, count, 0, 1, (int*)dnext, grid, smem, s);
   MSRCG_CUDA_TRY(cudaGetLastError());
-  int rc = MSRCG_OK;
-  std::vector<SolveState> st(count);
   for (int i = 0; i < count; ++i)
-    MSRCG_CUDA_TRY(cudaMemcpyAsync(&st[i], hs[i]->dS, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+    MSRCG_CUDA_TRY(cudaMemcpyAsync(&host_states[i], hs[i]->dS, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
   MSRCG_CUDA_TRY(cudaFreeAsync(dp, s));
   MSRCG_CUDA_TRY(cudaFreeAsync(dord, s));
   MSRCG_CUDA_TRY(cudaFreeAsync(dnext, s));
-  MSRCG_CUDA_TRY(cudaStreamSynchronize(s));
+  return MSRCG_OK;
+}
+
+int msrcg_batch_finish(int count, msrcg_hier* const* hs, const SolveState* host_states, msrcg_stats* stats) {
+  int rc = MSRCG_OK;
   for (int i = 0; i < count; ++i) {
     msrcg_stats one;
-    fill_stats(hs[i], st[i], &one, 0);
+    fill_stats(hs[i], host_states[i], &one, 0);
     if (stats) stats[i] = one;
     for (int k = 0; k < hs[i]->nlev; ++k) {
       hs[i]->last_iters[k] = one.iters[k];
@@ -1540,6 +1542,18 @@ extern "C" int msrcg_batch_solve(int count, msrcg_hier* const* hs, const double*
     }
   }
   return rc;
+}
+
+extern "C" int msrcg_batch_solve(int count, msrcg_hier* const* hs, const double* const* b, double tol, double* const* x,
+                                 msrcg_stats* stats, void* stream) {
+  if (count < 0) return MSRCG_EINVAL;
+  if (count == 0) return MSRCG_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<SolveState> st(count);
+  int rc = msrcg_batch_enqueue(count, hs, b, tol, x, s, st.data());
+  if (rc) return rc;
+  MSRCG_CUDA_TRY(cudaStreamSynchronize(s));
+  return msrcg_batch_finish(count, hs, st.data(), stats);
 }
 
 // ===========================================================================

@@ -80,6 +80,16 @@ def lib():
         L.msrcg_free.restype = None
         L.msrcg_solve_static.argtypes = [C.POINTER(Grid), vp, C.c_int, vp, C.POINTER(Opts), vp, C.c_double, vp,
                                          C.POINTER(Stats), vp]
+        L.msrcg_server_create.argtypes = [C.c_size_t, C.c_int, C.POINTER(Opts), C.POINTER(vp)]
+        L.msrcg_server_submit.argtypes = [vp, C.POINTER(Grid), vp, C.c_int, vp, vp, C.c_double, vp,
+                                          C.POINTER(C.c_int64)]
+        L.msrcg_server_progress.argtypes = [vp]
+        L.msrcg_server_poll.argtypes = [vp, C.c_int64, C.POINTER(Stats)]
+        L.msrcg_server_drain.argtypes = [vp]
+        L.msrcg_server_bytes_in_use.argtypes = [vp]
+        L.msrcg_server_bytes_in_use.restype = C.c_size_t
+        L.msrcg_server_destroy.argtypes = [vp]
+        L.msrcg_server_destroy.restype = None
         L.msrcg_strerror.argtypes = [C.c_int]
         L.msrcg_strerror.restype = C.c_char_p
         _lib = L

@@ -209,10 +209,12 @@ def config_problem(i: int, scale: Optional[int] = None) -> Problem:
 
 
 def serving_stream(count: int = 2000, rate_hz: float = 200.0, seed: int = 4004,
-                   max_side_2d: int = 1024, max_side_3d: int = 96):
+                   max_side_2d: int = 1024, max_side_3d: int = 96, channel_fraction: float = 0.5):
     """Poisson arrivals of mixed 2D / 3D requests.  Returns a list of
     (arrival_time_s, spec) with spec a dict that `serving_problem` expands;
-    the fields themselves are drawn lazily so the stream stays small."""
+    the fields themselves are drawn lazily so the stream stays small.
+    channel_fraction: share of requests with the layered channel model
+    (the rest are Gaussian random fields)."""
     rng = np.random.default_rng(seed)
     t = np.cumsum(rng.exponential(1.0 / rate_hz, size=count))
     out = []
@@ -222,7 +224,7 @@ def serving_stream(count: int = 2000, rate_hz: float = 200.0, seed: int = 4004,
             side = int(np.rint(np.exp(rng.uniform(np.log(32), np.log(max_side_2d)))))
         else:
             side = int(np.rint(np.exp(rng.uniform(np.log(32), np.log(max_side_3d)))))
-        kind = "grf" if rng.random() < 0.5 else "channel"
+        kind = "channel" if rng.random() < channel_fraction else "grf"
         decades = float(rng.uniform(2.0, 9.0))
         out.append((float(t[r]), {"dim": 2 if is2d else 3, "side": side, "kind": kind,
                                   "decades": decades, "seed": seed * 10000 + r}))
