@@ -117,8 +117,63 @@ struct Row {
   int j, k, pc, fx, fy, fz;
 };
 
-template <int DIM>
-__device__ __forceinline__ Row make_row(const DevLevel& L, int row) {
+// Level geometry and transfer tables held in registers.  The single-CTA
+// solver keeps its level descriptors in shared memory; reading them through
+// these copies keeps the compiler from re-loading descriptor fields after
+// every store to the level's vectors (it cannot rule out aliasing).
+struct Geo {
+  int nx, ny, nz, px, py;
+  long long plane, off, npad, n;
+};
+struct Xf {
+  int nx, ny, nz, px, py;
+  long long plane, off, npad, n;
+  const int* c0[3];
+  const int* c1[3];
+  const void* w[3];
+  const int* lo[3];
+  const int* hi[3];
+  const void* rw[3];
+  int W[3];
+};
+__device__ __forceinline__ Geo geo_of(const DevLevel& L) {
+  Geo g;
+  g.nx = L.nx;
+  g.ny = L.ny;
+  g.nz = L.nz;
+  g.px = L.px;
+  g.py = L.py;
+  g.plane = L.plane;
+  g.off = L.off;
+  g.npad = L.npad;
+  g.n = L.n;
+  return g;
+}
+__device__ __forceinline__ Xf xf_of(const DevLevel& L) {
+  Xf x;
+  x.nx = L.nx;
+  x.ny = L.ny;
+  x.nz = L.nz;
+  x.px = L.px;
+  x.py = L.py;
+  x.plane = L.plane;
+  x.off = L.off;
+  x.npad = L.npad;
+  x.n = L.n;
+  for (int a = 0; a < 3; ++a) {
+    x.c0[a] = L.c0[a];
+    x.c1[a] = L.c1[a];
+    x.w[a] = L.w[a];
+    x.lo[a] = L.lo[a];
+    x.hi[a] = L.hi[a];
+    x.rw[a] = L.rw[a];
+    x.W[a] = L.W[a];
+  }
+  return x;
+}
+
+template <int DIM, class LV>
+__device__ __forceinline__ Row make_row(const LV& L, int row) {
   Row r;
   r.j = row;
   r.k = 0;
@@ -134,8 +189,8 @@ __device__ __forceinline__ Row make_row(const DevLevel& L, int row) {
 }
 
 // Visit every cell of the level: f(i, row).
-template <int DIM, class F>
-__device__ __forceinline__ void for_cells(const Map& m, const DevLevel& L, F&& f) {
+template <int DIM, class LV, class F>
+__device__ __forceinline__ void for_cells(const Map& m, const LV& L, F&& f) {
   const int rows = L.ny * L.nz;
   for (int row = m.y0; row < rows; row += m.dy) {
     const Row r = make_row<DIM>(L, row);
@@ -146,8 +201,8 @@ __device__ __forceinline__ void for_cells(const Map& m, const DevLevel& L, F&& f
 // Visit the cells of one colour ((i + j + k) & 1 == colour): in a row they
 // are i = 2*ii + ((j + k + colour) & 1).  f(i, i2, row) also gets the other
 // colour's cell at the same pair position (i2); either may be >= nx.
-template <int DIM, class F>
-__device__ __forceinline__ void for_colour(const Map& m, const DevLevel& L, int colour, F&& f) {
+template <int DIM, class LV, class F>
+__device__ __forceinline__ void for_colour(const Map& m, const LV& L, int colour, F&& f) {
   const int rows = L.ny * L.nz;
   const int hx = (L.nx + 1) >> 1;
   for (int row = m.y0; row < rows; row += m.dy) {
@@ -169,8 +224,8 @@ __device__ __forceinline__ double quot<double>(double a, double b) {
 }
 
 // Sum of the face transmissibilities of a cell (the diagonal of A).
-template <int DIM, typename R>
-__device__ __forceinline__ R diag_of(const DevLevel& L, const R* Tx, const R* Ty, const R* Tz, int i, const Row& r) {
+template <int DIM, typename R, class LV>
+__device__ __forceinline__ R diag_of(const LV& L, const R* Tx, const R* Ty, const R* Tz, int i, const Row& r) {
   R d = Tx[r.fx + i];
   d += Tx[r.fx + i + 1];
   d += Ty[r.fy + i];
@@ -186,8 +241,8 @@ __device__ __forceinline__ R diag_of(const DevLevel& L, const R* Tx, const R* Ty
 // neighbours held, x_c = (rhs_c + sum_f T_f x_nb) / sum_f T_f  (Sec. 3); a
 // boundary face meets a zero ghost.  The FP32 smoother divides with the
 // fast hardware quotient; FP64 divides exactly.
-template <int DIM, typename R, typename RX>
-__device__ __forceinline__ R gs_value(const DevLevel& L, const R* Tx, const R* Ty, const R* Tz, R rhs, const RX* x,
+template <int DIM, typename R, typename RX, class LV>
+__device__ __forceinline__ R gs_value(const LV& L, const R* Tx, const R* Ty, const R* Tz, R rhs, const RX* x,
                                       int i, const Row& r) {
   const int pc = r.pc + i;
   const R tw = Tx[r.fx + i], te = Tx[r.fx + i + 1], ts = Ty[r.fy + i], tn = Ty[r.fy + i + L.nx];
@@ -212,8 +267,8 @@ __device__ __forceinline__ R gs_value(const DevLevel& L, const R* Tx, const R* T
 }
 
 // (A x)_c = sum_f T_f (x_c - x_nb); a boundary face gives T_f x_c.
-template <int DIM, typename R, typename RX>
-__device__ __forceinline__ R apply_value(const DevLevel& L, const R* Tx, const R* Ty, const R* Tz, const RX* x, int i,
+template <int DIM, typename R, typename RX, class LV>
+__device__ __forceinline__ R apply_value(const LV& L, const R* Tx, const R* Ty, const R* Tz, const RX* x, int i,
                                          const Row& r) {
   const int pc = r.pc + i;
   const R xc = (R)x[pc];
@@ -232,8 +287,8 @@ __device__ __forceinline__ R apply_value(const DevLevel& L, const R* Tx, const R
 // (R t)_C = (E^T t)_C for coarse cell (I, J, K) of level k+1: a gather over
 // the window of fine cells that interpolate from it, with the tabled weights
 // (Sec. 3, R = E^T).
-template <int DIM, typename R>
-__device__ __forceinline__ R restrict_value(const DevLevel& F, const R* t, int I, int J, int K) {
+template <int DIM, typename R, class FX>
+__device__ __forceinline__ R restrict_value(const FX& F, const R* t, int I, int J, int K) {
   const R* rwx = (const R*)F.rw[0] + (long long)I * F.W[0];
   const R* rwy = (const R*)F.rw[1] + (long long)J * F.W[1];
   const int ilo = __ldg(F.lo[0] + I), ihi = __ldg(F.hi[0] + I), jlo = __ldg(F.lo[1] + J), jhi = __ldg(F.hi[1] + J);
@@ -260,8 +315,8 @@ __device__ __forceinline__ R restrict_value(const DevLevel& F, const R* t, int I
 
 // (E x_c) at fine cell (i, j, k): tensor product of the 1-D linear
 // interpolation with zero slope at the boundary (Sec. 3).
-template <int DIM, typename R>
-__device__ __forceinline__ R prolong_value(const DevLevel& F, const DevLevel& C, const R* xc, int i, int j, int k) {
+template <int DIM, typename R, class FX, class CV>
+__device__ __forceinline__ R prolong_value(const FX& F, const CV& C, const R* xc, int i, int j, int k) {
   const int coff = (int)C.off, cpl = (int)C.plane;
   const R wx = __ldg((const R*)F.w[0] + i), wy = __ldg((const R*)F.w[1] + j);
   const int i0 = __ldg(F.c0[0] + i), i1 = __ldg(F.c1[0] + i), j0 = __ldg(F.c0[1] + j), j1 = __ldg(F.c1[1] + j);
@@ -303,9 +358,10 @@ enum : int { kNormal = 0, kZero = 1, kDot = 2 };
 template <int DIM, typename RP, typename V>
 __device__ __forceinline__ V t_sweep(const DevLevel& L, int colour, const V* r, RP* rp, RP* z, int mode) {
   const RP *Tx = (const RP*)L.T[0], *Ty = (const RP*)L.T[1], *Tz = (const RP*)L.T[2];
+  const Geo G = geo_of(L);
   V acc = 0;
   if (mode == kZero) {
-    for_cells<DIM>(team_map(L.nx), L, [&](int i, const Row& rw) {
+    for_cells<DIM>(team_map(G.nx), G, [&](int i, const Row& rw) {
       const int pc = rw.pc + i;
       RP rhs;
       if (sizeof(V) != sizeof(RP)) {
@@ -314,18 +370,18 @@ __device__ __forceinline__ V t_sweep(const DevLevel& L, int colour, const V* r, 
       } else {
         rhs = rp[pc];
       }
-      z[pc] = ((i + rw.j + rw.k) & 1) == colour ? quot<RP>(rhs, diag_of<DIM, RP>(L, Tx, Ty, Tz, i, rw)) : (RP)0;
+      z[pc] = ((i + rw.j + rw.k) & 1) == colour ? quot<RP>(rhs, diag_of<DIM, RP>(G, Tx, Ty, Tz, i, rw)) : (RP)0;
     });
   } else {
     const bool dot = mode == kDot;
-    for_colour<DIM>(team_map((L.nx + 1) >> 1), L, colour, [&](int i, int i2, const Row& rw) {
+    for_colour<DIM>(team_map((G.nx + 1) >> 1), G, colour, [&](int i, int i2, const Row& rw) {
       const int base = rw.pc;
-      if (i < L.nx) {
-        const RP v = gs_value<DIM, RP, RP>(L, Tx, Ty, Tz, rp[base + i], z, i, rw);
+      if (i < G.nx) {
+        const RP v = gs_value<DIM, RP, RP>(G, Tx, Ty, Tz, rp[base + i], z, i, rw);
         z[base + i] = v;
         if (dot) acc += r[base + i] * (V)v;
       }
-      if (dot && i2 < L.nx) acc += r[base + i2] * (V)z[base + i2];
+      if (dot && i2 < G.nx) acc += r[base + i2] * (V)z[base + i2];
     });
   }
   return acc;
@@ -356,17 +412,23 @@ __device__ V t_smooth(BlockTeam& tm, const DevLevel& L, int m, bool from_zero, b
 // Coarsest level: z = A^-1 r with the FP64 explicit inverse (the recursion
 // ends with the exact inverse, Sec. 2.2).  rc: compact shared scratch.
 template <int DIM, typename V, typename RP>
-__device__ void t_coarsest(BlockTeam& tm, const DevLevel& L, const double* Ainv, int nc, const V* r, RP* z, double* rc) {
-  for_cells<DIM>(team_map(L.nx), L, [&](int i, const Row& rw) {
-    rc[i + L.nx * (rw.j + L.ny * rw.k)] = (double)r[rw.pc + i];
+__device__ void t_coarsest(BlockTeam& tm, const DevLevel& L, const double* Ainv, bool transposed, int nc, const V* r,
+                           RP* z, double* rc) {
+  const Geo G = geo_of(L);
+  for_cells<DIM>(team_map(G.nx), G, [&](int i, const Row& rw) {
+    rc[i + G.nx * (rw.j + G.ny * rw.k)] = (double)r[rw.pc + i];
   });
   tm.sync();
   for (int c = threadIdx.x; c < nc; c += blockDim.x) {
     double s = 0.0;
-    const double* row = Ainv + (long long)c * nc;
-    for (int j = 0; j < nc; ++j) s += __ldg(row + j) * rc[j];
-    const int i = c % L.nx, rw = c / L.nx, jj = rw % L.ny, kk = rw / L.ny;
-    z[(int)L.off + i + L.px * jj + (int)L.plane * kk] = (RP)s;
+    if (transposed) {
+      for (int j = 0; j < nc; ++j) s += Ainv[j * nc + c] * rc[j];
+    } else {
+      const double* row = Ainv + (long long)c * nc;
+      for (int j = 0; j < nc; ++j) s += __ldg(row + j) * rc[j];
+    }
+    const int i = c % G.nx, rw = c / G.nx, jj = rw % G.ny, kk = rw / G.ny;
+    z[(int)G.off + i + G.px * jj + (int)G.plane * kk] = (RP)s;
   }
   tm.sync();
 }
@@ -402,11 +464,44 @@ struct Scal<float> {
 struct RecArgs {
   int kmax, m, nc;
   const double* Ainv;
+  bool ainv_t;      // Ainv held transposed (shared-memory copy)
   double eps2, floor2;
+  float floor2_f;
   SolveState* S;
   bool top_double;  // level 0 keeps FP64 vectors
   double* rc;       // shared scratch of the coarsest solve
+  // per level, in shared memory: f^k eps^2 N_k in both precisions, and the
+  // iteration / call counters of this launch (added to S at the end)
+  const double* thrN_d;
+  const float* thrN_f;
+  long long* iters;
+  long long* calls;
 };
+
+// Per-level thresholds of the level test and zeroed counters (thread 0),
+// then a barrier.
+__device__ void level_consts(const DevLevel* sL, int nlev, double eps2, double* thrN_d, float* thrN_f,
+                             long long* iters, long long* calls) {
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < nlev; ++k) {
+      thrN_d[k] = sL[k].fk * eps2 * (double)sL[k].n;
+      thrN_f[k] = (float)thrN_d[k];
+      iters[k] = 0;
+      calls[k] = 0;
+    }
+  }
+  __syncthreads();
+}
+
+// Add this launch's counters to the problem's state (thread 0).
+__device__ void flush_counts(SolveState* S, int nlev, const long long* iters, const long long* calls) {
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int k = 0; k < nlev; ++k) {
+      S->lv[k].iters += iters[k];
+      S->lv[k].calls += calls[k];
+    }
+}
 
 // Steps of one level with vector type V (double at level 0 of a full solve,
 // the smoother type RP elsewhere).
@@ -416,8 +511,9 @@ struct Ops {
   static __device__ V enter(BlockTeam& tm, const DevLevel& L) {
     V* x = (V*)L.x;
     const V* r = (const V*)L.r;
+    const int npad = (int)L.npad;
     V acc = 0;
-    for (int c = threadIdx.x; c < (int)L.npad; c += blockDim.x) {
+    for (int c = threadIdx.x; c < npad; c += blockDim.x) {
       x[c] = 0;
       acc += r[c] * r[c];
     }
@@ -430,13 +526,15 @@ struct Ops {
     const RP* z = (const RP*)L.z;
     RP* t = (RP*)L.t;
     const RP *Tx = (const RP*)L.T[0], *Ty = (const RP*)L.T[1], *Tz = (const RP*)L.T[2];
-    for_cells<DIM>(team_map(L.nx), L, [&](int i, const Row& rw) {
-      t[rw.pc + i] = rp[rw.pc + i] - apply_value<DIM, RP, RP>(L, Tx, Ty, Tz, z, i, rw);
+    const Geo G = geo_of(L), Gc = geo_of(C);
+    for_cells<DIM>(team_map(G.nx), G, [&](int i, const Row& rw) {
+      t[rw.pc + i] = rp[rw.pc + i] - apply_value<DIM, RP, RP>(G, Tx, Ty, Tz, z, i, rw);
     });
     tm.sync();
     RP* rc = (RP*)C.r;
-    for_cells<DIM>(team_map(C.nx), C, [&](int i, const Row& rw) {
-      rc[rw.pc + i] = restrict_value<DIM, RP>(L, t, i, rw.j, rw.k);
+    const Xf X = xf_of(L);
+    for_cells<DIM>(team_map(Gc.nx), Gc, [&](int i, const Row& rw) {
+      rc[rw.pc + i] = restrict_value<DIM, RP>(X, t, i, rw.j, rw.k);
     });
     tm.sync();
   }
@@ -446,18 +544,21 @@ struct Ops {
   static __device__ V prolong_postsmooth(BlockTeam& tm, const DevLevel& L, const DevLevel& C, int m) {
     RP* z = (RP*)L.z;
     const RP* xc = (const RP*)C.x;
-    for_colour<DIM>(team_map((L.nx + 1) >> 1), L, 1, [&](int i, int, const Row& rw) {
-      if (i < L.nx) z[rw.pc + i] += prolong_value<DIM, RP>(L, C, xc, i, rw.j, rw.k);
+    const Xf X = xf_of(L);
+    const Geo Gc = geo_of(C);
+    for_colour<DIM>(team_map((X.nx + 1) >> 1), X, 1, [&](int i, int, const Row& rw) {
+      if (i < X.nx) z[rw.pc + i] += prolong_value<DIM, RP>(X, Gc, xc, i, rw.j, rw.k);
     });
     tm.sync();
     return t_smooth<DIM, RP, V>(tm, L, m, false, true);
   }
   static __device__ V coarsest(BlockTeam& tm, const DevLevel& L, const RecArgs& a) {
-    t_coarsest<DIM, V, RP>(tm, L, a.Ainv, a.nc, (const V*)L.r, (RP*)L.z, a.rc);
+    t_coarsest<DIM, V, RP>(tm, L, a.Ainv, a.ainv_t, a.nc, (const V*)L.r, (RP*)L.z, a.rc);
     const V* r = (const V*)L.r;
     const RP* z = (const RP*)L.z;
+    const int npad = (int)L.npad;
     V acc = 0;
-    for (int c = threadIdx.x; c < (int)L.npad; c += blockDim.x) acc += r[c] * (V)z[c];
+    for (int c = threadIdx.x; c < npad; c += blockDim.x) acc += r[c] * (V)z[c];
     return tm.sum<V>(acc);
   }
   // p = z + beta p, q = A p, alpha = rho / p.q, x += alpha p, r -= alpha q.
@@ -469,12 +570,14 @@ struct Ops {
     V* p = (V*)L.p;
     V* q = (V*)L.q;
     const RP* z = (const RP*)L.z;
-    for (int c = threadIdx.x; c < (int)L.npad; c += blockDim.x) p[c] = first ? (V)z[c] : (V)z[c] + beta * p[c];
+    const Geo G = geo_of(L);
+    const int npad = (int)G.npad;
+    for (int c = threadIdx.x; c < npad; c += blockDim.x) p[c] = first ? (V)z[c] : (V)z[c] + beta * p[c];
     tm.sync();
     const V *Tx = Tvec<V>(L, 0), *Ty = Tvec<V>(L, 1), *Tz = DIM == 3 ? Tvec<V>(L, 2) : nullptr;
     V acc = 0;
-    for_cells<DIM>(team_map(L.nx), L, [&](int i, const Row& rw) {
-      const V v = apply_value<DIM, V, V>(L, Tx, Ty, Tz, p, i, rw);
+    for_cells<DIM>(team_map(G.nx), G, [&](int i, const Row& rw) {
+      const V v = apply_value<DIM, V, V>(G, Tx, Ty, Tz, p, i, rw);
       q[rw.pc + i] = v;
       acc += p[rw.pc + i] * v;
     });
@@ -484,7 +587,7 @@ struct Ops {
     V* x = (V*)L.x;
     V* r = (V*)L.r;
     V acc2 = 0;
-    for (int c = threadIdx.x; c < (int)L.npad; c += blockDim.x) {
+    for (int c = threadIdx.x; c < npad; c += blockDim.x) {
       x[c] += alpha * p[c];
       const V rv = r[c] - alpha * q[c];
       r[c] = rv;
@@ -495,11 +598,11 @@ struct Ops {
   }
   // one CG step and the level test; returns 0 = continue, 1 = converged,
   // 2 = breakdown
-  static __device__ int iterate(BlockTeam& tm, const DevLevel& L, LvlCtl& c, SolveState* S, int k) {
+  static __device__ int iterate(BlockTeam& tm, const DevLevel& L, LvlCtl& c, SolveState* S, const RecArgs& a, int k) {
     V rr;
     if (!cg_step(tm, L, c, rr)) return 2;
     if (threadIdx.x == 0) {
-      S->lv[k].iters++;
+      a.iters[k]++;
       if (k == 0) S->lv[0].rr = (double)rr;
     }
     return Scal<V>::below(c, rr) ? 1 : 0;
@@ -520,18 +623,28 @@ __device__ void recursion(BlockTeam& tm, const DevLevel* sL, int ks, const RecAr
     LvlCtl& c = ct[k];
     const bool dbl = a.top_double && k == 0;
     if (c.phase == kStart) {
-      if (threadIdx.x == 0) S->lv[k].calls++;
-      const double bb = dbl ? (double)Ops<DIM, double, RP>::enter(tm, L) : (double)Ops<DIM, RP, RP>::enter(tm, L);
-      if (!(bb > 0.0)) {
+      if (threadIdx.x == 0) a.calls[k]++;
+      // level test of Sec. 3: ||r||^2 / N_k < f^k eps^2, kept as
+      // ||r||^2 < f^k eps^2 N_k (thrN, precomputed per level); inner levels
+      // may also stop at a floor relative to ||b_k||.  FP32 levels do this in
+      // FP32 (FP64 only when the threshold leaves the normal FP32 range).
+      bool live;
+      if (dbl || sizeof(RP) == sizeof(double)) {
+        const double bb = dbl ? (double)Ops<DIM, double, RP>::enter(tm, L) : (double)Ops<DIM, RP, RP>::enter(tm, L);
+        live = bb > 0.0;
+        c.thrN_d = a.thrN_d[k];
+        if (k > 0 && a.floor2 > 0.0) c.thrN_d = fmax(c.thrN_d, a.floor2 * bb);
+        c.thrN_f = (float)c.thrN_d;
+      } else {
+        const float bb = (float)Ops<DIM, RP, RP>::enter(tm, L);
+        live = bb > 0.f;
+        c.thrN_f = fmaxf(a.thrN_f[k], a.floor2_f * bb);
+        if (!(c.thrN_f > 1e-30f)) c.thrN_d = fmax(a.thrN_d[k], a.floor2 * (double)bb);
+      }
+      if (!live) {
         c.phase = kReturn;
         continue;
       }
-      // level test of Sec. 3: ||r||^2 / N_k < f^k eps^2 (inner levels may
-      // also stop at a floor relative to ||b_k||)
-      double thr = L.fk * a.eps2;
-      if (k > 0 && a.floor2 > 0.0) thr = fmax(thr, a.floor2 * bb / (double)L.n);
-      c.thrN_d = thr * (double)L.n;
-      c.thrN_f = (float)c.thrN_d;
       c.it = 0;
       c.rho_old_d = 0.0;
       c.rho_old_f = 0.f;
@@ -553,7 +666,7 @@ __device__ void recursion(BlockTeam& tm, const DevLevel* sL, int ks, const RecAr
       else Scal<RP>::rho(c) = Ops<DIM, RP, RP>::prolong_postsmooth(tm, L, sL[k + 1], a.m);
       c.phase = kPrecondDone;
     } else if (c.phase == kPrecondDone) {
-      const int st = dbl ? Ops<DIM, double, RP>::iterate(tm, L, c, S, k) : Ops<DIM, RP, RP>::iterate(tm, L, c, S, k);
+      const int st = dbl ? Ops<DIM, double, RP>::iterate(tm, L, c, S, a, k) : Ops<DIM, RP, RP>::iterate(tm, L, c, S, a, k);
       c.it++;
       if (st == 2) {
         if (threadIdx.x == 0) atomicOr(&S->status, kStBreakdown);
@@ -596,9 +709,9 @@ __host__ __device__ __forceinline__ size_t level_smem_bytes(const DevLevel& L, s
 // and copy their transmissibilities.  Returns the first level placed.
 template <int DIM, typename RP>
 __device__ int place_levels(DevLevel* sL, const DevLevel* gL, int lo, int kmax, bool top_double, unsigned char* dsm,
-                            size_t budget) {
+                            size_t budget, size_t* used) {
   __shared__ int s_ksm;
-  __shared__ size_t s_vec_bytes;
+  __shared__ size_t s_vec_bytes, s_used;
   if (threadIdx.x == 0) {
     size_t off = 0;
     int ksm = kmax + 1;
@@ -642,9 +755,11 @@ __device__ int place_levels(DevLevel* sL, const DevLevel* gL, int lo, int kmax, 
       }
     }
     s_ksm = ksm;
+    s_used = off;
   }
   __syncthreads();
   const int ksm = s_ksm;
+  *used = s_used;
   for (size_t e = threadIdx.x; e < s_vec_bytes / 16; e += blockDim.x) ((float4*)dsm)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int k = ksm; k <= kmax; ++k) {
     for (int ax = 0; ax < DIM; ++ax) {
@@ -679,6 +794,9 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small(const ProblemDesc* _
   __shared__ double shd[64];
   __shared__ float shf[64];
   __shared__ double s_rc[kMaxCoarse];
+  __shared__ double s_thrN_d[kMaxLev];
+  __shared__ float s_thrN_f[kMaxLev];
+  __shared__ long long s_iters[kMaxLev], s_calls[kMaxLev];
   __shared__ int s_pid;
   for (int round = 0;; ++round) {
     if (threadIdx.x == 0) s_pid = mode == 1 ? atomicAdd(next, 1) : (round == 0 && blockIdx.x == 0 ? 0 : nprob);
@@ -694,16 +812,37 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small(const ProblemDesc* _
     const int kmax = pd.nlev - 1;
     const bool full = mode != 0;
     const int lo = full ? 0 : ks;
-    place_levels<DIM, RP>(sL, pd.L, lo, kmax, full, dsm, smem_budget);
+    size_t used = 0;
+    place_levels<DIM, RP>(sL, pd.L, lo, kmax, full, dsm, smem_budget, &used);
     RecArgs a;
     a.kmax = kmax;
     a.m = pd.m;
     a.nc = pd.nc;
     a.Ainv = pd.Ainv;
+    a.ainv_t = false;
+    {
+      // the coarsest inverse, transposed, into shared memory when it fits
+      const size_t need = sizeof(double) * (size_t)pd.nc * pd.nc;
+      if (used + need <= smem_budget) {
+        double* dst = (double*)(dsm + used);
+        for (int e = threadIdx.x; e < pd.nc * pd.nc; e += blockDim.x) {
+          const int c = e / pd.nc, j = e - c * pd.nc;
+          dst[j * pd.nc + c] = pd.Ainv[e];
+        }
+        a.Ainv = dst;
+        a.ainv_t = true;
+        __syncthreads();
+      }
+    }
     a.floor2 = S->inner_floor2;
+    a.floor2_f = (float)a.floor2;
     a.S = S;
     a.top_double = full;
     a.rc = s_rc;
+    a.thrN_d = s_thrN_d;
+    a.thrN_f = s_thrN_f;
+    a.iters = s_iters;
+    a.calls = s_calls;
     BlockTeam bt;
     bt.shd = shd;
     bt.shf = shf;
@@ -717,7 +856,9 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small(const ProblemDesc* _
         for (int c = threadIdx.x; c < (int)G.npad; c += blockDim.x) sr[c] = gr[c];
       __syncthreads();
       a.eps2 = S->eps2;
+      level_consts(sL, pd.nlev, a.eps2, s_thrN_d, s_thrN_f, s_iters, s_calls);
       recursion<DIM, RP>(bt, sL, ks, a);
+      flush_counts(S, pd.nlev, s_iters, s_calls);
       RP* gx = (RP*)G.x;
       const RP* sx = (const RP*)sL[ks].x;
       if (sx != gx)
@@ -754,6 +895,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small(const ProblemDesc* _
     }
     __syncthreads();
     a.eps2 = eps2;
+    level_consts(sL, pd.nlev, eps2, s_thrN_d, s_thrN_f, s_iters, s_calls);
     if (bb > 0.0 && isfinite(bb)) {
       for (int pass = 0; pass < 4; ++pass) {
         recursion<DIM, RP>(bt, sL, 0, a);
@@ -773,6 +915,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small(const ProblemDesc* _
         if (S->status != 0 || rt < pd.tol * pd.tol * bb) break;
       }
     }
+    flush_counts(S, pd.nlev, s_iters, s_calls);
     for_cells<DIM>(team_map(L0.nx), L0, [&](int i, const Row& rw) {
       pd.x[i + L0.nx * (rw.j + L0.ny * rw.k)] = xs[rw.pc + i];
     });
@@ -1351,6 +1494,8 @@ size_t levels_smem(const msrcg_hier* h, int lo, bool top_double) {
     if (tot + b > lim) break;
     tot += b;
   }
+  const size_t ainv = sizeof(double) * (size_t)h->nc * h->nc;
+  if (tot + ainv <= lim) tot += ainv;
   return tot;
 }
 
