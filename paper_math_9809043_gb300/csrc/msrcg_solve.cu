@@ -63,10 +63,10 @@ struct BlockTeam {
     par ^= 1;
     if ((threadIdx.x & 31) == 0) b[threadIdx.x >> 5] = v;
     __syncthreads();
-    T t = 0;
-    const int nw = blockDim.x >> 5;
-    for (int w = 0; w < nw; ++w) t += b[w];
-    return t;
+    // every warp folds the warp sums with the same butterfly, so all threads
+    // hold the identical total (a + b == b + a exactly at each stage)
+    const int lane = threadIdx.x & 31;
+    return warp_sum_t<T>(lane < (int)(blockDim.x >> 5) ? b[lane] : (T)0);
   }
 };
 
@@ -86,10 +86,10 @@ struct Map {
   int x0, dx, y0, dy;
 };
 
-// The CTA laid over rows of `width` columns: a power-of-two row width.
+// The CTA (a power-of-two number of threads) laid over rows of `width`
+// columns: a power-of-two row width, at most the CTA.
 __device__ __forceinline__ Map team_map(int width) {
-  int bx = 1;
-  while (bx < width && bx < (int)blockDim.x) bx <<= 1;
+  const int bx = width <= 1 ? 1 : min(1 << (32 - __clz(width - 1)), (int)blockDim.x);
   const int sh = __ffs(bx) - 1;
   Map m;
   m.x0 = threadIdx.x & (bx - 1);
@@ -123,11 +123,11 @@ struct Row {
 // every store to the level's vectors (it cannot rule out aliasing).
 struct Geo {
   int nx, ny, nz, px, py;
-  long long plane, off, npad, n;
+  int plane, off, npad, n;
 };
 struct Xf {
   int nx, ny, nz, px, py;
-  long long plane, off, npad, n;
+  int plane, off, npad, n;
   const int* c0[3];
   const int* c1[3];
   const void* w[3];
@@ -143,10 +143,10 @@ __device__ __forceinline__ Geo geo_of(const DevLevel& L) {
   g.nz = L.nz;
   g.px = L.px;
   g.py = L.py;
-  g.plane = L.plane;
-  g.off = L.off;
-  g.npad = L.npad;
-  g.n = L.n;
+  g.plane = (int)L.plane;
+  g.off = (int)L.off;
+  g.npad = (int)L.npad;
+  g.n = (int)L.n;
   return g;
 }
 __device__ __forceinline__ Xf xf_of(const DevLevel& L) {
@@ -156,10 +156,10 @@ __device__ __forceinline__ Xf xf_of(const DevLevel& L) {
   x.nz = L.nz;
   x.px = L.px;
   x.py = L.py;
-  x.plane = L.plane;
-  x.off = L.off;
-  x.npad = L.npad;
-  x.n = L.n;
+  x.plane = (int)L.plane;
+  x.off = (int)L.off;
+  x.npad = (int)L.npad;
+  x.n = (int)L.n;
   for (int a = 0; a < 3; ++a) {
     x.c0[a] = L.c0[a];
     x.c1[a] = L.c1[a];
@@ -188,14 +188,15 @@ __device__ __forceinline__ Row make_row(const LV& L, int row) {
   return r;
 }
 
-// Visit every cell of the level: f(i, row).
+// Visit every cell of the level: f(i, row).  A thread walks its column
+// through all of its rows before taking its next column (measured faster for
+// the single-CTA solver, where a thread holds two or more columns of the
+// widest levels).
 template <int DIM, class LV, class F>
 __device__ __forceinline__ void for_cells(const Map& m, const LV& L, F&& f) {
   const int rows = L.ny * L.nz;
-  for (int row = m.y0; row < rows; row += m.dy) {
-    const Row r = make_row<DIM>(L, row);
-    for (int i = m.x0; i < L.nx; i += m.dx) f(i, r);
-  }
+  for (int i = m.x0; i < L.nx; i += m.dx)
+    for (int row = m.y0; row < rows; row += m.dy) f(i, make_row<DIM>(L, row));
 }
 
 // Visit the cells of one colour ((i + j + k) & 1 == colour): in a row they
@@ -205,11 +206,12 @@ template <int DIM, class LV, class F>
 __device__ __forceinline__ void for_colour(const Map& m, const LV& L, int colour, F&& f) {
   const int rows = L.ny * L.nz;
   const int hx = (L.nx + 1) >> 1;
-  for (int row = m.y0; row < rows; row += m.dy) {
-    const Row r = make_row<DIM>(L, row);
-    const int s = (r.j + r.k + colour) & 1;
-    for (int ii = m.x0; ii < hx; ii += m.dx) f(2 * ii + s, 2 * ii + (s ^ 1), r);
-  }
+  for (int ii = m.x0; ii < hx; ii += m.dx)
+    for (int row = m.y0; row < rows; row += m.dy) {
+      const Row r = make_row<DIM>(L, row);
+      const int s = (r.j + r.k + colour) & 1;
+      f(2 * ii + s, 2 * ii + (s ^ 1), r);
+    }
 }
 
 template <typename R>
@@ -355,13 +357,33 @@ __device__ __forceinline__ R prolong_value(const FX& F, const CV& C, const R* xc
 //        (r in the level's vector type; the other colour is final already).
 enum : int { kNormal = 0, kZero = 1, kDot = 2 };
 
+// A level's geometry, smoother-precision transmissibilities and the CTA's
+// thread maps over all cells and over one colour, formed once for a run of
+// phases on the level.
+template <typename RP>
+struct TLevel {
+  Geo G;
+  const RP *Tx, *Ty, *Tz;
+  Map all, col;
+};
+template <typename RP>
+__device__ __forceinline__ TLevel<RP> tlevel_of(const DevLevel& L) {
+  TLevel<RP> t;
+  t.G = geo_of(L);
+  t.Tx = (const RP*)L.T[0];
+  t.Ty = (const RP*)L.T[1];
+  t.Tz = (const RP*)L.T[2];
+  t.all = team_map(t.G.nx);
+  t.col = team_map((t.G.nx + 1) >> 1);
+  return t;
+}
+
 template <int DIM, typename RP, typename V>
-__device__ __forceinline__ V t_sweep(const DevLevel& L, int colour, const V* r, RP* rp, RP* z, int mode) {
-  const RP *Tx = (const RP*)L.T[0], *Ty = (const RP*)L.T[1], *Tz = (const RP*)L.T[2];
-  const Geo G = geo_of(L);
+__device__ __forceinline__ V t_sweep(const TLevel<RP>& S, int colour, const V* r, RP* rp, RP* z, int mode) {
+  const Geo& G = S.G;
   V acc = 0;
   if (mode == kZero) {
-    for_cells<DIM>(team_map(G.nx), G, [&](int i, const Row& rw) {
+    for_cells<DIM>(S.all, G, [&](int i, const Row& rw) {
       const int pc = rw.pc + i;
       RP rhs;
       if (sizeof(V) != sizeof(RP)) {
@@ -370,18 +392,20 @@ __device__ __forceinline__ V t_sweep(const DevLevel& L, int colour, const V* r, 
       } else {
         rhs = rp[pc];
       }
-      z[pc] = ((i + rw.j + rw.k) & 1) == colour ? quot<RP>(rhs, diag_of<DIM, RP>(G, Tx, Ty, Tz, i, rw)) : (RP)0;
+      z[pc] = ((i + rw.j + rw.k) & 1) == colour ? quot<RP>(rhs, diag_of<DIM, RP>(G, S.Tx, S.Ty, S.Tz, i, rw)) : (RP)0;
     });
   } else {
     const bool dot = mode == kDot;
-    for_colour<DIM>(team_map((G.nx + 1) >> 1), G, colour, [&](int i, int i2, const Row& rw) {
+    // every load of a cell comes before its store: the compiler cannot
+    // move a load past a store it might alias
+    for_colour<DIM>(S.col, G, colour, [&](int i, int i2, const Row& rw) {
       const int base = rw.pc;
-      if (i < G.nx) {
-        const RP v = gs_value<DIM, RP, RP>(G, Tx, Ty, Tz, rp[base + i], z, i, rw);
-        z[base + i] = v;
-        if (dot) acc += r[base + i] * (V)v;
-      }
       if (dot && i2 < G.nx) acc += r[base + i2] * (V)z[base + i2];
+      if (i < G.nx) {
+        const RP v = gs_value<DIM, RP, RP>(G, S.Tx, S.Ty, S.Tz, rp[base + i], z, i, rw);
+        if (dot) acc += r[base + i] * (V)v;
+        z[base + i] = v;
+      }
     });
   }
   return acc;
@@ -392,17 +416,17 @@ __device__ __forceinline__ V t_sweep(const DevLevel& L, int colour, const V* r, 
 // reproduces the same values, so m steps are the 2m+1 half-sweeps
 // red (black red)^m.  Returns r . z after the last half-sweep when `dot`.
 template <int DIM, typename RP, typename V>
-__device__ V t_smooth(BlockTeam& tm, const DevLevel& L, int m, bool from_zero, bool dot) {
+__device__ V t_smooth(BlockTeam& tm, const DevLevel& L, const TLevel<RP>& S, int m, bool from_zero, bool dot) {
   const V* r = (const V*)L.r;
   RP* rp = (RP*)L.rp;
   RP* z = (RP*)L.z;
-  t_sweep<DIM, RP, V>(L, 0, r, rp, z, from_zero ? kZero : kNormal);
+  t_sweep<DIM, RP, V>(S, 0, r, rp, z, from_zero ? kZero : kNormal);
   tm.sync();
   for (int s = 0; s < m; ++s) {
-    t_sweep<DIM, RP, V>(L, 1, r, rp, z, kNormal);
+    t_sweep<DIM, RP, V>(S, 1, r, rp, z, kNormal);
     tm.sync();
     const bool last = s == m - 1;
-    const V d = t_sweep<DIM, RP, V>(L, 0, r, rp, z, dot && last ? kDot : kNormal);
+    const V d = t_sweep<DIM, RP, V>(S, 0, r, rp, z, dot && last ? kDot : kNormal);
     if (dot && last) return tm.sum<V>(d);
     tm.sync();
   }
@@ -514,25 +538,27 @@ struct Ops {
     const int npad = (int)L.npad;
     V acc = 0;
     for (int c = threadIdx.x; c < npad; c += blockDim.x) {
+      const V rv = r[c];
+      acc += rv * rv;
       x[c] = 0;
-      acc += r[c] * r[c];
     }
     return tm.sum<V>(acc);
   }
   // pre-smoothing from zero, t = r - A z, r_{k+1} = R t
   static __device__ void presmooth_restrict(BlockTeam& tm, const DevLevel& L, const DevLevel& C, int m) {
-    t_smooth<DIM, RP, V>(tm, L, m, true, false);
+    const TLevel<RP> S = tlevel_of<RP>(L);
+    t_smooth<DIM, RP, V>(tm, L, S, m, true, false);
     const RP* rp = (const RP*)L.rp;
     const RP* z = (const RP*)L.z;
     RP* t = (RP*)L.t;
-    const RP *Tx = (const RP*)L.T[0], *Ty = (const RP*)L.T[1], *Tz = (const RP*)L.T[2];
-    const Geo G = geo_of(L), Gc = geo_of(C);
-    for_cells<DIM>(team_map(G.nx), G, [&](int i, const Row& rw) {
-      t[rw.pc + i] = rp[rw.pc + i] - apply_value<DIM, RP, RP>(G, Tx, Ty, Tz, z, i, rw);
+    const Geo& G = S.G;
+    for_cells<DIM>(S.all, G, [&](int i, const Row& rw) {
+      t[rw.pc + i] = rp[rw.pc + i] - apply_value<DIM, RP, RP>(G, S.Tx, S.Ty, S.Tz, z, i, rw);
     });
     tm.sync();
     RP* rc = (RP*)C.r;
     const Xf X = xf_of(L);
+    const Geo Gc = geo_of(C);
     for_cells<DIM>(team_map(Gc.nx), Gc, [&](int i, const Row& rw) {
       rc[rw.pc + i] = restrict_value<DIM, RP>(X, t, i, rw.j, rw.k);
     });
@@ -542,15 +568,17 @@ struct Ops {
   // recomputes every red cell from its black neighbours, so a red cell's
   // prolonged value would never be read.  Then post-smoothing; returns r.z.
   static __device__ V prolong_postsmooth(BlockTeam& tm, const DevLevel& L, const DevLevel& C, int m) {
-    RP* z = (RP*)L.z;
-    const RP* xc = (const RP*)C.x;
-    const Xf X = xf_of(L);
-    const Geo Gc = geo_of(C);
-    for_colour<DIM>(team_map((X.nx + 1) >> 1), X, 1, [&](int i, int, const Row& rw) {
-      if (i < X.nx) z[rw.pc + i] += prolong_value<DIM, RP>(X, Gc, xc, i, rw.j, rw.k);
-    });
+    {
+      RP* z = (RP*)L.z;
+      const RP* xc = (const RP*)C.x;
+      const Xf X = xf_of(L);
+      const Geo Gc = geo_of(C);
+      for_colour<DIM>(team_map((X.nx + 1) >> 1), X, 1, [&](int i, int, const Row& rw) {
+        if (i < X.nx) z[rw.pc + i] += prolong_value<DIM, RP>(X, Gc, xc, i, rw.j, rw.k);
+      });
+    }
     tm.sync();
-    return t_smooth<DIM, RP, V>(tm, L, m, false, true);
+    return t_smooth<DIM, RP, V>(tm, L, tlevel_of<RP>(L), m, false, true);
   }
   static __device__ V coarsest(BlockTeam& tm, const DevLevel& L, const RecArgs& a) {
     t_coarsest<DIM, V, RP>(tm, L, a.Ainv, a.ainv_t, a.nc, (const V*)L.r, (RP*)L.z, a.rc);
@@ -571,15 +599,15 @@ struct Ops {
     V* q = (V*)L.q;
     const RP* z = (const RP*)L.z;
     const Geo G = geo_of(L);
-    const int npad = (int)G.npad;
+    const int npad = G.npad;
     for (int c = threadIdx.x; c < npad; c += blockDim.x) p[c] = first ? (V)z[c] : (V)z[c] + beta * p[c];
     tm.sync();
     const V *Tx = Tvec<V>(L, 0), *Ty = Tvec<V>(L, 1), *Tz = DIM == 3 ? Tvec<V>(L, 2) : nullptr;
     V acc = 0;
     for_cells<DIM>(team_map(G.nx), G, [&](int i, const Row& rw) {
       const V v = apply_value<DIM, V, V>(G, Tx, Ty, Tz, p, i, rw);
-      q[rw.pc + i] = v;
       acc += p[rw.pc + i] * v;
+      q[rw.pc + i] = v;
     });
     const V pq = tm.sum<V>(acc);
     if (!(pq > (V)0) || !isfinite(pq) || !isfinite(rho)) return false;
@@ -588,10 +616,11 @@ struct Ops {
     V* r = (V*)L.r;
     V acc2 = 0;
     for (int c = threadIdx.x; c < npad; c += blockDim.x) {
-      x[c] += alpha * p[c];
+      const V xv = x[c] + alpha * p[c];
       const V rv = r[c] - alpha * q[c];
-      r[c] = rv;
       acc2 += rv * rv;
+      x[c] = xv;
+      r[c] = rv;
     }
     rr_out = tm.sum<V>(acc2);
     return true;
@@ -1062,12 +1091,12 @@ __global__ void k_sweep_rho(DevLevel L, int k, SolveState* S, double* partials) 
   RP* z = (RP*)L.z;
   V acc = 0;
   for_colour<DIM>(grid_map(), L, 0, [&](int i, int i2, const Row& rw) {
+    if (i2 < L.nx) acc += r[rw.pc + i2] * (V)z[rw.pc + i2];
     if (i < L.nx) {
       const RP v = gs_value<DIM, RP, RP>(L, Tx, Ty, Tz, rp[rw.pc + i], z, i, rw);
-      z[rw.pc + i] = v;
       acc += r[rw.pc + i] * (V)v;
+      z[rw.pc + i] = v;
     }
-    if (i2 < L.nx) acc += r[rw.pc + i2] * (V)z[rw.pc + i2];
   });
   grid_total(acc, partials, &S->ticket[k], [&](double rho) {
     LevelState& ls = S->lv[k];
@@ -1092,11 +1121,8 @@ template <int DIM, typename RP>
 __global__ void k_restrict(DevLevel L, DevLevel C) {
   const RP* t = (const RP*)L.t;
   RP* rc = (RP*)C.r;
-  for_cells<DIM>(grid_map(), C, [&](int i, const Row& rw) {
-      const int pc = rw.pc + i;
-      const int j = rw.j, k = rw.k;
-      (void)j;
-      (void)k; rc[pc] = restrict_value<DIM, RP>(L, t, i, j, k); });
+  for_cells<DIM>(grid_map(), C,
+                 [&](int i, const Row& rw) { rc[rw.pc + i] = restrict_value<DIM, RP>(L, t, i, rw.j, rw.k); });
 }
 
 // z += E x_c on the black cells (see Ops::prolong_postsmooth)
@@ -1105,11 +1131,7 @@ __global__ void k_prolong_black(DevLevel L, DevLevel C) {
   const RP* xc = (const RP*)C.x;
   RP* z = (RP*)L.z;
   for_colour<DIM>(grid_map(), L, 1, [&](int i, int, const Row& rw) {
-      const int base = rw.pc;
-      const int j = rw.j, k = rw.k;
-      (void)j;
-      (void)k;
-    if (i < L.nx) z[base + i] += prolong_value<DIM, RP>(L, C, xc, i, j, k);
+    if (i < L.nx) z[rw.pc + i] += prolong_value<DIM, RP>(L, C, xc, i, rw.j, rw.k);
   });
 }
 
@@ -1136,8 +1158,8 @@ __global__ void k_apply_dot(DevLevel L, int k, SolveState* S, double* partials) 
   V acc = 0;
   for_cells<DIM>(grid_map(), L, [&](int i, const Row& rw) {
     const V v = apply_value<DIM, V, V>(L, Tx, Ty, Tz, p, i, rw);
-    q[rw.pc + i] = v;
     acc += p[rw.pc + i] * v;
+    q[rw.pc + i] = v;
   });
   grid_total(acc, partials, &S->ticket[k], [&](double pq) {
     LevelState& ls = S->lv[k];
@@ -1168,10 +1190,11 @@ __global__ void k_update(DevLevel L, int k, SolveState* S, double* partials, cud
   V acc = 0;
   const int n = (int)L.npad;
   for (int c = (int)lin_tid(); c < n; c += (int)lin_stride()) {
-    x[c] += alpha * p[c];
+    const V xv = x[c] + alpha * p[c];
     const V rv = r[c] - alpha * q[c];
-    r[c] = rv;
     acc += rv * rv;
+    x[c] = xv;
+    r[c] = rv;
   }
   grid_total(acc, partials, &S->ticket[k], [&](double rr) {
     LevelState& w = S->lv[k];
