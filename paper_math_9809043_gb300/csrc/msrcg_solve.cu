@@ -457,6 +457,51 @@ __device__ void t_coarsest(BlockTeam& tm, const DevLevel& L, const double* Ainv,
   tm.sync();
 }
 
+// r_{k+1} = R t by the CTA (the gather of restrict_value): G threads per
+// coarse cell, G a power of two up to 8 chosen so the coarse cells cover
+// the CTA, each taking every G-th fine row of the cell's window; the group
+// then adds its partial sums with shuffles.  The loop over coarse cells has
+// the same trip count in every thread, so every lane reaches the shuffles.
+template <int DIM, typename R>
+__device__ void t_restrict(const Xf& F, const Geo& Gc, const R* t, R* rc) {
+  const int nc = Gc.nx * Gc.ny * Gc.nz;
+  int lg = 0;
+  while (lg < 3 && (nc << (lg + 1)) <= (int)blockDim.x) ++lg;
+  const int G = 1 << lg, member = threadIdx.x & (G - 1), per = blockDim.x >> lg;
+  for (int base = 0; base < nc; base += per) {
+    const int cell = base + ((int)threadIdx.x >> lg);
+    R part = 0;
+    int pc = 0;
+    if (cell < nc) {
+      const int I = cell % Gc.nx, rest = cell / Gc.nx, J = rest % Gc.ny, K = rest / Gc.ny;
+      pc = Gc.off + I + Gc.px * J + Gc.plane * K;
+      const R* rwx = (const R*)F.rw[0] + I * F.W[0];
+      const R* rwy = (const R*)F.rw[1] + J * F.W[1];
+      const int ilo = __ldg(F.lo[0] + I), ihi = __ldg(F.hi[0] + I), jlo = __ldg(F.lo[1] + J), jhi = __ldg(F.hi[1] + J);
+      int klo = 0, khi = 0;
+      const R* rwz = nullptr;
+      if (DIM == 3) {
+        klo = __ldg(F.lo[2] + K);
+        khi = __ldg(F.hi[2] + K);
+        rwz = (const R*)F.rw[2] + K * F.W[2];
+      }
+      for (int kk = klo; kk <= khi; ++kk) {
+        R accy = 0;
+        for (int jj = jlo + member; jj <= jhi; jj += G) {
+          const R* row = t + (F.off + F.px * jj + F.plane * kk);
+          R accx = 0;
+#pragma unroll 4
+          for (int ii = ilo; ii <= ihi; ++ii) accx += __ldg(rwx + (ii - ilo)) * row[ii];
+          accy += __ldg(rwy + (jj - jlo)) * accx;
+        }
+        part += (DIM == 3 ? __ldg(rwz + (kk - klo)) : (R)1) * accy;
+      }
+    }
+    for (int o = G >> 1; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (cell < nc && member == 0) rc[pc] = part;
+  }
+}
+
 // Control of one level of the single-CTA state machine.  Scalars are kept
 // in both precisions so that an FP32 level never converts.
 struct LvlCtl {
@@ -556,12 +601,7 @@ struct Ops {
       t[rw.pc + i] = rp[rw.pc + i] - apply_value<DIM, RP, RP>(G, S.Tx, S.Ty, S.Tz, z, i, rw);
     });
     tm.sync();
-    RP* rc = (RP*)C.r;
-    const Xf X = xf_of(L);
-    const Geo Gc = geo_of(C);
-    for_cells<DIM>(team_map(Gc.nx), Gc, [&](int i, const Row& rw) {
-      rc[rw.pc + i] = restrict_value<DIM, RP>(X, t, i, rw.j, rw.k);
-    });
+    t_restrict<DIM, RP>(xf_of(L), geo_of(C), t, (RP*)C.r);
     tm.sync();
   }
   // z += E x_c on the black cells only: the first post-smoothing half-sweep
