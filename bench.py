@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the uneven-batch and 3D sections")
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="length of the arrival stream")
     return ap.parse_args()
 
@@ -255,6 +256,82 @@ def run_serving(args, M, P, dev):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def _timed_batch(M, hs, bs, steps, stream, dev):
+    import torch
+    M.batch_solve(hs, bs, TOL, stream=stream)
+    torch.cuda.synchronize(dev)
+    per, sts = [], None
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, sts = M.batch_solve(hs, bs, TOL, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        per.append(e0.elapsed_time(e1))
+    return per, sts
+
+
+def run_uneven(args, M, P, dev, stream):
+    """256 independent 2D problems of sides 64..512 (GRF, 1e6 contrast, N(0,1)
+    right-hand sides) in one persistent launch; both precisions."""
+    import torch
+    probs = P.batch_problems(256)
+    ncell = sum(p.N for p in probs)
+    out = {"workload": "256 2D problems, side U{64,96,128,192,256,384,512}, GRF corr. 8 cells, 1e6 contrast",
+           "unknowns": ncell}
+    for prec, key in ((1, "fp32_precond"), (0, "fp64_plain")):
+        if prec == 0 and args.no_fp64:
+            continue
+        opts = M.default_opts(precision=prec, inner_floor=1e-6 if prec else 0.0)
+        hs = [M.Hierarchy.from_problem(p, opts, device=dev) for p in probs]
+        bs = [h.rhs_for(p) for h, p in zip(hs, probs)]
+        per, sts = _timed_batch(M, hs, bs, 3 if prec else 2, stream, dev)
+        ms = statistics.mean(per)
+        out[key] = {"solves_per_s": 256 / (ms / 1e3), "unknowns_per_s": ncell / (ms / 1e3), "ms_per_batch": ms,
+                    "status": sorted({s["status"] for s in sts}), "relres_true_max": max(s["relres_true"] for s in sts)}
+        del hs, bs
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_3d(args, M, P, dev, stream, nb):
+    """128^3 7-point problems on a 3D Gaussian random field (1e9 contrast):
+    nb problems per launch with their own sources, and single-solve latency."""
+    import numpy as np
+    import torch
+    base = P.grf3d_problem(128)
+    out = {"workload": "3D 128^3 7-point, GRF corr. 8 cells, 1e9 contrast, N(0,1) source", "concurrent_solves": nb}
+    for prec, key in ((1, "fp32_precond"), (0, "fp64_plain")):
+        if prec == 0 and args.no_fp64:
+            continue
+        opts = M.default_opts(precision=prec, inner_floor=1e-6 if prec else 0.0)
+        hs, bs = [], []
+        for j in range(nb):
+            rng = np.random.default_rng(1002 * 1000 + j)
+            prob = P.Problem(dim=3, n=base.n, h=base.h, K=base.K, bc=base.bc, gD=base.gD,
+                             f=rng.standard_normal(base.N), pbf=base.pbf)
+            h = M.Hierarchy.from_problem(prob, opts, device=dev)
+            hs.append(h)
+            bs.append(h.rhs_for(prob))
+        per, sts = _timed_batch(M, hs, bs, 2, stream, dev)
+        ms = statistics.mean(per)
+        lat = []
+        hs[0].solve(bs[0], TOL, stats=False, stream=stream)
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            hs[0].solve(bs[0], TOL, stats=False, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            lat.append(e0.elapsed_time(e1))
+        out[key] = {"solves_per_s": nb / (ms / 1e3), "ms_per_batch": ms, "single_solve_ms": min(lat),
+                    "iters": sts[0]["iters"], "status": sorted({s["status"] for s in sts}),
+                    "relres_true_max": max(s["relres_true"] for s in sts)}
+        del hs, bs
+        torch.cuda.empty_cache()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -404,6 +481,12 @@ def main():
         del hs, bs, xs
         torch.cuda.empty_cache()
 
+    # ---- other workloads: uneven batch and 3D (rank 0 only) ----
+    uneven = grid3d = None
+    if rank == 0 and not args.no_extra:
+        uneven = run_uneven(args, M, P, dev, stream)
+        grid3d = run_3d(args, M, P, dev, stream, nb)
+
     # ---- serving: Poisson arrivals of mixed requests (rank 0 only) ----
     serving = None
     if rank == 0 and not args.no_serve:
@@ -434,7 +517,8 @@ def main():
                            "l2": "inputs larger than L2 (each problem's hierarchy ~70 MB resident in HBM)",
                            "parallelism": f"independent problems, {world} GPU(s)"},
                 "status": statuses, "relres_true_max": relres, "iters": sts[0]["iters"],
-                "latency_ms": latency, "fp64_plain": fp64, "serving": serving, "e2e": e2e, "roofline": roofline,
+                "latency_ms": latency, "fp64_plain": fp64, "uneven_batch": uneven, "grid3d": grid3d,
+                "serving": serving, "e2e": e2e, "roofline": roofline,
                 "cpu_baseline": cpu, "clocks": ck, "gpu_launches": args.steps}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -141,6 +141,14 @@ def grf_problem(n=(1024, 1024), seed=1001, ell=16.0, half_span=4.5, source=True)
                    meta={"seed": seed, "ell": ell, "log10K": [-half_span, half_span]})
 
 
+def grf3d_problem(side: int = 128, seed: int = 1002) -> Problem:
+    """3D Gaussian random field of the 3D workload's size: log10 K with
+    correlation length 8 cells rescaled to [-4.5, 4.5] (1e9 contrast), N(0,1)
+    source, lifted BCs.  Stands beside the layered channel field, on which
+    the method does not converge at this size (oracle and GPU alike)."""
+    return grf_problem((side, side, side), seed=seed, ell=8.0, half_span=4.5)
+
+
 def channel_problem(n=(128, 128, 128), seed=1002, slab=4, k_lo=1e-9, k_hi=1.0,
                     max_channels=4, wmin=2, wmax=8) -> Problem:
     """Layered 3D channel field.

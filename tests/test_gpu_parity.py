@@ -160,6 +160,45 @@ def test_full_size_1024_matches_oracle(M, prec):
         _counts_close(st["iters"], sr["iters"], sr["calls"])
 
 
+_ORACLE_CACHE = {}
+
+
+def _oracle_solution(key, prob):
+    if key not in _ORACLE_CACHE:
+        R = O.Hierarchy(prob)
+        _ORACLE_CACHE[key] = R.solve(R.lift_rhs(), 1e-8)
+    return _ORACLE_CACHE[key]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_full_size_3d_grf_matches_oracle(M, prec):
+    """128^3 Gaussian random field (1e9 contrast): the 3D workload's size on a
+    field where the method converges (the layered channel field of that size
+    stalls in the oracle as well)."""
+    prob = P.grf3d_problem(128)
+    H = M.Hierarchy.from_problem(prob, M.default_opts(precision=prec, inner_floor=1e-6 if prec else 0.0))
+    x, st = H.solve(H.rhs_for(prob), 1e-8)
+    xr, sr = _oracle_solution("grf3d-128", prob)
+    assert st["status"] == 0 and st["relres_true"] < 1e-8, st
+    err = np.linalg.norm(x.cpu().numpy() - xr) / np.linalg.norm(xr)
+    assert err <= SOL_RTOL, err
+    if prec == 0:
+        _counts_close(st["iters"], sr["iters"], sr["calls"])
+
+
+def test_channel_3d_32_fp64_matches_oracle(M):
+    """The layered channel field at 32^3, where the FP64 method still
+    converges (about 190 outer iterations in both implementations)."""
+    prob = P.config_problem(2, scale=32)
+    H = M.Hierarchy.from_problem(prob, M.default_opts(precision=0))
+    x, st = H.solve(H.rhs_for(prob), 1e-8)
+    xr, sr = _oracle_solution("chan-32", prob)
+    assert st["status"] == 0 and st["relres_true"] < 1e-8, st
+    err = np.linalg.norm(x.cpu().numpy() - xr) / np.linalg.norm(xr)
+    assert err <= SOL_RTOL, err
+    _counts_close(st["iters"], sr["iters"], sr["calls"])
+
+
 def test_repeat_solves_identical(M):
     """Deterministic reductions: two solves give the same bits."""
     prob = P.config_problem(1, scale=256)
@@ -220,3 +259,30 @@ def test_batch_matches_oracle(M, prec):
         assert err <= SOL_RTOL
         if prec == 0:
             _counts_close(st["iters"], sr["iters"], sr["calls"])
+
+
+
+def test_uneven_batch_full_size(M):
+    """The 256-problem uneven batch (sides 64..512) in one launch, FP32
+    preconditioner: every result's true residual, formed with the oracle's
+    operator, meets 1e-8 (to the rounding of that check); one problem per side
+    class matches the oracle's solution."""
+    probs = P.batch_problems(256)
+    opts = M.default_opts(precision=1, inner_floor=1e-6)
+    hs = [M.Hierarchy.from_problem(p, opts) for p in probs]
+    bs = [h.rhs_for(p) for h, p in zip(hs, probs)]
+    xs, sts = M.batch_solve(hs, bs, 1e-8)
+    for p, x, st in zip(probs, xs, sts):
+        assert st["status"] == 0, (p.name, st)
+        R = O.Hierarchy(p)
+        xv = x.cpu().numpy()
+        rel = np.linalg.norm(p.b - R.apply(0, xv)) / np.linalg.norm(p.b)
+        assert rel < 1.05e-8, (p.name, rel)
+    first = {}
+    for j, p in enumerate(probs):
+        first.setdefault(p.n[0], j)
+    for side, j in sorted(first.items()):
+        R = O.Hierarchy(probs[j])
+        xr, _ = R.solve(R.lift_rhs(), 1e-8)
+        err = np.linalg.norm(xs[j].cpu().numpy() - xr) / np.linalg.norm(xr)
+        assert err <= SOL_RTOL, (side, err)
