@@ -68,7 +68,11 @@ typedef struct {
   uint64_t timeout_ns;
   double inner_floor;
   int small_cells;   /* levels with at most this many cells run in one CTA; 0 = default */
-  int reserved[7];
+  int plain_sweeps;  /* 1: one pass over a level per red/black half-sweep everywhere; 0 (default):
+                        2D FP32-preconditioner levels in global memory that the single-CTA solver
+                        handles run all half-sweeps of one smoothing in a single pass over the
+                        level (same values, fewer memory passes) */
+  int reserved[6];
 } msrcg_opts;
 
 /* Per-solve statistics.  iters[k] = PCG iterations summed over all calls at

@@ -463,6 +463,7 @@ extern "C" int msrcg_default_opts(msrcg_opts* o) {
   o->timeout_ns = 2000000000ull;
   o->inner_floor = 0.0;
   o->small_cells = 0;
+  o->plain_sweeps = 0;
   return MSRCG_OK;
 }
 

@@ -103,6 +103,7 @@ struct ProblemDesc {
   double* xs;            // padded FP64 accumulator of the level-0 solution
   double tol;
   long long work;        // scheduling weight (cells of level 0)
+  int fuse;              // single-pass smoothing allowed on global-memory levels
 };
 
 }  // namespace msrcg

@@ -243,20 +243,38 @@ __device__ __forceinline__ R diag_of(const LV& L, const R* Tx, const R* Ty, cons
 // neighbours held, x_c = (rhs_c + sum_f T_f x_nb) / sum_f T_f  (Sec. 3); a
 // boundary face meets a zero ghost.  The FP32 smoother divides with the
 // fast hardware quotient; FP64 divides exactly.
+// The x/y part of a Gauss-Seidel value: d = sum of the four face T, s += the
+// four T x_nb terms, in this order.  Shared by every smoother so that all of
+// them round identically.
+template <typename R>
+__device__ __forceinline__ void gs_terms2(R& d, R& s, R tw, R te, R ts, R tn, R xw, R xe, R xs, R xn) {
+  d = tw;
+  d += te;
+  d += ts;
+  d += tn;
+  s += tw * xw;
+  s += te * xe;
+  s += ts * xs;
+  s += tn * xn;
+}
+
+// The x/y part of (A x)_c, in this order (shared like gs_terms2).
+template <typename R>
+__device__ __forceinline__ R apply_terms2(R tw, R te, R ts, R tn, R xc, R xw, R xe, R xs, R xn) {
+  R s = tw * (xc - xw);
+  s += te * (xc - xe);
+  s += ts * (xc - xs);
+  s += tn * (xc - xn);
+  return s;
+}
+
 template <int DIM, typename R, typename RX, class LV>
 __device__ __forceinline__ R gs_value(const LV& L, const R* Tx, const R* Ty, const R* Tz, R rhs, const RX* x,
                                       int i, const Row& r) {
   const int pc = r.pc + i;
   const R tw = Tx[r.fx + i], te = Tx[r.fx + i + 1], ts = Ty[r.fy + i], tn = Ty[r.fy + i + L.nx];
-  R d = tw;
-  d += te;
-  d += ts;
-  d += tn;
-  R s = rhs;
-  s += tw * (R)x[pc - 1];
-  s += te * (R)x[pc + 1];
-  s += ts * (R)x[pc - L.px];
-  s += tn * (R)x[pc + L.px];
+  R d, s = rhs;
+  gs_terms2<R>(d, s, tw, te, ts, tn, (R)x[pc - 1], (R)x[pc + 1], (R)x[pc - L.px], (R)x[pc + L.px]);
   if (DIM == 3) {
     const int pl = (int)L.plane;
     const R tb = Tz[r.fz + i], tt = Tz[r.fz + i + L.nx * L.ny];
@@ -274,10 +292,8 @@ __device__ __forceinline__ R apply_value(const LV& L, const R* Tx, const R* Ty, 
                                          const Row& r) {
   const int pc = r.pc + i;
   const R xc = (R)x[pc];
-  R s = Tx[r.fx + i] * (xc - (R)x[pc - 1]);
-  s += Tx[r.fx + i + 1] * (xc - (R)x[pc + 1]);
-  s += Ty[r.fy + i] * (xc - (R)x[pc - L.px]);
-  s += Ty[r.fy + i + L.nx] * (xc - (R)x[pc + L.px]);
+  R s = apply_terms2<R>(Tx[r.fx + i], Tx[r.fx + i + 1], Ty[r.fy + i], Ty[r.fy + i + L.nx], xc, (R)x[pc - 1],
+                        (R)x[pc + 1], (R)x[pc - L.px], (R)x[pc + L.px]);
   if (DIM == 3) {
     const int pl = (int)L.plane;
     s += Tz[r.fz + i] * (xc - (R)x[pc - pl]);
@@ -502,6 +518,227 @@ __device__ void t_restrict(const Xf& F, const Geo& Gc, const R* t, R* rc) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Single-pass red-black smoothing of a 2D level in global memory (one CTA)
+// ---------------------------------------------------------------------------
+// The 2m+1 half-sweeps of one smoothing run as the stages of a row pipeline:
+// at step s, stage q updates its colour's cells in row s - 2q.  Stage q reads
+// the other colour in rows s-2q-1 .. s-2q+1, which stage q-1 finished at steps
+// s-3 .. s-1, and no two stages of a step touch the same cells, so one barrier
+// per step orders everything and every cell sees exactly the values of the
+// plain half-sweep order.  The level is cut into column strips; a strip loads
+// its columns and 2m+1 more on each side (the cells whose later stages go
+// stale without the neighbouring strip; the neighbour recomputes them with the
+// same arithmetic) into rings of rows in shared memory, prefetched kFuseAhead
+// rows ahead with cp.async.  Each row of T, rp (and z) then crosses HBM once
+// per smoothing instead of once per half-sweep.  Three threads own each
+// column of the strip and, at step s, share the stages whose row has its
+// colour there; every load of a step precedes its stores.
+//   pre  (from zero): stage 0 sets z = rp/D on red cells and 0 on black; after
+//        the last stage a result step forms t = rp - A z and writes z and t.
+//   post (z holds the prolonged pre-smoothing result): the strip reads z and
+//        writes the smoothed z to `zout` (strips read their halo from the
+//        unsmoothed z, so the result cannot go back in place); the last stage
+//        adds r . z over the strip's own cells (returned per thread).
+constexpr int kFuseAhead = 8;    // rows prefetched ahead of stage 0
+constexpr int kFuseMinWidth = 16;
+constexpr int kFuseMaxM = 4;     // stages per thread <= 2 (three threads per column)
+constexpr int kFuseShare = 3;    // threads per ring column
+
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// all groups but the newest kFuseAhead are complete
+__device__ __forceinline__ void cp_async_wait_ahead() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(kFuseAhead) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Ring depths: T / rp / z rows live from the prefetch (s + kFuseAhead, and the
+// face row above it) down to the result step (s - 2S); r rows (post) only
+// from their prefetch to the last stage.
+__host__ __device__ __forceinline__ int fuse_depth(int S) { return 2 * S + kFuseAhead + 3; }
+__host__ __device__ __forceinline__ int fuse_rdepth() { return kFuseAhead + 2; }
+
+// Output columns per strip that fit `bytes` of shared memory and a CTA of
+// `threads` (kFuseShare threads per ring column); 0: fusion off.
+__host__ __device__ __forceinline__ int fuse_width(int m, size_t bytes, int vsz, int threads) {
+  if (m < 1 || m > kFuseMaxM || bytes < 64) return 0;
+  const int S = 2 * m + 1, D = fuse_depth(S);
+  const size_t per_col = 16 * (size_t)D + (size_t)fuse_rdepth() * vsz;
+  int ws = (int)((bytes - 16) / per_col);
+  if (ws > threads / kFuseShare) ws = threads / kFuseShare;
+  const int wo = ws - 2 * S - 2;
+  return wo >= kFuseMinWidth ? wo : 0;
+}
+
+template <typename V>
+__device__ V fused_smooth(const DevLevel& L, int m, bool pre, unsigned win_off, int Wo, float* zout) {
+  // the rings, addressed from the kernel's dynamic shared memory itself so
+  // that every ring access compiles to a shared-memory load or store
+  extern __shared__ __align__(16) unsigned char fuse_smem[];
+  float* const win = (float*)(fuse_smem + win_off);
+  const int S = 2 * m + 1, D = fuse_depth(S), DR = fuse_rdepth();
+  const int lag = pre ? 2 * S : 2 * S - 1;  // result (pre) / write-back (post) row = s - lag
+  const int nx = L.nx, ny = L.ny, px = L.px, off = (int)L.off;
+  const float* gTx = (const float*)L.T[0];
+  const float* gTy = (const float*)L.T[1];
+  const float* grp = (const float*)L.rp;
+  const float* gz = (const float*)L.z;
+  float* gzo = pre ? (float*)L.z : zout;
+  float* gt = (float*)L.t;
+  const V* gr = (const V*)L.r;
+  const int bd = blockDim.x, share = bd / kFuseShare;
+  // ring column, and which third of the column's stages (hs == kFuseShare:
+  // the few threads left over, idle)
+  const int col = threadIdx.x % share, hs = threadIdx.x / share;
+  const int s_end = ny - 1 + lag;
+  V acc = 0;
+  for (int a0 = 0; a0 < nx; a0 += Wo) {
+    const int a1 = min(nx, a0 + Wo), c0 = max(0, a0 - S), c1 = min(nx, a1 + S);
+    const int Ws = c1 - c0 + 2;  // ring row: columns c0-1 .. c1; the two ends stay zero
+    float* sTx = win;
+    float* sTy = sTx + D * Ws;
+    float* srp = sTy + D * Ws;
+    float* sz = srp + D * Ws;
+    V* sr = (V*)(win + ((4 * D * Ws + 3) & ~3));
+    for (int e = threadIdx.x; e < 4 * D * Ws; e += bd) win[e] = 0.f;
+    __syncthreads();
+    // this thread's ring column `col` is column i of the level
+    const int i = c0 - 1 + col;
+    const bool mine = col >= 1 && col <= Ws - 2 && hs < kFuseShare;  // a loaded cell
+    const bool face = col >= 1 && col <= Ws - 1 && hs < kFuseShare;  // a loaded x-face (west of cell i)
+    const bool own = i >= a0 && i < a1;           // a cell this strip writes
+    const size_t gi = (size_t)(i < 0 ? 0 : i);
+    // loads of row jl (T_x row, T_y face row jl+1, rp row, z row for post
+    // including the zero ghost row ny): share 0 takes T, share 1 rp and z,
+    // share 2 the r rows of the post-smoothing dot
+    auto load_row = [&](int jl, int sl) __attribute__((always_inline)) {
+      if (jl < ny) {
+        if (hs == 0) {
+          const int sf = sl + 1 == D ? 0 : sl + 1;
+          if (face) cp_async4(sTx + sl * Ws + col, gTx + (size_t)(nx + 1) * jl + gi);
+          if (mine) cp_async4(sTy + sf * Ws + col, gTy + (size_t)nx * (jl + 1) + gi);
+        } else if (hs == 1 && mine) {
+          cp_async4(srp + sl * Ws + col, grp + off + px * jl + i);
+          if (!pre) cp_async4(sz + sl * Ws + col, gz + off + px * jl + i);
+        }
+      } else if (jl == ny && !pre && mine && hs == 1) {
+        cp_async4(sz + sl * Ws + col, gz + off + px * jl + i);
+      }
+    };
+    if (mine && hs == 0) cp_async4(sTy + col, gTy + gi);  // face row 0
+    for (int jl = 0; jl < kFuseAhead; ++jl) {
+      load_row(jl, jl % D);
+      cp_async_commit();
+    }
+    int sb = 0;               // ring slot of row s
+    int ls = kFuseAhead % D;  // ring slot of row s + kFuseAhead
+    for (int s = 0; s <= s_end; ++s) {
+      load_row(s + kFuseAhead, ls);
+      ls = ls + 1 == D ? 0 : ls + 1;
+      int rs = 0;
+      if (!pre) {
+        const int jr = s + kFuseAhead - 2 * (S - 1);
+        if (hs == 2 && own && jr >= 0 && jr < ny) {
+          V* dst = sr + (jr % DR) * Ws + col;
+          if (sizeof(V) == 8) cp_async8(dst, gr + off + px * jr + i);
+          else cp_async4(dst, gr + off + px * jr + i);
+        }
+        const int jd = s - 2 * (S - 1);
+        rs = jd >= 0 ? jd % DR : 0;
+      }
+      cp_async_commit();
+      cp_async_wait_ahead();
+      __syncthreads();
+      if (pre && s == ny) {
+        // the zero ghost row above the last row (its slot held an older row)
+        const int sl = ny % D;
+        for (int e = threadIdx.x; e < Ws; e += bd) sz[sl * Ws + e] = 0.f;
+      }
+      if (mine) {
+        // stage q updates row s - 2q, whose colour at this column is (i+s)&1:
+        // the column takes the stages of that parity, dealt round its threads
+        const int q0 = (i + s) & 1;
+        float v[2];
+        int sl[2];
+        bool act[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int q = q0 + 2 * hs + 2 * kFuseShare * e;
+          const int j = s - 2 * q;
+          act[e] = q < S && j >= 0 && j < ny;
+          sl[e] = 0;
+          v[e] = 0.f;
+          if (act[e]) {
+            int sj = sb - 2 * q;
+            if (sj < 0) sj += D;
+            const int su = sj + 1 == D ? 0 : sj + 1, sd = sj == 0 ? D - 1 : sj - 1;
+            const float tw = sTx[sj * Ws + col], te = sTx[sj * Ws + col + 1], ts = sTy[sj * Ws + col],
+                        tn = sTy[su * Ws + col];
+            float d, sm = srp[sj * Ws + col];
+            if (pre && q == 0) {
+              // stage 0 of pre-smoothing (from zero): rp / D on red cells
+              d = tw;
+              d += te;
+              d += ts;
+              d += tn;
+            } else {
+              const float* zr = sz + sj * Ws;
+              gs_terms2<float>(d, sm, tw, te, ts, tn, zr[col - 1], zr[col + 1], sz[sd * Ws + col], sz[su * Ws + col]);
+            }
+            v[e] = quot<float>(sm, d);
+            sl[e] = sj;
+            if (!pre && q == S - 1 && own) acc += sr[rs * Ws + col] * (V)v[e];
+          }
+        }
+        if (hs == 0) {
+          if (pre && q0 == 1 && s < ny) sz[sb * Ws + col] = 0.f;  // black cell of stage 0's row
+          if (own) {
+            const int j = s - lag;
+            if (j >= 0 && j < ny) {
+              int sj = sb - lag;
+              if (sj < 0) sj += D;
+              const float zc = sz[sj * Ws + col];
+              const int g = off + px * j + i;
+              if (pre) {
+                const int su = sj + 1 == D ? 0 : sj + 1, sd = sj == 0 ? D - 1 : sj - 1;
+                const float* zr = sz + sj * Ws;
+                const float a = apply_terms2<float>(sTx[sj * Ws + col], sTx[sj * Ws + col + 1], sTy[sj * Ws + col],
+                                                    sTy[su * Ws + col], zc, zr[col - 1], zr[col + 1],
+                                                    sz[sd * Ws + col], sz[su * Ws + col]);
+                gt[g] = srp[sj * Ws + col] - a;
+              }
+              gzo[g] = zc;
+            }
+          }
+        } else if (hs == 1 && !pre && own && q0 != ((S - 1) & 1)) {
+          // the last stage's row at a cell of the other colour: final already
+          const int jd = s - 2 * (S - 1);
+          if (jd >= 0 && jd < ny) {
+            int sj = sb - 2 * (S - 1);
+            if (sj < 0) sj += D;
+            acc += sr[rs * Ws + col] * (V)sz[sj * Ws + col];
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < 2; ++e)
+          if (act[e]) sz[sl[e] * Ws + col] = v[e];
+      }
+      sb = sb + 1 == D ? 0 : sb + 1;
+    }
+    cp_async_wait_all();
+    __syncthreads();
+  }
+  return acc;
+}
+
 // Control of one level of the single-CTA state machine.  Scalars are kept
 // in both precisions so that an FP32 level never converts.
 struct LvlCtl {
@@ -545,7 +782,20 @@ struct RecArgs {
   const float* thrN_f;
   long long* iters;
   long long* calls;
+  // shared memory left after the resident levels: rings of the single-pass
+  // smoother, when allowed
+  unsigned win_off;  // byte offset in the dynamic shared memory
+  size_t win_bytes;
+  bool fuse;
 };
+
+// Strip width of the single-pass smoother for level L, or 0 for the plain
+// half-sweeps (levels in shared memory, small levels, no room).
+template <typename V>
+__device__ __forceinline__ int fuse_wo(const DevLevel& L, int m, const RecArgs& a) {
+  if (!a.fuse || __isShared(L.z) || (long long)L.nx * L.ny < 4096) return 0;
+  return fuse_width(m, a.win_bytes, (int)sizeof(V), blockDim.x);
+}
 
 // Per-level thresholds of the level test and zeroed counters (thread 0),
 // then a barrier.
@@ -590,7 +840,25 @@ struct Ops {
     return tm.sum<V>(acc);
   }
   // pre-smoothing from zero, t = r - A z, r_{k+1} = R t
-  static __device__ void presmooth_restrict(BlockTeam& tm, const DevLevel& L, const DevLevel& C, int m) {
+  static __device__ void presmooth_restrict(BlockTeam& tm, const DevLevel& L, const DevLevel& C, int m,
+                                             const RecArgs& a) {
+    if constexpr (DIM == 2 && sizeof(RP) == sizeof(float)) {
+      const int wo = fuse_wo<V>(L, m, a);
+      if (wo > 0) {
+        if (sizeof(V) != sizeof(RP)) {
+          // the smoother-precision copy of the right-hand side
+          const V* r = (const V*)L.r;
+          RP* rp = (RP*)L.rp;
+          const int npad = (int)L.npad;
+          for (int c = threadIdx.x; c < npad; c += blockDim.x) rp[c] = (RP)r[c];
+          tm.sync();
+        }
+        fused_smooth<V>(L, m, true, a.win_off, wo, nullptr);
+        t_restrict<DIM, RP>(xf_of(L), geo_of(C), (const RP*)L.t, (RP*)C.r);
+        tm.sync();
+        return;
+      }
+    }
     const TLevel<RP> S = tlevel_of<RP>(L);
     t_smooth<DIM, RP, V>(tm, L, S, m, true, false);
     const RP* rp = (const RP*)L.rp;
@@ -607,7 +875,8 @@ struct Ops {
   // z += E x_c on the black cells only: the first post-smoothing half-sweep
   // recomputes every red cell from its black neighbours, so a red cell's
   // prolonged value would never be read.  Then post-smoothing; returns r.z.
-  static __device__ V prolong_postsmooth(BlockTeam& tm, const DevLevel& L, const DevLevel& C, int m) {
+  static __device__ V prolong_postsmooth(BlockTeam& tm, const DevLevel& L, const DevLevel& C, int m,
+                                         const RecArgs& a) {
     {
       RP* z = (RP*)L.z;
       const RP* xc = (const RP*)C.x;
@@ -618,6 +887,21 @@ struct Ops {
       });
     }
     tm.sync();
+    if constexpr (DIM == 2 && sizeof(RP) == sizeof(float)) {
+      const int wo = fuse_wo<V>(L, m, a);
+      if (wo > 0) {
+        const V acc = fused_smooth<V>(L, m, false, a.win_off, wo, (float*)L.t);
+        // the smoothed z went to the t buffer (free after the restriction):
+        // swap the two in this CTA's copy of the level descriptor
+        if (threadIdx.x == 0) {
+          DevLevel& W = const_cast<DevLevel&>(L);
+          void* z = W.z;
+          W.z = W.t;
+          W.t = z;
+        }
+        return tm.sum<V>(acc);
+      }
+    }
     return t_smooth<DIM, RP, V>(tm, L, tlevel_of<RP>(L), m, false, true);
   }
   static __device__ V coarsest(BlockTeam& tm, const DevLevel& L, const RecArgs& a) {
@@ -724,15 +1008,15 @@ __device__ void recursion(BlockTeam& tm, const DevLevel* sL, int ks, const RecAr
         else Scal<RP>::rho(c) = Ops<DIM, RP, RP>::coarsest(tm, L, a);
         c.phase = kPrecondDone;
       } else {
-        if (dbl) Ops<DIM, double, RP>::presmooth_restrict(tm, L, sL[k + 1], a.m);
-        else Ops<DIM, RP, RP>::presmooth_restrict(tm, L, sL[k + 1], a.m);
+        if (dbl) Ops<DIM, double, RP>::presmooth_restrict(tm, L, sL[k + 1], a.m, a);
+        else Ops<DIM, RP, RP>::presmooth_restrict(tm, L, sL[k + 1], a.m, a);
         c.phase = kAfterCoarse;
         ++k;
         ct[k].phase = kStart;
       }
     } else if (c.phase == kAfterCoarse) {
-      if (dbl) c.rho_d = Ops<DIM, double, RP>::prolong_postsmooth(tm, L, sL[k + 1], a.m);
-      else Scal<RP>::rho(c) = Ops<DIM, RP, RP>::prolong_postsmooth(tm, L, sL[k + 1], a.m);
+      if (dbl) c.rho_d = Ops<DIM, double, RP>::prolong_postsmooth(tm, L, sL[k + 1], a.m, a);
+      else Scal<RP>::rho(c) = Ops<DIM, RP, RP>::prolong_postsmooth(tm, L, sL[k + 1], a.m, a);
       c.phase = kPrecondDone;
     } else if (c.phase == kPrecondDone) {
       const int st = dbl ? Ops<DIM, double, RP>::iterate(tm, L, c, S, a, k) : Ops<DIM, RP, RP>::iterate(tm, L, c, S, a, k);
@@ -902,6 +1186,12 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small(const ProblemDesc* _
         a.ainv_t = true;
         __syncthreads();
       }
+    }
+    {
+      const size_t base = align16(used + (a.ainv_t ? sizeof(double) * (size_t)pd.nc * pd.nc : 0));
+      a.win_off = (unsigned)base;
+      a.win_bytes = smem_budget > base ? smem_budget - base : 0;
+      a.fuse = pd.fuse != 0;
     }
     a.floor2 = S->inner_floor2;
     a.floor2_f = (float)a.floor2;
@@ -1545,20 +1835,29 @@ void launch_small_any(int dim, bool f32, const ProblemDesc* P, const int* order,
   }
 }
 
-// Shared memory that levels lo..kmax of hierarchy h need (from the coarsest
-// up, as many as fit under the per-CTA limit).
+// Dynamic shared memory of a single-CTA launch for levels lo..kmax of h: the
+// levels that fit (coarsest first) and the coarsest inverse; when a 2D FP32
+// level of at least 4096 cells stays in global memory, the whole per-CTA
+// limit, whose rest holds the rings of the single-pass smoother.  (512
+// threads of 128 registers fill an SM's register file, so the CTA has the SM
+// to itself either way; launches that need no rings keep the L1 share.)
 size_t levels_smem(const msrcg_hier* h, int lo, bool top_double) {
   const bool f32 = h->o.precision == 1;
   const size_t rsz = f32 ? sizeof(float) : sizeof(double), lim = small_smem_limit_any(h->dim, f32);
   size_t tot = 0;
+  int kfit = h->nlev;
   for (int k = h->nlev - 1; k >= lo; --k) {
     const size_t vsz = (top_double && k == 0) ? sizeof(double) : rsz;
     const size_t b = level_smem_bytes(h->hL[k], vsz, rsz, h->dim);
     if (tot + b > lim) break;
     tot += b;
+    kfit = k;
   }
   const size_t ainv = sizeof(double) * (size_t)h->nc * h->nc;
   if (tot + ainv <= lim) tot += ainv;
+  if (h->dim == 2 && f32 && h->o.plain_sweeps == 0)
+    for (int k = lo; k < kfit; ++k)
+      if (h->N[k] >= 4096) return lim;
   return tot;
 }
 
@@ -1577,6 +1876,7 @@ ProblemDesc make_desc(msrcg_hier* h, const double* b, double* x, double tol) {
   pd.xs = h->xs;
   pd.tol = tol;
   pd.work = h->N[0];
+  pd.fuse = h->o.plain_sweeps == 0;
   return pd;
 }
 

@@ -199,6 +199,21 @@ def test_channel_3d_32_fp64_matches_oracle(M):
     _counts_close(st["iters"], sr["iters"], sr["calls"])
 
 
+@pytest.mark.parametrize("plain", [0, 1])
+def test_batched_1024_single_pass_and_plain_sweeps(M, plain):
+    """The batched solver on the full 1024^2 problem, whose two finest levels
+    live in global memory: with the single-pass smoother (default) and with
+    one pass per half-sweep.  Both match the oracle."""
+    prob = P.config_problem(1)
+    opts = M.default_opts(precision=1, inner_floor=1e-6, plain_sweeps=plain)
+    H = M.Hierarchy.from_problem(prob, opts)
+    xs, sts = M.batch_solve([H], [H.rhs_for(prob)], 1e-8)
+    xr, sr = _oracle_solution("grf-1024", prob)
+    assert sts[0]["status"] == 0 and sts[0]["relres_true"] < 1e-8, sts[0]
+    err = np.linalg.norm(xs[0].cpu().numpy() - xr) / np.linalg.norm(xr)
+    assert err <= SOL_RTOL, err
+
+
 def test_repeat_solves_identical(M):
     """Deterministic reductions: two solves give the same bits."""
     prob = P.config_problem(1, scale=256)
