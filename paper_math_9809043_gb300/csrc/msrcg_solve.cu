@@ -595,7 +595,7 @@ __device__ V fused_smooth(const DevLevel& L, int m, bool pre, unsigned win_off, 
   float* gt = (float*)L.t;
   const V* gr = (const V*)L.r;
   const int bd = blockDim.x, share = bd / kFuseShare;
-  // ring column, and which third of the column's stages (hs == kFuseShare:
+  // ring column, and which share of the column's stages (hs == kFuseShare:
   // the few threads left over, idle)
   const int col = threadIdx.x % share, hs = threadIdx.x / share;
   const int s_end = ny - 1 + lag;
@@ -603,46 +603,67 @@ __device__ V fused_smooth(const DevLevel& L, int m, bool pre, unsigned win_off, 
   for (int a0 = 0; a0 < nx; a0 += Wo) {
     const int a1 = min(nx, a0 + Wo), c0 = max(0, a0 - S), c1 = min(nx, a1 + S);
     const int Ws = c1 - c0 + 2;  // ring row: columns c0-1 .. c1; the two ends stay zero
+    const int DW = D * Ws;       // one ring, in floats
     float* sTx = win;
-    float* sTy = sTx + D * Ws;
-    float* srp = sTy + D * Ws;
-    float* sz = srp + D * Ws;
-    V* sr = (V*)(win + ((4 * D * Ws + 3) & ~3));
-    for (int e = threadIdx.x; e < 4 * D * Ws; e += bd) win[e] = 0.f;
+    float* sTy = sTx + DW;
+    float* srp = sTy + DW;
+    float* sz = srp + DW;
+    V* sr = (V*)(win + ((4 * DW + 3) & ~3));
+    for (int e = threadIdx.x; e < 4 * DW; e += bd) win[e] = 0.f;
     __syncthreads();
     // this thread's ring column `col` is column i of the level
     const int i = c0 - 1 + col;
-    const bool mine = col >= 1 && col <= Ws - 2 && hs < kFuseShare;  // a loaded cell
-    const bool face = col >= 1 && col <= Ws - 1 && hs < kFuseShare;  // a loaded x-face (west of cell i)
-    const bool own = i >= a0 && i < a1;           // a cell this strip writes
-    const size_t gi = (size_t)(i < 0 ? 0 : i);
-    // loads of row jl (T_x row, T_y face row jl+1, rp row, z row for post
-    // including the zero ghost row ny): share 0 takes T, share 1 rp and z,
-    // share 2 the r rows of the post-smoothing dot
-    auto load_row = [&](int jl, int sl) __attribute__((always_inline)) {
+    const bool live = hs < kFuseShare;
+    const bool mine = live && col >= 1 && col <= Ws - 2;  // a loaded cell
+    const bool face = live && col >= 1 && col <= Ws - 1;  // a loaded x-face (west of cell i)
+    const bool own = live && i >= a0 && i < a1;           // a cell this strip writes
+    // loads (share 0: T rows; share 1: rp and z rows; share 2: r rows) walk
+    // down the level with running pointers
+    const float* pTx = gTx + (i < 0 ? 0 : i);
+    const float* pTy = gTy + (i < 0 ? 0 : i);
+    const float* prp = grp + off + i;
+    const float* pz = gz + off + i;
+    if (mine && hs == 0) cp_async4(sTy + col, pTy);  // face row 0
+    pTy += nx;
+    int jl = 0, lo = 0;  // next row to load and its ring offset
+    auto load_next = [&]() __attribute__((always_inline)) {
       if (jl < ny) {
         if (hs == 0) {
-          const int sf = sl + 1 == D ? 0 : sl + 1;
-          if (face) cp_async4(sTx + sl * Ws + col, gTx + (size_t)(nx + 1) * jl + gi);
-          if (mine) cp_async4(sTy + sf * Ws + col, gTy + (size_t)nx * (jl + 1) + gi);
+          const int fo = lo + Ws == DW ? 0 : lo + Ws;
+          if (face) cp_async4(sTx + lo + col, pTx);
+          if (mine) cp_async4(sTy + fo + col, pTy);
         } else if (hs == 1 && mine) {
-          cp_async4(srp + sl * Ws + col, grp + off + px * jl + i);
-          if (!pre) cp_async4(sz + sl * Ws + col, gz + off + px * jl + i);
+          cp_async4(srp + lo + col, prp);
+          if (!pre) cp_async4(sz + lo + col, pz);
         }
-      } else if (jl == ny && !pre && mine && hs == 1) {
-        cp_async4(sz + sl * Ws + col, gz + off + px * jl + i);
+        pTx += nx + 1;
+        pTy += nx;
+        prp += px;
+        pz += px;
+      } else if (jl == ny && !pre && hs == 1 && mine) {
+        cp_async4(sz + lo + col, pz);  // the zero ghost row
       }
+      lo = lo + Ws == DW ? 0 : lo + Ws;
+      ++jl;
     };
-    if (mine && hs == 0) cp_async4(sTy + col, gTy + gi);  // face row 0
-    for (int jl = 0; jl < kFuseAhead; ++jl) {
-      load_row(jl, jl % D);
+    for (int k = 0; k < kFuseAhead; ++k) {
+      load_next();
       cp_async_commit();
     }
-    int sb = 0;               // ring slot of row s
-    int ls = kFuseAhead % D;  // ring slot of row s + kFuseAhead
+    // stage q updates row s - 2q, whose colour at this column is (i+s)&1: the
+    // column takes the stages of that parity, dealt round its threads; the
+    // parity flips every step
+    int qa0 = 2 * hs, qb0 = 2 * hs + 2 * kFuseShare;  // parity 0: stages qa0, qb0
+    int qa1 = qa0 + 1, qb1 = qb0 + 1;                 // parity 1
+    if (qa0 >= S) qa0 = -1;
+    if (qb0 >= S) qb0 = -1;
+    if (qa1 >= S) qa1 = -1;
+    if (qb1 >= S) qb1 = -1;
+    int par = i & 1;
+    int sbo = 0;  // ring offset of row s
+    const int lago = lag * Ws, lasto = 2 * (S - 1) * Ws;
     for (int s = 0; s <= s_end; ++s) {
-      load_row(s + kFuseAhead, ls);
-      ls = ls + 1 == D ? 0 : ls + 1;
+      load_next();
       int rs = 0;
       if (!pre) {
         const int jr = s + kFuseAhead - 2 * (S - 1);
@@ -652,37 +673,34 @@ __device__ V fused_smooth(const DevLevel& L, int m, bool pre, unsigned win_off, 
           else cp_async4(dst, gr + off + px * jr + i);
         }
         const int jd = s - 2 * (S - 1);
-        rs = jd >= 0 ? jd % DR : 0;
+        rs = (jd >= 0 ? jd % DR : 0) * Ws + col;
       }
       cp_async_commit();
       cp_async_wait_ahead();
       __syncthreads();
       if (pre && s == ny) {
         // the zero ghost row above the last row (its slot held an older row)
-        const int sl = ny % D;
-        for (int e = threadIdx.x; e < Ws; e += bd) sz[sl * Ws + e] = 0.f;
+        const int sl = (ny % D) * Ws;
+        for (int e = threadIdx.x; e < Ws; e += bd) sz[sl + e] = 0.f;
       }
       if (mine) {
-        // stage q updates row s - 2q, whose colour at this column is (i+s)&1:
-        // the column takes the stages of that parity, dealt round its threads
-        const int q0 = (i + s) & 1;
+        const int qa = par ? qa1 : qa0, qb = par ? qb1 : qb0;
         float v[2];
-        int sl[2];
+        int ro[2];
         bool act[2];
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
-          const int q = q0 + 2 * hs + 2 * kFuseShare * e;
-          const int j = s - 2 * q;
-          act[e] = q < S && j >= 0 && j < ny;
-          sl[e] = 0;
+          const int q = e == 0 ? qa : qb;
+          act[e] = q >= 0 && s >= 2 * q && s < 2 * q + ny;
+          ro[e] = 0;
           v[e] = 0.f;
           if (act[e]) {
-            int sj = sb - 2 * q;
-            if (sj < 0) sj += D;
-            const int su = sj + 1 == D ? 0 : sj + 1, sd = sj == 0 ? D - 1 : sj - 1;
-            const float tw = sTx[sj * Ws + col], te = sTx[sj * Ws + col + 1], ts = sTy[sj * Ws + col],
-                        tn = sTy[su * Ws + col];
-            float d, sm = srp[sj * Ws + col];
+            int r0 = sbo - 2 * q * Ws;
+            if (r0 < 0) r0 += DW;
+            const int ru = r0 + Ws == DW ? 0 : r0 + Ws, rd = r0 == 0 ? DW - Ws : r0 - Ws;
+            const int c = r0 + col;
+            const float tw = sTx[c], te = sTx[c + 1], ts = sTy[c], tn = sTy[ru + col];
+            float d, sm = srp[c];
             if (pre && q == 0) {
               // stage 0 of pre-smoothing (from zero): rp / D on red cells
               d = tw;
@@ -690,48 +708,43 @@ __device__ V fused_smooth(const DevLevel& L, int m, bool pre, unsigned win_off, 
               d += ts;
               d += tn;
             } else {
-              const float* zr = sz + sj * Ws;
-              gs_terms2<float>(d, sm, tw, te, ts, tn, zr[col - 1], zr[col + 1], sz[sd * Ws + col], sz[su * Ws + col]);
+              gs_terms2<float>(d, sm, tw, te, ts, tn, sz[c - 1], sz[c + 1], sz[rd + col], sz[ru + col]);
             }
             v[e] = quot<float>(sm, d);
-            sl[e] = sj;
-            if (!pre && q == S - 1 && own) acc += sr[rs * Ws + col] * (V)v[e];
+            ro[e] = c;
+            if (!pre && q == S - 1 && own) acc += sr[rs] * (V)v[e];
           }
         }
         if (hs == 0) {
-          if (pre && q0 == 1 && s < ny) sz[sb * Ws + col] = 0.f;  // black cell of stage 0's row
-          if (own) {
-            const int j = s - lag;
-            if (j >= 0 && j < ny) {
-              int sj = sb - lag;
-              if (sj < 0) sj += D;
-              const float zc = sz[sj * Ws + col];
-              const int g = off + px * j + i;
-              if (pre) {
-                const int su = sj + 1 == D ? 0 : sj + 1, sd = sj == 0 ? D - 1 : sj - 1;
-                const float* zr = sz + sj * Ws;
-                const float a = apply_terms2<float>(sTx[sj * Ws + col], sTx[sj * Ws + col + 1], sTy[sj * Ws + col],
-                                                    sTy[su * Ws + col], zc, zr[col - 1], zr[col + 1],
-                                                    sz[sd * Ws + col], sz[su * Ws + col]);
-                gt[g] = srp[sj * Ws + col] - a;
-              }
-              gzo[g] = zc;
+          if (pre && par == 1 && s < ny) sz[sbo + col] = 0.f;  // black cell of stage 0's row
+          if (own && s >= lag && s < lag + ny) {
+            int r0 = sbo - lago;
+            if (r0 < 0) r0 += DW;
+            const int c = r0 + col;
+            const float zc = sz[c];
+            const int g = off + px * (s - lag) + i;
+            if (pre) {
+              const int ru = r0 + Ws == DW ? 0 : r0 + Ws, rd = r0 == 0 ? DW - Ws : r0 - Ws;
+              const float a = apply_terms2<float>(sTx[c], sTx[c + 1], sTy[c], sTy[ru + col], zc, sz[c - 1], sz[c + 1],
+                                                  sz[rd + col], sz[ru + col]);
+              gt[g] = srp[c] - a;
             }
+            gzo[g] = zc;
           }
-        } else if (hs == 1 && !pre && own && q0 != ((S - 1) & 1)) {
+        } else if (hs == 1 && !pre && own && par != ((S - 1) & 1)) {
           // the last stage's row at a cell of the other colour: final already
-          const int jd = s - 2 * (S - 1);
-          if (jd >= 0 && jd < ny) {
-            int sj = sb - 2 * (S - 1);
-            if (sj < 0) sj += D;
-            acc += sr[rs * Ws + col] * (V)sz[sj * Ws + col];
+          if (s >= 2 * (S - 1) && s < 2 * (S - 1) + ny) {
+            int r0 = sbo - lasto;
+            if (r0 < 0) r0 += DW;
+            acc += sr[rs] * (V)sz[r0 + col];
           }
         }
 #pragma unroll
         for (int e = 0; e < 2; ++e)
-          if (act[e]) sz[sl[e] * Ws + col] = v[e];
+          if (act[e]) sz[ro[e]] = v[e];
       }
-      sb = sb + 1 == D ? 0 : sb + 1;
+      par ^= 1;
+      sbo = sbo + Ws == DW ? 0 : sbo + Ws;
     }
     cp_async_wait_all();
     __syncthreads();
