@@ -22,7 +22,14 @@ namespace msrcg {
 
 constexpr int kMaxLev = MSRCG_MAXLEV;
 constexpr int kThreads = 256;        // block size of the multi-CTA level kernels
-constexpr int kSmallThreads = 512;   // block size of the single-CTA solver
+#ifndef MSRCG_SMALL_THREADS
+#define MSRCG_SMALL_THREADS 512
+#endif
+#ifndef MSRCG_SMALL_PER_SM
+#define MSRCG_SMALL_PER_SM 1
+#endif
+constexpr int kSmallThreads = MSRCG_SMALL_THREADS;  // block size of the single-CTA solver
+constexpr int kSmallPerSM = MSRCG_SMALL_PER_SM;     // single-CTA solvers resident per SM
 constexpr int kMaxGrid = 4096;       // upper bound of blocks per multi-CTA launch
 
 // status bits written on the device (host maps them to MSRCG_E*)

@@ -543,7 +543,14 @@ __device__ void t_restrict(const Xf& F, const Geo& Gc, const R* t, R* rc) {
 constexpr int kFuseAhead = 8;    // rows prefetched ahead of stage 0
 constexpr int kFuseMinWidth = 16;
 constexpr int kFuseMaxM = 4;     // stages per thread <= 2 (three threads per column)
-constexpr int kFuseShare = 3;    // threads per ring column
+#ifndef MSRCG_FUSE_SHARE
+#define MSRCG_FUSE_SHARE 3
+#endif
+constexpr int kFuseShare = MSRCG_FUSE_SHARE;  // threads per ring column
+// stage entries per thread and step: the column's stages of one parity
+// (at most kFuseMaxM + 1) dealt round kFuseShare threads
+constexpr int kFuseE = (kFuseMaxM + 1 + kFuseShare - 1) / kFuseShare;
+constexpr int kFuseRoleZ = kFuseShare > 1 ? 1 : 0;  // share loading rp / z, adding the black r.z
 
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
@@ -632,7 +639,8 @@ __device__ V fused_smooth(const DevLevel& L, int m, bool pre, unsigned win_off, 
           const int fo = lo + Ws == DW ? 0 : lo + Ws;
           if (face) cp_async4(sTx + lo + col, pTx);
           if (mine) cp_async4(sTy + fo + col, pTy);
-        } else if (hs == 1 && mine) {
+        }
+        if (hs == kFuseRoleZ && mine) {
           cp_async4(srp + lo + col, prp);
           if (!pre) cp_async4(sz + lo + col, pz);
         }
@@ -640,7 +648,7 @@ __device__ V fused_smooth(const DevLevel& L, int m, bool pre, unsigned win_off, 
         pTy += nx;
         prp += px;
         pz += px;
-      } else if (jl == ny && !pre && hs == 1 && mine) {
+      } else if (jl == ny && !pre && hs == kFuseRoleZ && mine) {
         cp_async4(sz + lo + col, pz);  // the zero ghost row
       }
       lo = lo + Ws == DW ? 0 : lo + Ws;
@@ -653,12 +661,6 @@ __device__ V fused_smooth(const DevLevel& L, int m, bool pre, unsigned win_off, 
     // stage q updates row s - 2q, whose colour at this column is (i+s)&1: the
     // column takes the stages of that parity, dealt round its threads; the
     // parity flips every step
-    int qa0 = 2 * hs, qb0 = 2 * hs + 2 * kFuseShare;  // parity 0: stages qa0, qb0
-    int qa1 = qa0 + 1, qb1 = qb0 + 1;                 // parity 1
-    if (qa0 >= S) qa0 = -1;
-    if (qb0 >= S) qb0 = -1;
-    if (qa1 >= S) qa1 = -1;
-    if (qb1 >= S) qb1 = -1;
     int par = i & 1;
     int sbo = 0;  // ring offset of row s
     const int lago = lag * Ws, lasto = 2 * (S - 1) * Ws;
@@ -667,7 +669,7 @@ __device__ V fused_smooth(const DevLevel& L, int m, bool pre, unsigned win_off, 
       int rs = 0;
       if (!pre) {
         const int jr = s + kFuseAhead - 2 * (S - 1);
-        if (hs == 2 && own && jr >= 0 && jr < ny) {
+        if (hs == kFuseShare - 1 && own && jr >= 0 && jr < ny) {
           V* dst = sr + (jr % DR) * Ws + col;
           if (sizeof(V) == 8) cp_async8(dst, gr + off + px * jr + i);
           else cp_async4(dst, gr + off + px * jr + i);
@@ -684,14 +686,13 @@ __device__ V fused_smooth(const DevLevel& L, int m, bool pre, unsigned win_off, 
         for (int e = threadIdx.x; e < Ws; e += bd) sz[sl + e] = 0.f;
       }
       if (mine) {
-        const int qa = par ? qa1 : qa0, qb = par ? qb1 : qb0;
-        float v[2];
-        int ro[2];
-        bool act[2];
+        float v[kFuseE];
+        int ro[kFuseE];
+        bool act[kFuseE];
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const int q = e == 0 ? qa : qb;
-          act[e] = q >= 0 && s >= 2 * q && s < 2 * q + ny;
+        for (int e = 0; e < kFuseE; ++e) {
+          const int q = par + 2 * hs + 2 * kFuseShare * e;
+          act[e] = q < S && s >= 2 * q && s < 2 * q + ny;
           ro[e] = 0;
           v[e] = 0.f;
           if (act[e]) {
@@ -731,7 +732,8 @@ __device__ V fused_smooth(const DevLevel& L, int m, bool pre, unsigned win_off, 
             }
             gzo[g] = zc;
           }
-        } else if (hs == 1 && !pre && own && par != ((S - 1) & 1)) {
+        }
+        if (hs == kFuseRoleZ && !pre && own && par != ((S - 1) & 1)) {
           // the last stage's row at a cell of the other colour: final already
           if (s >= 2 * (S - 1) && s < 2 * (S - 1) + ny) {
             int r0 = sbo - lasto;
@@ -740,7 +742,7 @@ __device__ V fused_smooth(const DevLevel& L, int m, bool pre, unsigned win_off, 
           }
         }
 #pragma unroll
-        for (int e = 0; e < 2; ++e)
+        for (int e = 0; e < kFuseE; ++e)
           if (act[e]) sz[ro[e]] = v[e];
       }
       par ^= 1;
@@ -1152,7 +1154,7 @@ __device__ int place_levels(DevLevel* sL, const DevLevel* gL, int lo, int kmax, 
 // to xs, forms the true residual b - A xs in FP64 and, if that misses tol,
 // runs the recursion again on it (at most 3 restarts); x = xs at the end.
 template <int DIM, typename RP>
-__global__ void __launch_bounds__(kSmallThreads, 1) k_small(const ProblemDesc* __restrict__ P,
+__global__ void __launch_bounds__(kSmallThreads, kSmallPerSM) k_small(const ProblemDesc* __restrict__ P,
                                                             const int* __restrict__ order, int nprob, int ks, int mode,
                                                             int* next, size_t smem_budget) {
   extern __shared__ __align__(16) unsigned char dsm[];
@@ -1818,6 +1820,11 @@ size_t small_smem_limit() {
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaFuncAttributes fa;
     cudaFuncGetAttributes(&fa, k_small<DIM, RP>);
+    if (kSmallPerSM > 1) {
+      int per_sm = 0;
+      cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+      optin = std::min(optin, per_sm / kSmallPerSM - 1024);
+    }
     size_t l = (size_t)optin > fa.sharedSizeBytes + 1024 ? (size_t)optin - fa.sharedSizeBytes - 1024 : 0;
     cudaFuncSetAttribute(k_small<DIM, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l);
     (void)cudaGetLastError();
