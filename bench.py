@@ -275,14 +275,17 @@ def run_uneven(args, M, P, dev, stream):
     """256 independent 2D problems of sides 64..512 (GRF, 1e6 contrast, N(0,1)
     right-hand sides) in one persistent launch; both precisions."""
     import torch
+    from paper_math_9809043_gb300 import tune as TU
+    tuned_rec = TU.best(torch.cuda.get_device_name(dev), "uneven256")
+    tuned = tuned_rec or {}
     probs = P.batch_problems(256)
     ncell = sum(p.N for p in probs)
     out = {"workload": "256 2D problems, side U{64,96,128,192,256,384,512}, GRF corr. 8 cells, 1e6 contrast",
-           "unknowns": ncell}
+           "unknowns": ncell, "tile_shapes": TU.key_of(tuned) + (" (autotuner record)" if tuned_rec is not None else "")}
     for prec, key in ((1, "fp32_precond"), (0, "fp64_plain")):
         if prec == 0 and args.no_fp64:
             continue
-        opts = M.default_opts(precision=prec, inner_floor=1e-6 if prec else 0.0)
+        opts = M.default_opts(precision=prec, inner_floor=1e-6 if prec else 0.0, **(tuned if prec else {}))
         hs = [M.Hierarchy.from_problem(p, opts, device=dev) for p in probs]
         bs = [h.rhs_for(p) for h, p in zip(hs, probs)]
         per, sts = _timed_batch(M, hs, bs, 3 if prec else 2, stream, dev)
@@ -362,8 +365,14 @@ def main():
     base = P.config_problem(1, scale=args.size)
     stream = torch.cuda.current_stream(dev)
 
+    # tile shapes of the batched solver for this GPU and workload (autotuner record)
+    from paper_math_9809043_gb300 import tune as TU
+    gpu_name = torch.cuda.get_device_name(dev)
+    tuned_rec = TU.best(gpu_name, f"grf{args.size}x{nb}")
+    tuned = tuned_rec or {}
+
     def make_batch(prec):
-        opts = M.default_opts(precision=prec, inner_floor=1e-6 if prec else 0.0)
+        opts = M.default_opts(precision=prec, inner_floor=1e-6 if prec else 0.0, **(tuned if prec else {}))
         hs, bs = [], []
         for j in range(nb):
             # problem j of this rank: the shared permeability field with its own
@@ -515,7 +524,8 @@ def main():
                 "config": {"workload": WORKLOAD, "size": args.size, "concurrent_solves_per_gpu": nb,
                            "precision": "FP32 preconditioner (smoother, transfers, inner PCG) in FP64 outer PCG",
                            "l2": "inputs larger than L2 (each problem's hierarchy ~70 MB resident in HBM)",
-                           "parallelism": f"independent problems, {world} GPU(s)"},
+                           "parallelism": f"independent problems, {world} GPU(s)",
+                           "tile_shapes": TU.key_of(tuned) + (" (autotuner record)" if tuned_rec is not None else "")},
                 "status": statuses, "relres_true_max": relres, "iters": sts[0]["iters"],
                 "latency_ms": latency, "fp64_plain": fp64, "uneven_batch": uneven, "grid3d": grid3d,
                 "serving": serving, "e2e": e2e, "roofline": roofline,

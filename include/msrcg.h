@@ -72,7 +72,11 @@ typedef struct {
                         2D FP32-preconditioner levels in global memory that the single-CTA solver
                         handles run all half-sweeps of one smoothing in a single pass over the
                         level (same values, fewer memory passes) */
-  int reserved[6];
+  int fuse_width;      /* single-pass smoothing: most output columns per strip (0 = as many as the
+                          shared memory holds); a tile shape the autotuner may set */
+  int fuse_min_cells;  /* single-pass smoothing only on levels of at least this many cells
+                          (0 = 4096) */
+  int reserved[4];
 } msrcg_opts;
 
 /* Per-solve statistics.  iters[k] = PCG iterations summed over all calls at

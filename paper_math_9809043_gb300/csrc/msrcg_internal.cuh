@@ -111,6 +111,8 @@ struct ProblemDesc {
   double tol;
   long long work;        // scheduling weight (cells of level 0)
   int fuse;              // single-pass smoothing allowed on global-memory levels
+  int fuse_width;        // its strip width cap (0: none)
+  int fuse_min_cells;    // its smallest level (cells)
 };
 
 }  // namespace msrcg

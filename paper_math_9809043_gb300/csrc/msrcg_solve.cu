@@ -542,6 +542,7 @@ __device__ void t_restrict(const Xf& F, const Geo& Gc, const R* t, R* rc) {
 //        adds r . z over the strip's own cells (returned per thread).
 constexpr int kFuseAhead = 8;    // rows prefetched ahead of stage 0
 constexpr int kFuseMinWidth = 16;
+constexpr int kFuseMinCells = 4096;  // default smallest level that takes the single pass
 constexpr int kFuseMaxM = 4;     // stages per thread <= 2 (three threads per column)
 #ifndef MSRCG_FUSE_SHARE
 #define MSRCG_FUSE_SHARE 3
@@ -802,14 +803,16 @@ struct RecArgs {
   unsigned win_off;  // byte offset in the dynamic shared memory
   size_t win_bytes;
   bool fuse;
+  int fuse_width, fuse_min_cells;
 };
 
 // Strip width of the single-pass smoother for level L, or 0 for the plain
 // half-sweeps (levels in shared memory, small levels, no room).
 template <typename V>
 __device__ __forceinline__ int fuse_wo(const DevLevel& L, int m, const RecArgs& a) {
-  if (!a.fuse || __isShared(L.z) || (long long)L.nx * L.ny < 4096) return 0;
-  return fuse_width(m, a.win_bytes, (int)sizeof(V), blockDim.x);
+  if (!a.fuse || __isShared(L.z) || (long long)L.nx * L.ny < a.fuse_min_cells) return 0;
+  const int w = fuse_width(m, a.win_bytes, (int)sizeof(V), blockDim.x);
+  return a.fuse_width > 0 && a.fuse_width < w ? max(a.fuse_width, kFuseMinWidth) : w;
 }
 
 // Per-level thresholds of the level test and zeroed counters (thread 0),
@@ -1207,6 +1210,8 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallPerSM) k_small(const Prob
       a.win_off = (unsigned)base;
       a.win_bytes = smem_budget > base ? smem_budget - base : 0;
       a.fuse = pd.fuse != 0;
+      a.fuse_width = pd.fuse_width;
+      a.fuse_min_cells = pd.fuse_min_cells;
     }
     a.floor2 = S->inner_floor2;
     a.floor2_f = (float)a.floor2;
@@ -1875,9 +1880,10 @@ size_t levels_smem(const msrcg_hier* h, int lo, bool top_double) {
   }
   const size_t ainv = sizeof(double) * (size_t)h->nc * h->nc;
   if (tot + ainv <= lim) tot += ainv;
+  const long long fmin = h->o.fuse_min_cells > 0 ? h->o.fuse_min_cells : kFuseMinCells;
   if (h->dim == 2 && f32 && h->o.plain_sweeps == 0)
     for (int k = lo; k < kfit; ++k)
-      if (h->N[k] >= 4096) return lim;
+      if (h->N[k] >= fmin) return lim;
   return tot;
 }
 
@@ -1897,6 +1903,8 @@ ProblemDesc make_desc(msrcg_hier* h, const double* b, double* x, double tol) {
   pd.tol = tol;
   pd.work = h->N[0];
   pd.fuse = h->o.plain_sweeps == 0;
+  pd.fuse_width = h->o.fuse_width;
+  pd.fuse_min_cells = h->o.fuse_min_cells > 0 ? h->o.fuse_min_cells : kFuseMinCells;
   return pd;
 }
 

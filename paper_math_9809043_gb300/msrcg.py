@@ -31,7 +31,8 @@ class Opts(C.Structure):
     _fields_ = [("scale", C.c_int), ("m", C.c_int), ("f", C.c_double), ("coarsest_max_side", C.c_int),
                 ("precision", C.c_int), ("maxit_outer", C.c_int), ("maxit_inner", C.c_int),
                 ("timeout_ns", C.c_uint64), ("inner_floor", C.c_double), ("small_cells", C.c_int),
-                ("plain_sweeps", C.c_int), ("reserved", C.c_int * 6)]
+                ("plain_sweeps", C.c_int), ("fuse_width", C.c_int), ("fuse_min_cells", C.c_int),
+                ("reserved", C.c_int * 4)]
 
 
 class Stats(C.Structure):

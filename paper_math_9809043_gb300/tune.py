@@ -1,0 +1,127 @@
+"""Autotuner for the tile shapes of the batched solver.
+
+The batched solver (`msrcg_batch_solve`, one CTA per problem) smooths the
+levels it keeps in global memory in one pass over column strips (see
+`fused_smooth` in csrc/msrcg_solve.cu).  Its tile shape is the strip width
+(output columns per strip) and the smallest level that takes the single pass;
+the plain per-half-sweep passes are the alternative.  Which is fastest depends
+on the problem sizes, the batch and the GPU, so `tune` times the candidates on
+the actual workload and `best` returns the winner recorded for this GPU.
+
+Records live in `tuned.json` beside this module, keyed by GPU name and a
+workload key chosen by the caller; `python -m paper_math_9809043_gb300.tune
+--out FILE` tunes the 1024^2 and the uneven-batch workloads and writes them.
+"""
+from __future__ import annotations
+
+import json
+import os
+import statistics
+from typing import Dict, List, Optional
+
+TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
+
+# candidate settings (fields of msrcg_opts); the first is the library default
+CANDIDATES: List[Dict[str, int]] = [
+    {},
+    {"plain_sweeps": 1},
+    {"fuse_width": 96},
+    {"fuse_width": 64},
+    {"fuse_min_cells": 262144},
+]
+
+
+def key_of(cand: Dict[str, int]) -> str:
+    return ",".join(f"{k}={v}" for k, v in sorted(cand.items())) or "default"
+
+
+def load_table(path: str = TABLE) -> dict:
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def record(table: dict, gpu: str, workload: str, best: Dict[str, int], times: Dict[str, float]) -> dict:
+    table.setdefault(gpu, {})[workload] = {"best": best, "ms": times}
+    return table
+
+
+def best(gpu: str, workload: str, path: str = TABLE) -> Optional[Dict[str, int]]:
+    """The recorded fastest settings for (gpu, workload), or None."""
+    ent = load_table(path).get(gpu, {}).get(workload)
+    return dict(ent["best"]) if ent else None
+
+
+def tune(problems, precision: int = 1, tol: float = 1e-8, steps: int = 2,
+         candidates: List[Dict[str, int]] = CANDIDATES, device=None):
+    """Time one batched solve of `problems` per candidate (after one warm-up)
+    and return (fastest candidate, {candidate key: mean ms})."""
+    import torch
+
+    from . import msrcg as M
+
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    times: Dict[str, float] = {}
+    for cand in candidates:
+        opts = M.default_opts(precision=precision, inner_floor=1e-6 if precision else 0.0, **cand)
+        hs = [M.Hierarchy.from_problem(p, opts, device=dev) for p in problems]
+        bs = [h.rhs_for(p) for h, p in zip(hs, problems)]
+        M.batch_solve(hs, bs, tol)
+        torch.cuda.synchronize(dev)
+        per = []
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, sts = M.batch_solve(hs, bs, tol)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            if any(s["status"] != 0 for s in sts):
+                raise RuntimeError(f"candidate {key_of(cand)} did not converge")
+            per.append(e0.elapsed_time(e1))
+        times[key_of(cand)] = statistics.mean(per)
+        del hs, bs
+        torch.cuda.empty_cache()
+    fastest = min(candidates, key=lambda c: times[key_of(c)])
+    return dict(fastest), times
+
+
+def _grf_batch(n_problems: int, side: int):
+    import numpy as np
+
+    from . import problems as P
+
+    base = P.config_problem(1, scale=side)
+    out = []
+    for j in range(n_problems):
+        rng = np.random.default_rng(1001 * 1000 + j)
+        out.append(P.Problem(dim=2, n=base.n, h=base.h, K=base.K, bc=base.bc, gD=base.gD,
+                             f=rng.standard_normal(base.N), pbf=base.pbf))
+    return out
+
+
+def main(argv=None) -> int:
+    import argparse
+
+    import torch
+
+    from . import problems as P
+
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--out", default=TABLE)
+    args = ap.parse_args(argv)
+    gpu = torch.cuda.get_device_name()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    table = load_table(args.out)
+    for workload, probs in ((f"grf1024x{sms}", _grf_batch(sms, 1024)), ("uneven256", P.batch_problems(256))):
+        fastest, times = tune(probs)
+        record(table, gpu, workload, fastest, times)
+        print(workload, key_of(fastest), {k: round(v, 2) for k, v in times.items()}, flush=True)
+    with open(args.out, "w") as f:
+        json.dump(table, f, indent=1, sort_keys=True)
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

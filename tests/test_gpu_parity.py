@@ -199,13 +199,14 @@ def test_channel_3d_32_fp64_matches_oracle(M):
     _counts_close(st["iters"], sr["iters"], sr["calls"])
 
 
-@pytest.mark.parametrize("plain", [0, 1])
-def test_batched_1024_single_pass_and_plain_sweeps(M, plain):
+@pytest.mark.parametrize("extra", [{}, {"plain_sweeps": 1}, {"fuse_width": 40}, {"fuse_min_cells": 262144}])
+def test_batched_1024_single_pass_and_plain_sweeps(M, extra):
     """The batched solver on the full 1024^2 problem, whose two finest levels
-    live in global memory: with the single-pass smoother (default) and with
-    one pass per half-sweep.  Both match the oracle."""
+    live in global memory: with the single-pass smoother (default, and with
+    narrow 40-column strips, and on level 0 only) and with one pass per
+    half-sweep.  All match the oracle."""
     prob = P.config_problem(1)
-    opts = M.default_opts(precision=1, inner_floor=1e-6, plain_sweeps=plain)
+    opts = M.default_opts(precision=1, inner_floor=1e-6, **extra)
     H = M.Hierarchy.from_problem(prob, opts)
     xs, sts = M.batch_solve([H], [H.rhs_for(prob)], 1e-8)
     xr, sr = _oracle_solution("grf-1024", prob)
@@ -301,3 +302,14 @@ def test_uneven_batch_full_size(M):
         xr, _ = R.solve(R.lift_rhs(), 1e-8)
         err = np.linalg.norm(xs[j].cpu().numpy() - xr) / np.linalg.norm(xr)
         assert err <= SOL_RTOL, (side, err)
+
+
+def test_tuner_picks_a_candidate(M):
+    """The autotuner times every candidate tile shape on a small batch, all of
+    them solve, and it returns the fastest."""
+    from paper_math_9809043_gb300 import tune as TU
+    probs = [P.config_problem(1, scale=256) for _ in range(2)]
+    cands = [{}, {"plain_sweeps": 1}, {"fuse_width": 64}]
+    fastest, times = TU.tune(probs, steps=1, candidates=cands)
+    assert fastest in cands and set(times) == {TU.key_of(c) for c in cands}
+    assert times[TU.key_of(fastest)] == min(times.values())
