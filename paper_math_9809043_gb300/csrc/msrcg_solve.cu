@@ -552,6 +552,9 @@ constexpr int kFuseShare = MSRCG_FUSE_SHARE;  // threads per ring column
 // (at most kFuseMaxM + 1) dealt round kFuseShare threads
 constexpr int kFuseE = (kFuseMaxM + 1 + kFuseShare - 1) / kFuseShare;
 constexpr int kFuseRoleZ = kFuseShare > 1 ? 1 : 0;  // share loading rp / z, adding the black r.z
+// share with the fewest stages: the result (pre) / write-back (post) step and
+// the r rows of the post-smoothing dot
+constexpr int kFuseRoleR = kFuseShare - 1;
 
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
@@ -625,8 +628,8 @@ __device__ V fused_smooth(const DevLevel& L, int m, bool pre, unsigned win_off, 
     const bool mine = live && col >= 1 && col <= Ws - 2;  // a loaded cell
     const bool face = live && col >= 1 && col <= Ws - 1;  // a loaded x-face (west of cell i)
     const bool own = live && i >= a0 && i < a1;           // a cell this strip writes
-    // loads (share 0: T rows; share 1: rp and z rows; share 2: r rows) walk
-    // down the level with running pointers
+    // loads (share 0: T rows; share 1: rp and z rows; the last share: r rows)
+    // walk down the level with running pointers
     const float* pTx = gTx + (i < 0 ? 0 : i);
     const float* pTy = gTy + (i < 0 ? 0 : i);
     const float* prp = grp + off + i;
@@ -670,7 +673,7 @@ __device__ V fused_smooth(const DevLevel& L, int m, bool pre, unsigned win_off, 
       int rs = 0;
       if (!pre) {
         const int jr = s + kFuseAhead - 2 * (S - 1);
-        if (hs == kFuseShare - 1 && own && jr >= 0 && jr < ny) {
+        if (hs == kFuseRoleR && own && jr >= 0 && jr < ny) {
           V* dst = sr + (jr % DR) * Ws + col;
           if (sizeof(V) == 8) cp_async8(dst, gr + off + px * jr + i);
           else cp_async4(dst, gr + off + px * jr + i);
@@ -717,8 +720,8 @@ __device__ V fused_smooth(const DevLevel& L, int m, bool pre, unsigned win_off, 
             if (!pre && q == S - 1 && own) acc += sr[rs] * (V)v[e];
           }
         }
-        if (hs == 0) {
-          if (pre && par == 1 && s < ny) sz[sbo + col] = 0.f;  // black cell of stage 0's row
+        if (hs == 0 && pre && par == 1 && s < ny) sz[sbo + col] = 0.f;  // black cell of stage 0's row
+        if (hs == kFuseRoleR) {
           if (own && s >= lag && s < lag + ny) {
             int r0 = sbo - lago;
             if (r0 < 0) r0 += DW;
