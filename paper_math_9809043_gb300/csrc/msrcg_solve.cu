@@ -436,6 +436,69 @@ __device__ V t_smooth(BlockTeam& tm, const DevLevel& L, const TLevel<RP>& S, int
   const V* r = (const V*)L.r;
   RP* rp = (RP*)L.rp;
   RP* z = (RP*)L.z;
+  const Geo& G = S.G;
+  if (G.n <= (int)blockDim.x) {
+    // one thread per cell: its face transmissibilities and diagonal stay in
+    // registers for all half-sweeps (the terms and their order as in
+    // diag_of / gs_value, so the values are the same)
+    const int c = threadIdx.x;
+    const bool own = c < G.n;
+    int i = 0, j = 0, k = 0, pc = 0;
+    RP tw = 0, te = 0, ts = 0, tn = 0, tb = 0, tt = 0, d = 1;
+    if (own) {
+      i = c % G.nx;
+      const int row = c / G.nx;
+      const Row rw = make_row<DIM>(G, row);
+      j = rw.j;
+      k = rw.k;
+      pc = rw.pc + i;
+      tw = S.Tx[rw.fx + i];
+      te = S.Tx[rw.fx + i + 1];
+      ts = S.Ty[rw.fy + i];
+      tn = S.Ty[rw.fy + i + G.nx];
+      d = tw;
+      d += te;
+      d += ts;
+      d += tn;
+      if (DIM == 3) {
+        tb = S.Tz[rw.fz + i];
+        tt = S.Tz[rw.fz + i + G.nx * G.ny];
+        d += tb;
+        d += tt;
+      }
+    }
+    const int colour = (i + j + k) & 1;
+    auto gs = [&]() __attribute__((always_inline)) {
+      RP dd, sm = rp[pc];
+      gs_terms2<RP>(dd, sm, tw, te, ts, tn, z[pc - 1], z[pc + 1], z[pc - G.px], z[pc + G.px]);
+      if (DIM == 3) {
+        sm += tb * z[pc - G.plane];
+        sm += tt * z[pc + G.plane];
+      }
+      z[pc] = quot<RP>(sm, d);
+    };
+    if (own) {
+      if (from_zero) {
+        RP rhs;
+        if (sizeof(V) != sizeof(RP)) {
+          rhs = (RP)r[pc];
+          rp[pc] = rhs;
+        } else {
+          rhs = rp[pc];
+        }
+        z[pc] = colour == 0 ? quot<RP>(rhs, d) : (RP)0;
+      } else if (colour == 0) {
+        gs();
+      }
+    }
+    tm.sync();
+    for (int h = 1; h <= 2 * m; ++h) {
+      if (own && colour == (h & 1)) gs();
+      if (h == 2 * m && dot) return tm.sum<V>(own ? r[pc] * (V)z[pc] : (V)0);
+      tm.sync();
+    }
+    return (V)0;
+  }
   t_sweep<DIM, RP, V>(S, 0, r, rp, z, from_zero ? kZero : kNormal);
   tm.sync();
   for (int s = 0; s < m; ++s) {
