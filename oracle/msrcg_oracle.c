@@ -16,7 +16,9 @@
  *     transmissibility is 2 (h_perp/h_par) K_cell; a Neumann face has T = 0
  *     (Sec. 3, "the type of boundary condition affects the discretized K").
  *   - unknowns are visited in red-black order (colour = (i+j+k) mod 2, red
- *     first); the splitting of Sec. 3 is applied in that ordering.
+ *     first); the symmetric Gauss-Seidel splitting of Sec. 3 is applied in
+ *     that ordering.  The modified Jacobi splitting of Sec. 3 (P = 2D) is the
+ *     alternative smoother (or_set_splitting).
  *   - level sides: n_{k+1} = max(2, floor(n_k/s + 1/2)) per axis while the
  *     axis is longer than the coarsest side limit; stop when no axis is.
  *   - coarse transmissibility: the face-dual series/parallel reading of the
@@ -50,7 +52,7 @@ typedef struct {
   int *i0[3], *i1[3];
   double *w[3];
   /* work vectors */
-  double *b, *x, *r, *p, *z, *q, *t;
+  double *b, *x, *r, *p, *z, *q, *t, *aw; /* aw: A x of a Jacobi step */
 } or_level;
 
 typedef struct {
@@ -64,6 +66,7 @@ typedef struct {
   int nc;
   int64_t iters[OR_MAXLEV], calls[OR_MAXLEV];
   int status;
+  int splitting;                        /* 0: symmetric Gauss-Seidel, 1: modified Jacobi */
 } or_hier;
 
 static int64_t idx3(int i, int j, int k, int nx, int ny) {
@@ -418,6 +421,29 @@ static void sgs_step(const or_level *L, const double *rhs, double *x) {
   colour_sweep(L, 0, rhs, x); /* backward: red */
 }
 
+/* ---------------------------------------------------------------------------
+ * Modified Jacobi splitting, Sec. 3: P = 2D, Q = D - U - L.  One step
+ * x <- x + P^-1 (rhs - A x) updates every cell from the old values:
+ * x_c += (rhs_c - (A x)_c) / (2 D_c), D_c = sum of the cell's face T.
+ * ------------------------------------------------------------------------- */
+static void jacobi_step(const or_level *L, const double *rhs, double *x) {
+  int nx = L->nx, ny = L->ny, nz = L->nz, d3 = L->Tz != NULL;
+  apply(L, x, L->aw);
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        int64_t c = idx3(i, j, k, nx, ny);
+        double d = T_xl(L, i, j, k) + T_xl(L, i + 1, j, k) + T_yl(L, i, j, k) + T_yl(L, i, j + 1, k);
+        if (d3) d += T_zl(L, i, j, k) + T_zl(L, i, j, k + 1);
+        x[c] += (rhs[c] - L->aw[c]) / (2.0 * d);
+      }
+}
+
+static void smooth_step(const or_hier *H, const or_level *L, const double *rhs, double *x) {
+  if (H->splitting == 1) jacobi_step(L, rhs, x);
+  else sgs_step(L, rhs, x);
+}
+
 static double dot(const double *a, const double *b, int64_t n) {
   double s = 0.0;
   for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
@@ -493,6 +519,7 @@ void or_free(or_hier *H) {
     free(L->z);
     free(L->q);
     free(L->t);
+    free(L->aw);
   }
   free(H->chol);
   free(H);
@@ -528,6 +555,7 @@ or_hier *or_build(int dim, const int n[3], const double h[3], const double *K, i
     L->z = calloc(L->n, sizeof(double));
     L->q = calloc(L->n, sizeof(double));
     L->t = calloc(L->n, sizeof(double));
+    L->aw = calloc(L->n, sizeof(double));
   }
   or_face_trans(dim, n, h, K, ncomp, bc, H->L[0].Tx, H->L[0].Ty, H->L[0].Tz);
   for (int k = 0; k + 1 < nlev; ++k) {
@@ -565,6 +593,8 @@ void or_get_T(const or_hier *H, int k, double *Tx, double *Ty, double *Tz) {
   if (L->Tz && Tz) memcpy(Tz, L->Tz, sizeof(double) * L->nx * L->ny * (L->nz + 1));
 }
 void or_set_eps2(or_hier *H, double eps2) { H->eps2 = eps2; }
+/* 0: symmetric Gauss-Seidel (red-black), 1: modified Jacobi (Sec. 3) */
+void or_set_splitting(or_hier *H, int splitting) { H->splitting = splitting; }
 void or_get_stats(const or_hier *H, int64_t *iters, int64_t *calls) {
   for (int k = 0; k < H->nlev; ++k) {
     iters[k] = H->iters[k];
@@ -593,13 +623,13 @@ static void precond(or_hier *H, int k, const double *r, double *z) {
   }
   or_level *C = &H->L[k + 1];
   memset(z, 0, sizeof(double) * L->n);
-  for (int s = 0; s < H->m; ++s) sgs_step(L, r, z);
+  for (int s = 0; s < H->m; ++s) smooth_step(H, L, r, z);
   apply(L, z, L->t);
   for (int64_t i = 0; i < L->n; ++i) L->t[i] = r[i] - L->t[i];
   restrict_(L, C, L->t, C->b);
   pcg(H, k + 1, C->b, C->x);
   prolong_add(L, C, C->x, z);
-  for (int s = 0; s < H->m; ++s) sgs_step(L, r, z);
+  for (int s = 0; s < H->m; ++s) smooth_step(H, L, r, z);
 }
 
 /* ---------------------------------------------------------------------------
@@ -683,6 +713,7 @@ int or_solve(or_hier *H, const double *b, double tau, double *x, double *out) {
  * ------------------------------------------------------------------------- */
 void or_apply_level(const or_hier *H, int k, const double *x, double *y) { apply(&H->L[k], x, y); }
 void or_sgs_level(const or_hier *H, int k, const double *rhs, double *x) { sgs_step(&H->L[k], rhs, x); }
+void or_jacobi_level(const or_hier *H, int k, const double *rhs, double *x) { jacobi_step(&H->L[k], rhs, x); }
 void or_sweep_level(const or_hier *H, int k, int colour, const double *rhs, double *x) {
   colour_sweep(&H->L[k], colour, rhs, x);
 }

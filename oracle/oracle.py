@@ -71,7 +71,9 @@ def lib():
         L.or_reset_stats.restype = None
         L.or_solve.argtypes = [C.c_void_p, _dp, C.c_double, _dp, _dp]
         L.or_solve.restype = C.c_int
-        for name in ("or_apply_level", "or_sgs_level", "or_restrict_level", "or_prolong_level"):
+        L.or_set_splitting.argtypes = [C.c_void_p, C.c_int]
+        L.or_set_splitting.restype = None
+        for name in ("or_apply_level", "or_sgs_level", "or_jacobi_level", "or_restrict_level", "or_prolong_level"):
             getattr(L, name).argtypes = [C.c_void_p, C.c_int, _dp, _dp]
             getattr(L, name).restype = None
         L.or_sweep_level.argtypes = [C.c_void_p, C.c_int, C.c_int, _dp, _dp]
@@ -143,7 +145,9 @@ def transfer_table(nf, nc):
 class Hierarchy:
     """Oracle level hierarchy of one problem (Sec. 2.3 / Sec. 3)."""
 
-    def __init__(self, prob, s=4, m=4, f=0.1, maxside=None, maxit_outer=200, maxit_inner=500):
+    def __init__(self, prob, s=4, m=4, f=0.1, maxside=None, maxit_outer=200, maxit_inner=500, splitting=0):
+        """splitting: 0 = symmetric Gauss-Seidel (red-black), 1 = modified
+        Jacobi P = 2D (Sec. 3)."""
         self.prob = prob
         self.dim = prob.dim
         maxside = maxside or (8 if prob.dim == 2 else 4)
@@ -153,6 +157,7 @@ class Hierarchy:
                                  maxit_outer, maxit_inner)
         if not self._h:
             raise ValueError("oracle build failed")
+        lib().or_set_splitting(self._h, int(splitting))
         self.nlev = lib().or_nlev(self._h)
         self.dims = []
         for k in range(self.nlev):
@@ -207,6 +212,11 @@ class Hierarchy:
     def sgs(self, k, rhs, x):
         x = np.array(x, np.float64)
         lib().or_sgs_level(self._h, k, np.ascontiguousarray(rhs, np.float64), x)
+        return x
+
+    def jacobi(self, k, rhs, x):
+        x = np.array(x, np.float64)
+        lib().or_jacobi_level(self._h, k, np.ascontiguousarray(rhs, np.float64), x)
         return x
 
     def sweep(self, k, colour, rhs, x):

@@ -437,6 +437,97 @@ def test_preconditioner_is_eq_2_10(n, m):
 
 
 # --------------------------------------------------------------------------
+# Modified Jacobi splitting (Sec. 3): P = 2D, Q = D - U - L
+# --------------------------------------------------------------------------
+def _jacobi_PQ(A):
+    D = np.diag(np.diag(A))
+    return 2.0 * D, D - np.triu(A, 1) - np.tril(A, -1)
+
+
+@pytest.mark.parametrize("n", [(8, 6), (5, 4, 3)])
+def test_jacobi_step_is_splitting_update(n):
+    """One modified Jacobi step equals x + P^-1 (rhs - A x) = P^-1 (Q x + rhs)
+    with P = 2D and Q = D - U - L taken from the decomposition A = D + U + L
+    (Sec. 3); P - Q = A, and the step damps in the A-norm."""
+    rng = np.random.default_rng(13)
+    N = int(np.prod(n))
+    prob = _prob(n, 10.0 ** rng.uniform(-3, 3, N))
+    H = O.Hierarchy(prob, splitting=1)
+    A = H.dense(0)
+    Pm, Qm = _jacobi_PQ(A)
+    np.testing.assert_allclose(Pm - Qm, A, atol=1e-12 * np.abs(A).max())
+    rhs, x = rng.standard_normal(N), rng.standard_normal(N)
+    ex = np.linalg.solve(Pm, Qm @ x + rhs)
+    np.testing.assert_allclose(H.jacobi(0, rhs, x), ex, rtol=1e-10, atol=1e-12)
+    Hm = np.linalg.solve(Pm, Qm)
+    Lc = np.linalg.cholesky(A)
+    assert np.linalg.norm(Lc.T @ Hm @ np.linalg.inv(Lc.T), 2) < 1.0
+
+
+def test_modified_jacobi_removes_checkerboard_mode():
+    """Constant K: on an interior cell the checkerboard vector v = (-1)^(i+j)
+    gives (A v)_c = sum_f T_f (v_c - v_nb) = 2 D_c v_c, so one modified Jacobi
+    step (P = 2D) leaves exactly 0 there, while the standard Jacobi step
+    (P = D) only flips the sign -- the damping of checkerboard modes that Sec. 3
+    gives as the reason for the modified splitting."""
+    nx, ny = 12, 10
+    prob = _prob((nx, ny), np.ones(nx * ny))
+    H = O.Hierarchy(prob, splitting=1)
+    i, j = np.meshgrid(np.arange(nx), np.arange(ny))
+    v = ((-1.0) ** (i + j)).reshape(-1)
+    interior = ((i > 0) & (i < nx - 1) & (j > 0) & (j < ny - 1)).reshape(-1)
+    out = H.jacobi(0, np.zeros(nx * ny), v)
+    assert np.abs(out[interior]).max() == 0.0
+    assert np.abs(out[~interior]).max() > 0.0
+    A = H.dense(0)
+    std = v - (A @ v) / np.diag(A)
+    np.testing.assert_allclose(std[interior], -v[interior], atol=1e-12)
+
+
+@pytest.mark.parametrize("n,m", [((16, 12), 4), ((8, 8, 8), 2)])
+def test_jacobi_preconditioner_is_eq_2_10(n, m):
+    """Two levels with the exact coarse inverse and the modified Jacobi
+    smoother: the preconditioner applied column by column equals eq. 2.10
+    with P = 2D, Q = D - U - L, and is symmetric positive definite."""
+    rng = np.random.default_rng(16)
+    N = int(np.prod(n))
+    prob = _prob(n, 10.0 ** rng.uniform(-2, 2, N))
+    H = O.Hierarchy(prob, m=m, splitting=1)
+    assert H.nlev == 2
+    H.set_eps2(1e-40)
+    Mcols = np.stack([H.precond(0, np.eye(N)[i]) for i in range(N)], axis=1)
+    A = H.dense(0)
+    Ac = H.dense(1)
+    E = _E_dense_interp(n, H.dims[1][:len(n)])
+    W = E @ np.linalg.solve(Ac, E.T)
+    Pm, Qm = _jacobi_PQ(A)
+    Pi = np.linalg.inv(Pm)
+    Hm = Pi @ Qm
+    Ht = Qm @ Pi
+    M = np.linalg.matrix_power(Hm, m) @ W @ np.linalg.matrix_power(Ht, m)
+    for j in range(2 * m):
+        M += np.linalg.matrix_power(Hm, j) @ Pi
+    scale = np.abs(M).max()
+    np.testing.assert_allclose(Mcols, M, atol=1e-9 * scale)
+    np.testing.assert_allclose(Mcols, Mcols.T, atol=1e-9 * scale)
+    assert np.linalg.eigvalsh(0.5 * (Mcols + Mcols.T)).min() > 0
+
+
+@pytest.mark.parametrize("n", [(29, 19), (12, 10, 9)])
+def test_jacobi_solve_matches_direct_solve(n):
+    rng = np.random.default_rng(19)
+    N = int(np.prod(n))
+    prob = _prob(n, 10.0 ** rng.uniform(-3, 3, N))
+    H = O.Hierarchy(prob, splitting=1)
+    b = H.lift_rhs()
+    x, st = H.solve(b, 1e-13)
+    assert st["status"] == 0
+    ex = spla.spsolve(_sparse_A(H, 0), b)
+    assert np.linalg.norm(x - ex) / np.linalg.norm(ex) < 1e-10
+    assert st["relres_true"] < 1e-12
+
+
+# --------------------------------------------------------------------------
 # PCG (Sec. 3, Templates Fig. 2.5) and the level tolerance test
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("n", [(32, 32), (29, 19), (40, 9), (12, 10, 9)])
