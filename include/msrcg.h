@@ -76,7 +76,9 @@ typedef struct {
                           shared memory holds); a tile shape the autotuner may set */
   int fuse_min_cells;  /* single-pass smoothing only on levels of at least this many cells
                           (0 = 4096) */
-  int reserved[4];
+  int splitting;       /* smoother of eq. 2.10 (Sec. 3): 0 = symmetric Gauss-Seidel in red-black
+                          order (default), 1 = modified Jacobi P = 2D, Q = D - U - L */
+  int reserved[3];
 } msrcg_opts;
 
 /* Per-solve statistics.  iters[k] = PCG iterations summed over all calls at

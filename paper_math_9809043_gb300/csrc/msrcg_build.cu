@@ -466,6 +466,7 @@ extern "C" int msrcg_default_opts(msrcg_opts* o) {
   o->plain_sweeps = 0;
   o->fuse_width = 0;
   o->fuse_min_cells = 0;
+  o->splitting = 0;
   return MSRCG_OK;
 }
 
@@ -502,7 +503,7 @@ int msrcg_build_ex(const msrcg_grid* grid, const double* K, int ncomp, const uin
   if (opts) o = *opts;
   else msrcg_default_opts(&o);
   if (o.scale < 2 || o.m < 1 || !(o.f > 0.0) || o.maxit_outer < 1 || o.maxit_inner < 1 || o.fuse_width < 0 ||
-      o.fuse_min_cells < 0)
+      o.fuse_min_cells < 0 || o.splitting < 0 || o.splitting > 1)
     return MSRCG_EINVAL;
   if (o.precision != 0 && o.precision != 1) return MSRCG_EINVAL;
   if (o.coarsest_max_side <= 0) o.coarsest_max_side = dim == 2 ? 8 : 4;
@@ -845,7 +846,7 @@ int msrcg_build_into(msrcg_hier* h, const msrcg_grid* grid, const double* K, int
   if (opts) o = *opts;
   else msrcg_default_opts(&o);
   if (o.scale < 2 || o.m < 1 || !(o.f > 0.0) || o.maxit_outer < 1 || o.maxit_inner < 1 || o.fuse_width < 0 ||
-      o.fuse_min_cells < 0)
+      o.fuse_min_cells < 0 || o.splitting < 0 || o.splitting > 1)
     return MSRCG_EINVAL;
   if (o.precision != 0 && o.precision != 1) return MSRCG_EINVAL;
   if (o.coarsest_max_side <= 0) o.coarsest_max_side = dim == 2 ? 8 : 4;

@@ -427,12 +427,62 @@ __device__ __forceinline__ V t_sweep(const TLevel<RP>& S, int colour, const V* r
   return acc;
 }
 
+// m modified Jacobi steps (P = 2D, Q = D - U - L, Sec. 3): every cell moves
+// from the old values, z <- z + (rp - A z) / (2D), with A z formed first
+// (into the t buffer, free during smoothing); from zero the first step is
+// z = rp / (2D).  Returns r . z after the last step when `dot`.
+template <int DIM, typename RP, typename V>
+__device__ V t_jacobi(BlockTeam& tm, const DevLevel& L, const TLevel<RP>& S, int m, bool from_zero, bool dot) {
+  const V* r = (const V*)L.r;
+  RP* rp = (RP*)L.rp;
+  RP* z = (RP*)L.z;
+  RP* w = (RP*)L.t;
+  const Geo& G = S.G;
+  int s0 = 0;
+  if (from_zero) {
+    for_cells<DIM>(S.all, G, [&](int i, const Row& rw) {
+      const int pc = rw.pc + i;
+      RP rhs;
+      if (sizeof(V) != sizeof(RP)) {
+        rhs = (RP)r[pc];
+        rp[pc] = rhs;
+      } else {
+        rhs = rp[pc];
+      }
+      const RP d = diag_of<DIM, RP>(G, S.Tx, S.Ty, S.Tz, i, rw);
+      z[pc] = quot<RP>(rhs, d + d);
+    });
+    tm.sync();
+    s0 = 1;
+  }
+  V acc = 0;
+  for (int st = s0; st < m; ++st) {
+    for_cells<DIM>(S.all, G, [&](int i, const Row& rw) {
+      w[rw.pc + i] = apply_value<DIM, RP, RP>(G, S.Tx, S.Ty, S.Tz, z, i, rw);
+    });
+    tm.sync();
+    const bool last = st == m - 1;
+    for_cells<DIM>(S.all, G, [&](int i, const Row& rw) {
+      const int pc = rw.pc + i;
+      const RP d = diag_of<DIM, RP>(G, S.Tx, S.Ty, S.Tz, i, rw);
+      const RP v = z[pc] + quot<RP>(rp[pc] - w[pc], d + d);
+      if (dot && last) acc += r[pc] * (V)v;
+      z[pc] = v;
+    });
+    if (dot && last) return tm.sum<V>(acc);
+    tm.sync();
+  }
+  return (V)0;
+}
+
 // m symmetric Gauss-Seidel steps (the smoothing factors of eq. 2.10):
 // forward red, black, backward black, red; the repeated black half-sweep
 // reproduces the same values, so m steps are the 2m+1 half-sweeps
 // red (black red)^m.  Returns r . z after the last half-sweep when `dot`.
 template <int DIM, typename RP, typename V>
-__device__ V t_smooth(BlockTeam& tm, const DevLevel& L, const TLevel<RP>& S, int m, bool from_zero, bool dot) {
+__device__ V t_smooth(BlockTeam& tm, const DevLevel& L, const TLevel<RP>& S, int m, bool from_zero, bool dot,
+                      int splitting) {
+  if (splitting == 1) return t_jacobi<DIM, RP, V>(tm, L, S, m, from_zero, dot);
   const V* r = (const V*)L.r;
   RP* rp = (RP*)L.rp;
   RP* z = (RP*)L.z;
@@ -870,13 +920,14 @@ struct RecArgs {
   size_t win_bytes;
   bool fuse;
   int fuse_width, fuse_min_cells;
+  int splitting;  // 0: red-black symmetric Gauss-Seidel, 1: modified Jacobi
 };
 
 // Strip width of the single-pass smoother for level L, or 0 for the plain
 // half-sweeps (levels in shared memory, small levels, no room).
 template <typename V>
 __device__ __forceinline__ int fuse_wo(const DevLevel& L, int m, const RecArgs& a) {
-  if (!a.fuse || __isShared(L.z) || (long long)L.nx * L.ny < a.fuse_min_cells) return 0;
+  if (!a.fuse || a.splitting != 0 || __isShared(L.z) || (long long)L.nx * L.ny < a.fuse_min_cells) return 0;
   const int w = fuse_width(m, a.win_bytes, (int)sizeof(V), blockDim.x);
   return a.fuse_width > 0 && a.fuse_width < w ? max(a.fuse_width, kFuseMinWidth) : w;
 }
@@ -944,7 +995,7 @@ struct Ops {
       }
     }
     const TLevel<RP> S = tlevel_of<RP>(L);
-    t_smooth<DIM, RP, V>(tm, L, S, m, true, false);
+    t_smooth<DIM, RP, V>(tm, L, S, m, true, false, a.splitting);
     const RP* rp = (const RP*)L.rp;
     const RP* z = (const RP*)L.z;
     RP* t = (RP*)L.t;
@@ -958,7 +1009,8 @@ struct Ops {
   }
   // z += E x_c on the black cells only: the first post-smoothing half-sweep
   // recomputes every red cell from its black neighbours, so a red cell's
-  // prolonged value would never be read.  Then post-smoothing; returns r.z.
+  // prolonged value would never be read (every cell for the Jacobi smoother).
+  // Then post-smoothing; returns r.z.
   static __device__ V prolong_postsmooth(BlockTeam& tm, const DevLevel& L, const DevLevel& C, int m,
                                          const RecArgs& a) {
     {
@@ -966,9 +1018,16 @@ struct Ops {
       const RP* xc = (const RP*)C.x;
       const Xf X = xf_of(L);
       const Geo Gc = geo_of(C);
-      for_colour<DIM>(team_map((X.nx + 1) >> 1), X, 1, [&](int i, int, const Row& rw) {
-        if (i < X.nx) z[rw.pc + i] += prolong_value<DIM, RP>(X, Gc, xc, i, rw.j, rw.k);
-      });
+      if (a.splitting == 1) {
+        // the Jacobi smoother reads every cell's prolonged value
+        for_cells<DIM>(team_map(X.nx), X, [&](int i, const Row& rw) {
+          z[rw.pc + i] += prolong_value<DIM, RP>(X, Gc, xc, i, rw.j, rw.k);
+        });
+      } else {
+        for_colour<DIM>(team_map((X.nx + 1) >> 1), X, 1, [&](int i, int, const Row& rw) {
+          if (i < X.nx) z[rw.pc + i] += prolong_value<DIM, RP>(X, Gc, xc, i, rw.j, rw.k);
+        });
+      }
     }
     tm.sync();
     if constexpr (DIM == 2 && sizeof(RP) == sizeof(float)) {
@@ -986,7 +1045,7 @@ struct Ops {
         return tm.sum<V>(acc);
       }
     }
-    return t_smooth<DIM, RP, V>(tm, L, tlevel_of<RP>(L), m, false, true);
+    return t_smooth<DIM, RP, V>(tm, L, tlevel_of<RP>(L), m, false, true, a.splitting);
   }
   static __device__ V coarsest(BlockTeam& tm, const DevLevel& L, const RecArgs& a) {
     t_coarsest<DIM, V, RP>(tm, L, a.Ainv, a.ainv_t, a.nc, (const V*)L.r, (RP*)L.z, a.rc);
@@ -1278,6 +1337,7 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallPerSM) k_small(const Prob
       a.fuse = pd.fuse != 0;
       a.fuse_width = pd.fuse_width;
       a.fuse_min_cells = pd.fuse_min_cells;
+      a.splitting = pd.splitting;
     }
     a.floor2 = S->inner_floor2;
     a.floor2_f = (float)a.floor2;
@@ -1551,6 +1611,72 @@ __global__ void k_prolong_black(DevLevel L, DevLevel C) {
   });
 }
 
+// Modified Jacobi on a wide level (see t_jacobi): phase 0 (from zero)
+// z = rp / 2D, rounding r into rp when the vector types differ; phase 1
+// t = A z; phase 2 z += (rp - t) / 2D.
+template <int DIM, typename RP, typename V>
+__global__ void k_jacobi(DevLevel L, int phase) {
+  const RP *Tx = (const RP*)L.T[0], *Ty = (const RP*)L.T[1], *Tz = (const RP*)L.T[2];
+  const V* r = (const V*)L.r;
+  RP* rp = (RP*)L.rp;
+  RP* z = (RP*)L.z;
+  RP* t = (RP*)L.t;
+  for_cells<DIM>(grid_map(), L, [&](int i, const Row& rw) {
+    const int pc = rw.pc + i;
+    if (phase == 1) {
+      t[pc] = apply_value<DIM, RP, RP>(L, Tx, Ty, Tz, z, i, rw);
+      return;
+    }
+    const RP d = diag_of<DIM, RP>(L, Tx, Ty, Tz, i, rw);
+    if (phase == 0) {
+      RP rhs;
+      if (sizeof(V) != sizeof(RP)) {
+        rhs = (RP)r[pc];
+        rp[pc] = rhs;
+      } else {
+        rhs = rp[pc];
+      }
+      z[pc] = quot<RP>(rhs, d + d);
+    } else {
+      z[pc] = z[pc] + quot<RP>(rp[pc] - t[pc], d + d);
+    }
+  });
+}
+
+// The last post-smoothing Jacobi update with rho = r . z and beta (as
+// k_sweep_rho).
+template <int DIM, typename RP, typename V>
+__global__ void k_jacobi_rho(DevLevel L, int k, SolveState* S, double* partials) {
+  const RP *Tx = (const RP*)L.T[0], *Ty = (const RP*)L.T[1], *Tz = (const RP*)L.T[2];
+  const V* r = (const V*)L.r;
+  const RP* rp = (const RP*)L.rp;
+  const RP* t = (const RP*)L.t;
+  RP* z = (RP*)L.z;
+  V acc = 0;
+  for_cells<DIM>(grid_map(), L, [&](int i, const Row& rw) {
+    const int pc = rw.pc + i;
+    const RP d = diag_of<DIM, RP>(L, Tx, Ty, Tz, i, rw);
+    const RP v = z[pc] + quot<RP>(rp[pc] - t[pc], d + d);
+    acc += r[pc] * (V)v;
+    z[pc] = v;
+  });
+  grid_total(acc, partials, &S->ticket[k], [&](double rho) {
+    LevelState& ls = S->lv[k];
+    ls.rho = rho;
+    ls.beta = ls.it == 0 ? 0.0 : rho / ls.rho_old;
+    ls.beta_f = (float)ls.beta;
+  });
+}
+
+// z += E x_c on every cell (the Jacobi smoother reads them all)
+template <int DIM, typename RP>
+__global__ void k_prolong_all(DevLevel L, DevLevel C) {
+  const RP* xc = (const RP*)C.x;
+  RP* z = (RP*)L.z;
+  for_cells<DIM>(grid_map(), L,
+                 [&](int i, const Row& rw) { z[rw.pc + i] += prolong_value<DIM, RP>(L, C, xc, i, rw.j, rw.k); });
+}
+
 // p = z (first iteration) or z + beta p
 template <typename V, typename RP>
 __global__ void k_direction(DevLevel L, int k, SolveState* S) {
@@ -1747,6 +1873,21 @@ void emit_pcg(Emit& E, int k, cudaStream_t s);
 template <int DIM, typename RP, typename V>
 void emit_smooth(const DevLevel& L, int m, bool from_zero, bool with_rho, int k, msrcg_hier* h, int gmax, cudaStream_t s) {
   const Launch lp = pairs_launch(L, gmax), lc = cells_launch(L, gmax);
+  if (h->o.splitting == 1) {
+    int s0 = 0;
+    if (from_zero) {
+      k_jacobi<DIM, RP, V><<<lc.grid, lc.block, 0, s>>>(L, 0);
+      s0 = 1;
+    }
+    for (int i = s0; i < m; ++i) {
+      k_jacobi<DIM, RP, V><<<lc.grid, lc.block, 0, s>>>(L, 1);
+      if (with_rho && i == m - 1)
+        k_jacobi_rho<DIM, RP, V><<<lc.grid, lc.block, 0, s>>>(L, k, h->dS, h->partials + (size_t)k * kMaxGrid);
+      else
+        k_jacobi<DIM, RP, V><<<lc.grid, lc.block, 0, s>>>(L, 2);
+    }
+    return;
+  }
   if (from_zero) k_sweep<DIM, RP, V><<<lc.grid, lc.block, 0, s>>>(L, 0, 1);
   else k_sweep<DIM, RP, V><<<lp.grid, lp.block, 0, s>>>(L, 0, 0);
   for (int i = 0; i < m; ++i) {
@@ -1778,8 +1919,10 @@ void emit_precond(Emit& E, int k, cudaStream_t s) {
   // coarse solve: A_c^-1 applied by the PCG one level down (Sec. 2.3)
   if (k + 1 < h->ks) emit_pcg<DIM, RP>(E, k + 1, s);
   else k_small<DIM, RP><<<1, kSmallThreads, h->sub_smem, s>>>(h->dP, nullptr, 1, k + 1, 0, nullptr, h->sub_smem);
-  // prolongation (black cells) and post-smoothing with rho = r . z
-  k_prolong_black<DIM, RP><<<lp.grid, lp.block, 0, s>>>(L, C);
+  // prolongation (black cells; every cell for the Jacobi smoother) and
+  // post-smoothing with rho = r . z
+  if (h->o.splitting == 1) k_prolong_all<DIM, RP><<<lc.grid, lc.block, 0, s>>>(L, C);
+  else k_prolong_black<DIM, RP><<<lp.grid, lp.block, 0, s>>>(L, C);
   if (k == 0) emit_smooth<DIM, RP, double>(L, m, false, true, k, h, gmax, s);
   else emit_smooth<DIM, RP, RP>(L, m, false, true, k, h, gmax, s);
 }
@@ -1971,6 +2114,7 @@ ProblemDesc make_desc(msrcg_hier* h, const double* b, double* x, double tol) {
   pd.fuse = h->o.plain_sweeps == 0;
   pd.fuse_width = h->o.fuse_width;
   pd.fuse_min_cells = h->o.fuse_min_cells > 0 ? h->o.fuse_min_cells : kFuseMinCells;
+  pd.splitting = h->o.splitting;
   return pd;
 }
 

@@ -160,6 +160,63 @@ def test_full_size_1024_matches_oracle(M, prec):
         _counts_close(st["iters"], sr["iters"], sr["calls"])
 
 
+# ---------------------------------------------------------------------------
+# modified Jacobi splitting (P = 2D, Sec. 3) as the smoother
+# ---------------------------------------------------------------------------
+JACOBI_CASES = [
+    ("cfg0", lambda: P.config_problem(0), 0),
+    ("ragged-37x23-wide", lambda: _prob_uniform((37, 23)), 64),
+    ("grf-128", lambda: P.config_problem(1, scale=128), 0),
+    ("grf-200x72-wide", lambda: P.grf_problem((200, 72), seed=21, ell=6.0, half_span=4.5), 256),
+    ("tiny-3x2", lambda: _prob_uniform((3, 2)), 0),
+    ("chan3d-16", lambda: P.config_problem(2, scale=16), 0),
+    ("ragged3d-13x9x7", lambda: _prob_uniform((13, 9, 7)), 64),
+]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("name,mk,small", JACOBI_CASES, ids=[c[0] for c in JACOBI_CASES])
+def test_solve_jacobi_matches_oracle(M, name, mk, small, prec):
+    """Single solves (wide levels as graph kernels, narrow levels in one CTA)
+    with the modified Jacobi smoother against the oracle's Jacobi solve."""
+    prob = mk()
+    opts = M.default_opts(precision=prec, small_cells=small, splitting=1, inner_floor=1e-6 if prec else 0.0)
+    H = M.Hierarchy.from_problem(prob, opts)
+    x, st = H.solve(H.rhs_for(prob), 1e-8)
+    R = O.Hierarchy(prob, splitting=1)
+    xr, sr = R.solve(R.lift_rhs(), 1e-8)
+    assert sr["status"] == 0 and st["status"] == 0, (st, sr)
+    assert st["relres_true"] < 1e-8
+    err = np.linalg.norm(x.cpu().numpy() - xr) / max(np.linalg.norm(xr), 1e-300)
+    assert err <= SOL_RTOL, err
+    if prec == 0:
+        _counts_close(st["iters"], sr["iters"], sr["calls"])
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batched_jacobi_matches_oracle(M, prec):
+    """The batched solver (whole recursion in one CTA per problem) with the
+    modified Jacobi smoother: the 256^2 GRF problem and ragged 2D / 3D grids."""
+    probs = [P.config_problem(1, scale=256), _prob_uniform((37, 23)), _prob_uniform((13, 9, 7))]
+    opts = M.default_opts(precision=prec, splitting=1, inner_floor=1e-6 if prec else 0.0)
+    for p in probs:
+        H = M.Hierarchy.from_problem(p, opts)
+        xs, sts = M.batch_solve([H], [H.rhs_for(p)], 1e-8)
+        R = O.Hierarchy(p, splitting=1)
+        xr, sr = R.solve(R.lift_rhs(), 1e-8)
+        assert sts[0]["status"] == 0 and sts[0]["relres_true"] < 1e-8, sts[0]
+        err = np.linalg.norm(xs[0].cpu().numpy() - xr) / np.linalg.norm(xr)
+        assert err <= SOL_RTOL, err
+        if prec == 0:
+            _counts_close(sts[0]["iters"], sr["iters"], sr["calls"])
+
+
+def test_splitting_option_validated(M):
+    prob = _prob_uniform((8, 8))
+    with pytest.raises(M.MsrcgError):
+        M.Hierarchy.from_problem(prob, M.default_opts(splitting=2))
+
+
 _ORACLE_CACHE = {}
 
 
