@@ -297,6 +297,34 @@ def run_uneven(args, M, P, dev, stream):
     return out
 
 
+def run_jacobi(args, M, P, dev, stream, nb, size):
+    """The 1024^2 batch with the modified Jacobi smoother (P = 2D) in place of
+    red-black symmetric Gauss-Seidel, FP32 preconditioner: solves/s and
+    iterations per level."""
+    import numpy as np
+    import torch
+    base = P.config_problem(1, scale=size)
+    out = {"workload": f"as the headline ({nb} x {size}^2), smoother = modified Jacobi P = 2D (Sec. 3)"}
+    for prec, key, steps in ((1, "fp32_precond", 2),):
+        opts = M.default_opts(precision=prec, inner_floor=1e-6 if prec else 0.0, splitting=1)
+        hs, bs = [], []
+        for j in range(nb):
+            rng = np.random.default_rng(1001 * 1000 + j)
+            prob = P.Problem(dim=2, n=base.n, h=base.h, K=base.K, bc=base.bc, gD=base.gD,
+                             f=rng.standard_normal(base.N), pbf=base.pbf)
+            h = M.Hierarchy.from_problem(prob, opts, device=dev)
+            hs.append(h)
+            bs.append(h.rhs_for(prob))
+        per, sts = _timed_batch(M, hs, bs, steps, stream, dev)
+        ms = statistics.mean(per)
+        out[key] = {"solves_per_s": nb / (ms / 1e3), "ms_per_batch": ms, "iters": sts[0]["iters"],
+                    "status": sorted({s["status"] for s in sts}),
+                    "relres_true_max": max(s["relres_true"] for s in sts)}
+        del hs, bs
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_3d(args, M, P, dev, stream, nb):
     """128^3 7-point problems on a 3D Gaussian random field (1e9 contrast):
     nb problems per launch with their own sources, and single-solve latency."""
@@ -491,10 +519,11 @@ def main():
         torch.cuda.empty_cache()
 
     # ---- other workloads: uneven batch and 3D (rank 0 only) ----
-    uneven = grid3d = None
+    uneven = grid3d = jacobi = None
     if rank == 0 and not args.no_extra:
         uneven = run_uneven(args, M, P, dev, stream)
         grid3d = run_3d(args, M, P, dev, stream, nb)
+        jacobi = run_jacobi(args, M, P, dev, stream, nb, args.size)
 
     # ---- serving: Poisson arrivals of mixed requests (rank 0 only) ----
     serving = None
@@ -527,7 +556,7 @@ def main():
                            "parallelism": f"independent problems, {world} GPU(s)",
                            "tile_shapes": TU.key_of(tuned) + (" (autotuner record)" if tuned_rec is not None else "")},
                 "status": statuses, "relres_true_max": relres, "iters": sts[0]["iters"],
-                "latency_ms": latency, "fp64_plain": fp64, "uneven_batch": uneven, "grid3d": grid3d,
+                "latency_ms": latency, "fp64_plain": fp64, "uneven_batch": uneven, "grid3d": grid3d, "jacobi": jacobi,
                 "serving": serving, "e2e": e2e, "roofline": roofline,
                 "cpu_baseline": cpu, "clocks": ck, "gpu_launches": args.steps}
         print(json.dumps(line), flush=True)
