@@ -17,8 +17,9 @@
  *     (Sec. 3, "the type of boundary condition affects the discretized K").
  *   - unknowns are visited in red-black order (colour = (i+j+k) mod 2, red
  *     first); the symmetric Gauss-Seidel splitting of Sec. 3 is applied in
- *     that ordering.  The modified Jacobi splitting of Sec. 3 (P = 2D) is the
- *     alternative smoother (or_set_splitting).
+ *     that ordering.  The alternatives (or_set_splitting) are the modified
+ *     Jacobi splitting of Sec. 3 (P = 2D) and symmetric Gauss-Seidel in the
+ *     natural order of the unknowns.
  *   - level sides: n_{k+1} = max(2, floor(n_k/s + 1/2)) per axis while the
  *     axis is longer than the coarsest side limit; stop when no axis is.
  *   - coarse transmissibility: the face-dual series/parallel reading of the
@@ -66,7 +67,8 @@ typedef struct {
   int nc;
   int64_t iters[OR_MAXLEV], calls[OR_MAXLEV];
   int status;
-  int splitting;                        /* 0: symmetric Gauss-Seidel, 1: modified Jacobi */
+  int splitting;                        /* 0: symmetric Gauss-Seidel (red-black), 1: modified
+                                           Jacobi, 2: symmetric Gauss-Seidel (natural order) */
 } or_hier;
 
 static int64_t idx3(int i, int j, int k, int nx, int ny) {
@@ -381,37 +383,53 @@ static void apply(const or_level *L, const double *x, double *y) {
  * (red cells, then black) followed by a backward sweep (black, then red).
  * Each cell update solves row c of A for x_c with the neighbours fixed.
  * ------------------------------------------------------------------------- */
-static void colour_sweep(const or_level *L, int colour, const double *rhs, double *x) {
+/* Gauss-Seidel update of cell (i, j, k): row c of A solved for x_c with the
+ * neighbours held at their current values. */
+static void gs_cell(const or_level *L, int i, int j, int k, const double *rhs, double *x) {
   int nx = L->nx, ny = L->ny, nz = L->nz, d3 = L->Tz != NULL;
-  for (int k = 0; k < nz; ++k)
-    for (int j = 0; j < ny; ++j)
-      for (int i = 0; i < nx; ++i) {
-        if (((i + j + k) & 1) != colour) continue;
-        int64_t c = idx3(i, j, k, nx, ny);
-        double d = 0.0, s = rhs[c], t;
-        t = T_xl(L, i, j, k);
-        d += t;
-        if (i > 0) s += t * x[c - 1];
-        t = T_xl(L, i + 1, j, k);
-        d += t;
-        if (i < nx - 1) s += t * x[c + 1];
-        t = T_yl(L, i, j, k);
-        d += t;
-        if (j > 0) s += t * x[c - nx];
-        t = T_yl(L, i, j + 1, k);
-        d += t;
-        if (j < ny - 1) s += t * x[c + nx];
-        if (d3) {
-          int64_t pl = (int64_t)nx * ny;
-          t = T_zl(L, i, j, k);
-          d += t;
-          if (k > 0) s += t * x[c - pl];
-          t = T_zl(L, i, j, k + 1);
-          d += t;
-          if (k < nz - 1) s += t * x[c + pl];
-        }
-        x[c] = s / d;
-      }
+  int64_t c = idx3(i, j, k, nx, ny);
+  double d = 0.0, s = rhs[c], t;
+  t = T_xl(L, i, j, k);
+  d += t;
+  if (i > 0) s += t * x[c - 1];
+  t = T_xl(L, i + 1, j, k);
+  d += t;
+  if (i < nx - 1) s += t * x[c + 1];
+  t = T_yl(L, i, j, k);
+  d += t;
+  if (j > 0) s += t * x[c - nx];
+  t = T_yl(L, i, j + 1, k);
+  d += t;
+  if (j < ny - 1) s += t * x[c + nx];
+  if (d3) {
+    int64_t pl = (int64_t)nx * ny;
+    t = T_zl(L, i, j, k);
+    d += t;
+    if (k > 0) s += t * x[c - pl];
+    t = T_zl(L, i, j, k + 1);
+    d += t;
+    if (k < nz - 1) s += t * x[c + pl];
+  }
+  x[c] = s / d;
+}
+
+static void colour_sweep(const or_level *L, int colour, const double *rhs, double *x) {
+  for (int k = 0; k < L->nz; ++k)
+    for (int j = 0; j < L->ny; ++j)
+      for (int i = 0; i < L->nx; ++i)
+        if (((i + j + k) & 1) == colour) gs_cell(L, i, j, k, rhs, x);
+}
+
+/* Symmetric Gauss-Seidel in the natural order of the unknowns (i fastest,
+ * then j, then k), the ordering in which A = D + U + L is read literally:
+ * a forward sweep over c = 0 .. N-1, then a backward sweep over N-1 .. 0. */
+static void lex_sgs_step(const or_level *L, const double *rhs, double *x) {
+  for (int k = 0; k < L->nz; ++k)
+    for (int j = 0; j < L->ny; ++j)
+      for (int i = 0; i < L->nx; ++i) gs_cell(L, i, j, k, rhs, x);
+  for (int k = L->nz - 1; k >= 0; --k)
+    for (int j = L->ny - 1; j >= 0; --j)
+      for (int i = L->nx - 1; i >= 0; --i) gs_cell(L, i, j, k, rhs, x);
 }
 
 static void sgs_step(const or_level *L, const double *rhs, double *x) {
@@ -441,6 +459,7 @@ static void jacobi_step(const or_level *L, const double *rhs, double *x) {
 
 static void smooth_step(const or_hier *H, const or_level *L, const double *rhs, double *x) {
   if (H->splitting == 1) jacobi_step(L, rhs, x);
+  else if (H->splitting == 2) lex_sgs_step(L, rhs, x);
   else sgs_step(L, rhs, x);
 }
 
@@ -593,7 +612,8 @@ void or_get_T(const or_hier *H, int k, double *Tx, double *Ty, double *Tz) {
   if (L->Tz && Tz) memcpy(Tz, L->Tz, sizeof(double) * L->nx * L->ny * (L->nz + 1));
 }
 void or_set_eps2(or_hier *H, double eps2) { H->eps2 = eps2; }
-/* 0: symmetric Gauss-Seidel (red-black), 1: modified Jacobi (Sec. 3) */
+/* 0: symmetric Gauss-Seidel (red-black), 1: modified Jacobi, 2: symmetric
+ * Gauss-Seidel in the natural order (Sec. 3) */
 void or_set_splitting(or_hier *H, int splitting) { H->splitting = splitting; }
 void or_get_stats(const or_hier *H, int64_t *iters, int64_t *calls) {
   for (int k = 0; k < H->nlev; ++k) {
@@ -714,6 +734,7 @@ int or_solve(or_hier *H, const double *b, double tau, double *x, double *out) {
 void or_apply_level(const or_hier *H, int k, const double *x, double *y) { apply(&H->L[k], x, y); }
 void or_sgs_level(const or_hier *H, int k, const double *rhs, double *x) { sgs_step(&H->L[k], rhs, x); }
 void or_jacobi_level(const or_hier *H, int k, const double *rhs, double *x) { jacobi_step(&H->L[k], rhs, x); }
+void or_lex_level(const or_hier *H, int k, const double *rhs, double *x) { lex_sgs_step(&H->L[k], rhs, x); }
 void or_sweep_level(const or_hier *H, int k, int colour, const double *rhs, double *x) {
   colour_sweep(&H->L[k], colour, rhs, x);
 }

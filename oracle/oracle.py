@@ -73,7 +73,8 @@ def lib():
         L.or_solve.restype = C.c_int
         L.or_set_splitting.argtypes = [C.c_void_p, C.c_int]
         L.or_set_splitting.restype = None
-        for name in ("or_apply_level", "or_sgs_level", "or_jacobi_level", "or_restrict_level", "or_prolong_level"):
+        for name in ("or_apply_level", "or_sgs_level", "or_jacobi_level", "or_lex_level", "or_restrict_level",
+                     "or_prolong_level"):
             getattr(L, name).argtypes = [C.c_void_p, C.c_int, _dp, _dp]
             getattr(L, name).restype = None
         L.or_sweep_level.argtypes = [C.c_void_p, C.c_int, C.c_int, _dp, _dp]
@@ -147,7 +148,8 @@ class Hierarchy:
 
     def __init__(self, prob, s=4, m=4, f=0.1, maxside=None, maxit_outer=200, maxit_inner=500, splitting=0):
         """splitting: 0 = symmetric Gauss-Seidel (red-black), 1 = modified
-        Jacobi P = 2D (Sec. 3)."""
+        Jacobi P = 2D, 2 = symmetric Gauss-Seidel in the natural order
+        (Sec. 3)."""
         self.prob = prob
         self.dim = prob.dim
         maxside = maxside or (8 if prob.dim == 2 else 4)
@@ -212,6 +214,11 @@ class Hierarchy:
     def sgs(self, k, rhs, x):
         x = np.array(x, np.float64)
         lib().or_sgs_level(self._h, k, np.ascontiguousarray(rhs, np.float64), x)
+        return x
+
+    def lex_sgs(self, k, rhs, x):
+        x = np.array(x, np.float64)
+        lib().or_lex_level(self._h, k, np.ascontiguousarray(rhs, np.float64), x)
         return x
 
     def jacobi(self, k, rhs, x):

@@ -528,6 +528,70 @@ def test_jacobi_solve_matches_direct_solve(n):
 
 
 # --------------------------------------------------------------------------
+# Symmetric Gauss-Seidel in the natural order of the unknowns (Sec. 3 read
+# literally: A = D + U + L with cells numbered i fastest)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [(8, 6), (5, 4, 3)])
+def test_lex_sgs_step_is_splitting_update(n):
+    """One natural-order step equals x + P^-1 (rhs - A x) with
+    P = (D+L) D^-1 (D+U), Q = L D^-1 U taken in the natural numbering."""
+    rng = np.random.default_rng(23)
+    N = int(np.prod(n))
+    prob = _prob(n, 10.0 ** rng.uniform(-3, 3, N))
+    H = O.Hierarchy(prob, splitting=2)
+    A = H.dense(0)
+    Pm, Qm = _sgs_PQ(A, np.arange(N))
+    np.testing.assert_allclose(Pm - Qm, A, atol=1e-12 * np.abs(A).max())
+    rhs, x = rng.standard_normal(N), rng.standard_normal(N)
+    ex = x + np.linalg.solve(Pm, rhs - A @ x)
+    np.testing.assert_allclose(H.lex_sgs(0, rhs, x), ex, rtol=1e-10, atol=1e-12)
+    # a different operator from the red-black step on the same grid
+    assert np.abs(H.lex_sgs(0, rhs, x) - H.sgs(0, rhs, x)).max() > 1e-6
+
+
+@pytest.mark.parametrize("n,m", [((16, 12), 4), ((8, 8, 8), 2)])
+def test_lex_preconditioner_is_eq_2_10(n, m):
+    """Two levels, exact coarse inverse, natural-order SGS smoother: the
+    preconditioner equals eq. 2.10 with that splitting and is SPD."""
+    rng = np.random.default_rng(26)
+    N = int(np.prod(n))
+    prob = _prob(n, 10.0 ** rng.uniform(-2, 2, N))
+    H = O.Hierarchy(prob, m=m, splitting=2)
+    assert H.nlev == 2
+    H.set_eps2(1e-40)
+    Mcols = np.stack([H.precond(0, np.eye(N)[i]) for i in range(N)], axis=1)
+    A = H.dense(0)
+    Ac = H.dense(1)
+    E = _E_dense_interp(n, H.dims[1][:len(n)])
+    W = E @ np.linalg.solve(Ac, E.T)
+    Pm, Qm = _sgs_PQ(A, np.arange(N))
+    Pi = np.linalg.inv(Pm)
+    Hm = Pi @ Qm
+    Ht = Qm @ Pi
+    M = np.linalg.matrix_power(Hm, m) @ W @ np.linalg.matrix_power(Ht, m)
+    for j in range(2 * m):
+        M += np.linalg.matrix_power(Hm, j) @ Pi
+    scale = np.abs(M).max()
+    np.testing.assert_allclose(Mcols, M, atol=1e-9 * scale)
+    np.testing.assert_allclose(Mcols, Mcols.T, atol=1e-9 * scale)
+    assert np.linalg.eigvalsh(0.5 * (Mcols + Mcols.T)).min() > 0
+
+
+@pytest.mark.parametrize("n", [(29, 19), (12, 10, 9)])
+def test_lex_solve_matches_direct_solve(n):
+    rng = np.random.default_rng(29)
+    N = int(np.prod(n))
+    prob = _prob(n, 10.0 ** rng.uniform(-3, 3, N))
+    H = O.Hierarchy(prob, splitting=2)
+    b = H.lift_rhs()
+    x, st = H.solve(b, 1e-13)
+    assert st["status"] == 0
+    ex = spla.spsolve(_sparse_A(H, 0), b)
+    assert np.linalg.norm(x - ex) / np.linalg.norm(ex) < 1e-10
+    assert st["relres_true"] < 1e-12
+
+
+# --------------------------------------------------------------------------
 # PCG (Sec. 3, Templates Fig. 2.5) and the level tolerance test
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("n", [(32, 32), (29, 19), (40, 9), (12, 10, 9)])
