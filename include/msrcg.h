@@ -77,7 +77,10 @@ typedef struct {
   int fuse_min_cells;  /* single-pass smoothing only on levels of at least this many cells
                           (0 = 4096) */
   int splitting;       /* smoother of eq. 2.10 (Sec. 3): 0 = symmetric Gauss-Seidel in red-black
-                          order (default), 1 = modified Jacobi P = 2D, Q = D - U - L */
+                          order (default), 1 = modified Jacobi P = 2D, Q = D - U - L,
+                          2 = symmetric Gauss-Seidel in the natural order of the cells (a
+                          wavefront over the planes i+j+k = d; single solves then run every
+                          level in one CTA) */
   int reserved[3];
 } msrcg_opts;
 

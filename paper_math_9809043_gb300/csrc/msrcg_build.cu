@@ -503,7 +503,7 @@ int msrcg_build_ex(const msrcg_grid* grid, const double* K, int ncomp, const uin
   if (opts) o = *opts;
   else msrcg_default_opts(&o);
   if (o.scale < 2 || o.m < 1 || !(o.f > 0.0) || o.maxit_outer < 1 || o.maxit_inner < 1 || o.fuse_width < 0 ||
-      o.fuse_min_cells < 0 || o.splitting < 0 || o.splitting > 1)
+      o.fuse_min_cells < 0 || o.splitting < 0 || o.splitting > 2)
     return MSRCG_EINVAL;
   if (o.precision != 0 && o.precision != 1) return MSRCG_EINVAL;
   if (o.coarsest_max_side <= 0) o.coarsest_max_side = dim == 2 ? 8 : 4;
@@ -531,6 +531,9 @@ int msrcg_build_ex(const msrcg_grid* grid, const double* K, int ncomp, const uin
   if (h->N[h->nlev - 1] > 1024) return fail(MSRCG_EINVAL);
   h->ks = h->nlev - 1;
   while (h->ks > 0 && h->N[h->ks - 1] <= o.small_cells) --h->ks;
+  // the natural-order smoother runs plane by plane inside one CTA: every
+  // level of a single solve goes to the single-CTA solver
+  if (o.splitting == 2) h->ks = 0;
 
   const bool f32 = o.precision == 1;
   const size_t rsz = f32 ? sizeof(float) : sizeof(double);
@@ -846,7 +849,7 @@ int msrcg_build_into(msrcg_hier* h, const msrcg_grid* grid, const double* K, int
   if (opts) o = *opts;
   else msrcg_default_opts(&o);
   if (o.scale < 2 || o.m < 1 || !(o.f > 0.0) || o.maxit_outer < 1 || o.maxit_inner < 1 || o.fuse_width < 0 ||
-      o.fuse_min_cells < 0 || o.splitting < 0 || o.splitting > 1)
+      o.fuse_min_cells < 0 || o.splitting < 0 || o.splitting > 2)
     return MSRCG_EINVAL;
   if (o.precision != 0 && o.precision != 1) return MSRCG_EINVAL;
   if (o.coarsest_max_side <= 0) o.coarsest_max_side = dim == 2 ? 8 : 4;

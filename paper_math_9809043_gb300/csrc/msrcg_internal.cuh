@@ -113,7 +113,7 @@ struct ProblemDesc {
   int fuse;              // single-pass smoothing allowed on global-memory levels
   int fuse_width;        // its strip width cap (0: none)
   int fuse_min_cells;    // its smallest level (cells)
-  int splitting;         // 0: red-black symmetric Gauss-Seidel, 1: modified Jacobi
+  int splitting;         // 0: red-black symmetric Gauss-Seidel, 1: modified Jacobi, 2: natural order
 };
 
 }  // namespace msrcg

@@ -475,6 +475,45 @@ __device__ V t_jacobi(BlockTeam& tm, const DevLevel& L, const TLevel<RP>& S, int
   return (V)0;
 }
 
+// m symmetric Gauss-Seidel steps in the natural order of the cells (i
+// fastest, then j, then k): a forward sweep over increasing cell numbers,
+// then a backward one.  A cell's update reads its lower neighbours (i-1, j-1,
+// k-1) from the current sweep and its upper ones from before it, so the cells
+// of one plane i + j + k = d are independent: each sweep runs plane by plane
+// (forward: d ascending, backward: descending), a barrier apart.  Returns
+// r . z at the end when `dot`.
+template <int DIM, typename RP, typename V>
+__device__ V t_lex(BlockTeam& tm, const DevLevel& L, const TLevel<RP>& S, int m, bool from_zero, bool dot) {
+  const V* r = (const V*)L.r;
+  RP* rp = (RP*)L.rp;
+  RP* z = (RP*)L.z;
+  const Geo& G = S.G;
+  if (from_zero) {
+    for_cells<DIM>(S.all, G, [&](int i, const Row& rw) {
+      const int pc = rw.pc + i;
+      if (sizeof(V) != sizeof(RP)) rp[pc] = (RP)r[pc];
+      z[pc] = (RP)0;
+    });
+    tm.sync();
+  }
+  const int rows = G.ny * G.nz, nd = G.nx + G.ny + G.nz - 3;  // planes d = 0 .. nd
+  for (int st = 0; st < m; ++st)
+    for (int dir = 0; dir < 2; ++dir)
+      for (int e = 0; e <= nd; ++e) {
+        const int d = dir == 0 ? e : nd - e;
+        for (int row = threadIdx.x; row < rows; row += blockDim.x) {
+          const Row rw = make_row<DIM>(G, row);
+          const int i = d - rw.j - rw.k;
+          if (i >= 0 && i < G.nx) z[rw.pc + i] = gs_value<DIM, RP, RP>(G, S.Tx, S.Ty, S.Tz, rp[rw.pc + i], z, i, rw);
+        }
+        tm.sync();
+      }
+  if (!dot) return (V)0;
+  V acc = 0;
+  for_cells<DIM>(S.all, G, [&](int i, const Row& rw) { acc += r[rw.pc + i] * (V)z[rw.pc + i]; });
+  return tm.sum<V>(acc);
+}
+
 // m symmetric Gauss-Seidel steps (the smoothing factors of eq. 2.10):
 // forward red, black, backward black, red; the repeated black half-sweep
 // reproduces the same values, so m steps are the 2m+1 half-sweeps
@@ -483,6 +522,7 @@ template <int DIM, typename RP, typename V>
 __device__ V t_smooth(BlockTeam& tm, const DevLevel& L, const TLevel<RP>& S, int m, bool from_zero, bool dot,
                       int splitting) {
   if (splitting == 1) return t_jacobi<DIM, RP, V>(tm, L, S, m, from_zero, dot);
+  if (splitting == 2) return t_lex<DIM, RP, V>(tm, L, S, m, from_zero, dot);
   const V* r = (const V*)L.r;
   RP* rp = (RP*)L.rp;
   RP* z = (RP*)L.z;
@@ -920,7 +960,7 @@ struct RecArgs {
   size_t win_bytes;
   bool fuse;
   int fuse_width, fuse_min_cells;
-  int splitting;  // 0: red-black symmetric Gauss-Seidel, 1: modified Jacobi
+  int splitting;  // 0: red-black symmetric Gauss-Seidel, 1: modified Jacobi, 2: natural-order SGS
 };
 
 // Strip width of the single-pass smoother for level L, or 0 for the plain
@@ -1009,7 +1049,7 @@ struct Ops {
   }
   // z += E x_c on the black cells only: the first post-smoothing half-sweep
   // recomputes every red cell from its black neighbours, so a red cell's
-  // prolonged value would never be read (every cell for the Jacobi smoother).
+  // prolonged value would never be read (every cell for the other smoothers).
   // Then post-smoothing; returns r.z.
   static __device__ V prolong_postsmooth(BlockTeam& tm, const DevLevel& L, const DevLevel& C, int m,
                                          const RecArgs& a) {
@@ -1018,8 +1058,9 @@ struct Ops {
       const RP* xc = (const RP*)C.x;
       const Xf X = xf_of(L);
       const Geo Gc = geo_of(C);
-      if (a.splitting == 1) {
-        // the Jacobi smoother reads every cell's prolonged value
+      if (a.splitting != 0) {
+        // the Jacobi and natural-order smoothers read every cell's prolonged
+        // value
         for_cells<DIM>(team_map(X.nx), X, [&](int i, const Row& rw) {
           z[rw.pc + i] += prolong_value<DIM, RP>(X, Gc, xc, i, rw.j, rw.k);
         });

@@ -211,10 +211,44 @@ def test_batched_jacobi_matches_oracle(M, prec):
             _counts_close(sts[0]["iters"], sr["iters"], sr["calls"])
 
 
+LEX_CASES = [
+    ("cfg0", lambda: P.config_problem(0)),
+    ("ragged-37x23", lambda: _prob_uniform((37, 23))),
+    ("grf-128", lambda: P.config_problem(1, scale=128)),
+    ("tiny-3x2", lambda: _prob_uniform((3, 2))),
+    ("direct-rhs-50x50", lambda: _prob_uniform((50, 50), lifted=False)),
+    ("chan3d-16", lambda: P.config_problem(2, scale=16)),
+    ("ragged3d-13x9x7", lambda: _prob_uniform((13, 9, 7))),
+]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("name,mk", LEX_CASES, ids=[c[0] for c in LEX_CASES])
+def test_solve_natural_order_sgs_matches_oracle(M, name, mk, prec):
+    """Symmetric Gauss-Seidel in the natural order (a plane-by-plane
+    wavefront on the GPU) against the oracle's sequential sweeps, single and
+    batched solves."""
+    prob = mk()
+    opts = M.default_opts(precision=prec, splitting=2, inner_floor=1e-6 if prec else 0.0)
+    H = M.Hierarchy.from_problem(prob, opts)
+    b = H.rhs_for(prob)
+    x, st = H.solve(b, 1e-8)
+    xs, sts = M.batch_solve([H], [b], 1e-8)
+    R = O.Hierarchy(prob, splitting=2)
+    xr, sr = R.solve(R.lift_rhs(), 1e-8)
+    assert sr["status"] == 0 and st["status"] == 0 and sts[0]["status"] == 0, (st, sr)
+    for xg, sg in ((x, st), (xs[0], sts[0])):
+        assert sg["relres_true"] < 1e-8
+        err = np.linalg.norm(xg.cpu().numpy() - xr) / max(np.linalg.norm(xr), 1e-300)
+        assert err <= SOL_RTOL, err
+        if prec == 0:
+            _counts_close(sg["iters"], sr["iters"], sr["calls"])
+
+
 def test_splitting_option_validated(M):
     prob = _prob_uniform((8, 8))
     with pytest.raises(M.MsrcgError):
-        M.Hierarchy.from_problem(prob, M.default_opts(splitting=2))
+        M.Hierarchy.from_problem(prob, M.default_opts(splitting=3))
 
 
 _ORACLE_CACHE = {}
