@@ -297,16 +297,15 @@ def run_uneven(args, M, P, dev, stream):
     return out
 
 
-def run_jacobi(args, M, P, dev, stream, nb, size):
-    """The 1024^2 batch with the modified Jacobi smoother (P = 2D) in place of
-    red-black symmetric Gauss-Seidel, FP32 preconditioner: solves/s and
-    iterations per level."""
+def run_splitting(args, M, P, dev, stream, nb, size, splitting, label):
+    """The 1024^2 batch with another smoother in place of red-black symmetric
+    Gauss-Seidel, FP32 preconditioner: solves/s and iterations per level."""
     import numpy as np
     import torch
     base = P.config_problem(1, scale=size)
-    out = {"workload": f"as the headline ({nb} x {size}^2), smoother = modified Jacobi P = 2D (Sec. 3)"}
-    for prec, key, steps in ((1, "fp32_precond", 2),):
-        opts = M.default_opts(precision=prec, inner_floor=1e-6 if prec else 0.0, splitting=1)
+    out = {"workload": f"as the headline ({nb} x {size}^2), smoother = {label} (Sec. 3)"}
+    for prec, key, steps in ((1, "fp32_precond", 1),):
+        opts = M.default_opts(precision=prec, inner_floor=1e-6 if prec else 0.0, splitting=splitting)
         hs, bs = [], []
         for j in range(nb):
             rng = np.random.default_rng(1001 * 1000 + j)
@@ -519,11 +518,13 @@ def main():
         torch.cuda.empty_cache()
 
     # ---- other workloads: uneven batch and 3D (rank 0 only) ----
-    uneven = grid3d = jacobi = None
+    uneven = grid3d = jacobi = natural = None
     if rank == 0 and not args.no_extra:
         uneven = run_uneven(args, M, P, dev, stream)
         grid3d = run_3d(args, M, P, dev, stream, nb)
-        jacobi = run_jacobi(args, M, P, dev, stream, nb, args.size)
+        jacobi = run_splitting(args, M, P, dev, stream, nb, args.size, 1, "modified Jacobi P = 2D")
+        natural = run_splitting(args, M, P, dev, stream, nb, args.size, 2,
+                                "symmetric Gauss-Seidel in the natural order (plane wavefront)")
 
     # ---- serving: Poisson arrivals of mixed requests (rank 0 only) ----
     serving = None
@@ -557,6 +558,7 @@ def main():
                            "tile_shapes": TU.key_of(tuned) + (" (autotuner record)" if tuned_rec is not None else "")},
                 "status": statuses, "relres_true_max": relres, "iters": sts[0]["iters"],
                 "latency_ms": latency, "fp64_plain": fp64, "uneven_batch": uneven, "grid3d": grid3d, "jacobi": jacobi,
+                "natural_order_sgs": natural,
                 "serving": serving, "e2e": e2e, "roofline": roofline,
                 "cpu_baseline": cpu, "clocks": ck, "gpu_launches": args.steps}
         print(json.dumps(line), flush=True)
