@@ -77,11 +77,21 @@ static int64_t idx3(int i, int j, int k, int nx, int ny) {
 
 /* ---------------------------------------------------------------------------
  * Level sides.  Sec. 3 (scale factor about 4, adjusted to integer sizes).
+ * rule 0: every axis longer than maxside shrinks by the factor s.
+ * rule 1 (Sec. 4.4, anisotropic cells): coarsening aims at square cells --
+ *   the coarse cell size is s times the smallest cell size h_min among the
+ *   axes still longer than maxside, so an axis whose cells are already
+ *   longer shrinks less or not at all (the "semi-coarsening" the paper
+ *   describes); square cells coarsen as rule 0 up to rounding.  Axis a gets
+ *   max(2, min(n_a, round(L_a / (s h_min)))), L_a = n_a h_a.
  * ------------------------------------------------------------------------- */
-int or_hierarchy_dims(int dim, const int n[3], int s, int maxside, int maxlev, int *dims_out) {
+int or_hierarchy_dims2(int dim, const int n[3], const double h[3], int s, int maxside, int rule, int maxlev,
+                       int *dims_out) {
   int cur[3] = {n[0], n[1], dim == 3 ? n[2] : 1};
+  double La[3] = {0.0, 0.0, 0.0};
   int nlev = 0;
-  if (s < 2 || maxside < 1) return OR_EINVAL;
+  if (s < 2 || maxside < 1 || rule < 0 || rule > 1) return OR_EINVAL;
+  for (int a = 0; a < dim; ++a) La[a] = (double)n[a] * h[a];
   for (;;) {
     if (nlev >= maxlev) return OR_EINVAL;
     dims_out[3 * nlev + 0] = cur[0];
@@ -92,14 +102,35 @@ int or_hierarchy_dims(int dim, const int n[3], int s, int maxside, int maxlev, i
     for (int a = 0; a < dim; ++a)
       if (cur[a] > maxside) any = 1;
     if (!any) break;
+    double hmin = 0.0; /* smallest cell size among the axes still coarsened */
+    int first = 1;
+    for (int a = 0; a < dim; ++a) {
+      double ha = La[a] / (double)cur[a];
+      if (cur[a] > maxside && (first || ha < hmin)) {
+        hmin = ha;
+        first = 0;
+      }
+    }
     for (int a = 0; a < dim; ++a) {
       if (cur[a] > maxside) {
-        int c = (2 * cur[a] + s) / (2 * s); /* floor(n/s + 1/2) */
+        int c;
+        if (rule == 0) {
+          c = (2 * cur[a] + s) / (2 * s); /* floor(n/s + 1/2) */
+        } else {
+          double t = La[a] / ((double)s * hmin);
+          c = (int)floor(t + 0.5);
+          if (c > cur[a]) c = cur[a];
+        }
         cur[a] = c < 2 ? 2 : c;
       }
     }
   }
   return nlev;
+}
+
+int or_hierarchy_dims(int dim, const int n[3], int s, int maxside, int maxlev, int *dims_out) {
+  const double h[3] = {1.0, 1.0, 1.0};
+  return or_hierarchy_dims2(dim, n, h, s, maxside, 0, maxlev, dims_out);
 }
 
 /* ---------------------------------------------------------------------------
@@ -303,6 +334,16 @@ void or_transfer_table(int nf, int nc, int *i0, int *i1, double *w) {
       i1[i] = (int)fl + 1;
       w[i] = (double)rem / (double)den;
     }
+  }
+}
+
+/* Piecewise constant interpolation (Sec. 3, "works nearly as well"): a fine
+ * cell takes the value of the coarse cell that contains its centre,
+ * floor((2i+1) nc / (2 nf)). */
+void or_transfer_table_pc(int nf, int nc, int *i0, int *i1, double *w) {
+  for (int i = 0; i < nf; ++i) {
+    i0[i] = i1[i] = (int)(((2 * (int64_t)i + 1) * nc) / (2 * (int64_t)nf));
+    w[i] = 0.0;
   }
 }
 
@@ -544,11 +585,14 @@ void or_free(or_hier *H) {
   free(H);
 }
 
-/* opts: s, m, f, coarsest side limit, max outer / inner iterations */
+/* opts: s, m, f, coarsest side limit, max outer / inner iterations, level-side
+ * rule (0: factor s per long axis, 1: toward square cells), interpolation
+ * (0: linear with zero slope at the boundary, 1: piecewise constant) */
 or_hier *or_build(int dim, const int n[3], const double h[3], const double *K, int ncomp, const unsigned char *bc,
-                  int s, int m, double f, int maxside, int maxit_outer, int maxit_inner) {
+                  int s, int m, double f, int maxside, int maxit_outer, int maxit_inner, int coarsening, int interp) {
   int dims[OR_MAXLEV * 3];
-  int nlev = or_hierarchy_dims(dim, n, s, maxside, OR_MAXLEV, dims);
+  int nlev = or_hierarchy_dims2(dim, n, h, s, maxside, coarsening, OR_MAXLEV, dims);
+  if (interp < 0 || interp > 1) return NULL;
   if (nlev < 1) return NULL;
   or_hier *H = calloc(1, sizeof(or_hier));
   H->dim = dim;
@@ -585,7 +629,8 @@ or_hier *or_build(int dim, const int n[3], const double h[3], const double *K, i
       F->i0[a] = malloc(sizeof(int) * nf[a]);
       F->i1[a] = malloc(sizeof(int) * nf[a]);
       F->w[a] = malloc(sizeof(double) * nf[a]);
-      or_transfer_table(nf[a], nc[a], F->i0[a], F->i1[a], F->w[a]);
+      if (interp == 1) or_transfer_table_pc(nf[a], nc[a], F->i0[a], F->i1[a], F->w[a]);
+      else or_transfer_table(nf[a], nc[a], F->i0[a], F->i1[a], F->w[a]);
     }
   }
   or_level *Lc = &H->L[nlev - 1];

@@ -46,6 +46,10 @@ def lib():
         L = C.CDLL(_LIB)
         L.or_hierarchy_dims.argtypes = [C.c_int, _ip, C.c_int, C.c_int, C.c_int, _ip]
         L.or_hierarchy_dims.restype = C.c_int
+        L.or_hierarchy_dims2.argtypes = [C.c_int, _ip, _dp, C.c_int, C.c_int, C.c_int, C.c_int, _ip]
+        L.or_hierarchy_dims2.restype = C.c_int
+        L.or_transfer_table_pc.argtypes = [C.c_int, C.c_int, _ip, _ip, _dp]
+        L.or_transfer_table_pc.restype = None
         L.or_face_trans.argtypes = [C.c_int, _ip, _dp, _dp, C.c_int, _u8p, _dp, _dp, C.c_void_p]
         L.or_face_trans.restype = None
         L.or_upscale.argtypes = [C.c_int, _ip, _ip, _dp, _dp, C.c_void_p, _dp, _dp, C.c_void_p]
@@ -53,7 +57,7 @@ def lib():
         L.or_transfer_table.argtypes = [C.c_int, C.c_int, _ip, _ip, _dp]
         L.or_transfer_table.restype = None
         L.or_build.argtypes = [C.c_int, _ip, _dp, _dp, C.c_int, _u8p, C.c_int, C.c_int, C.c_double,
-                               C.c_int, C.c_int, C.c_int]
+                               C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]
         L.or_build.restype = C.c_void_p
         L.or_free.argtypes = [C.c_void_p]
         L.or_free.restype = None
@@ -101,10 +105,14 @@ def _d3(v, dim):
     return np.array(a[:3], np.float64)
 
 
-def hierarchy_dims(dim, n, s=4, maxside=None):
+def hierarchy_dims(dim, n, s=4, maxside=None, h=None, coarsening=0):
+    """Level sides; coarsening 1 aims at square cells (needs the cell sizes h)."""
     maxside = maxside or (8 if dim == 2 else 4)
     out = np.zeros(3 * MAXLEV, np.int32)
-    nl = lib().or_hierarchy_dims(dim, _i3(n, dim), s, maxside, MAXLEV, out)
+    if coarsening:
+        nl = lib().or_hierarchy_dims2(dim, _i3(n, dim), _d3(h, dim), s, maxside, coarsening, MAXLEV, out)
+    else:
+        nl = lib().or_hierarchy_dims(dim, _i3(n, dim), s, maxside, MAXLEV, out)
     if nl < 1:
         raise ValueError("invalid grid")
     return [tuple(int(v) for v in out[3 * k:3 * k + 3]) for k in range(nl)]
@@ -135,28 +143,33 @@ def upscale(dim, nf, nc, Tx, Ty, Tz=None):
     return Txc, Tyc, Tzc
 
 
-def transfer_table(nf, nc):
+def transfer_table(nf, nc, interp=0):
+    """1-D extension table: interp 0 = linear with zero slope at the boundary,
+    1 = piecewise constant."""
     i0 = np.zeros(nf, np.int32)
     i1 = np.zeros(nf, np.int32)
     w = np.zeros(nf, np.float64)
-    lib().or_transfer_table(nf, nc, i0, i1, w)
+    (lib().or_transfer_table_pc if interp else lib().or_transfer_table)(nf, nc, i0, i1, w)
     return i0, i1, w
 
 
 class Hierarchy:
     """Oracle level hierarchy of one problem (Sec. 2.3 / Sec. 3)."""
 
-    def __init__(self, prob, s=4, m=4, f=0.1, maxside=None, maxit_outer=200, maxit_inner=500, splitting=0):
+    def __init__(self, prob, s=4, m=4, f=0.1, maxside=None, maxit_outer=200, maxit_inner=500, splitting=0,
+                 coarsening=0, interp=0):
         """splitting: 0 = symmetric Gauss-Seidel (red-black), 1 = modified
         Jacobi P = 2D, 2 = symmetric Gauss-Seidel in the natural order
-        (Sec. 3)."""
+        (Sec. 3).  coarsening: 0 = factor s on every long axis, 1 = toward
+        square cells (Sec. 4.4).  interp: 0 = linear extension, 1 = piecewise
+        constant (Sec. 3)."""
         self.prob = prob
         self.dim = prob.dim
         maxside = maxside or (8 if prob.dim == 2 else 4)
         K = np.ascontiguousarray(prob.K, np.float64)
         self._h = lib().or_build(prob.dim, _i3(prob.n, prob.dim), _d3(prob.h, prob.dim), K.reshape(-1),
                                  K.shape[0], np.ascontiguousarray(prob.bc, np.uint8), s, m, f, maxside,
-                                 maxit_outer, maxit_inner)
+                                 maxit_outer, maxit_inner, coarsening, interp)
         if not self._h:
             raise ValueError("oracle build failed")
         lib().or_set_splitting(self._h, int(splitting))

@@ -335,6 +335,118 @@ def test_extension_reproduces_linear_functions_in_interior():
 
 
 # --------------------------------------------------------------------------
+# Anisotropic cells (Sec. 4.4): coarsening toward square cells, and the
+# piecewise constant extension (Sec. 3)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [(1024, 1024), (96, 64), (512, 256), (128, 128, 128), (64, 32, 16)])
+def test_square_cell_coarsening_keeps_square_grids(n):
+    """With square cells the square-cell rule reproduces the factor-s sides."""
+    h = tuple(1.0 / max(n) for _ in n)
+    assert O.hierarchy_dims(len(n), n, h=h, coarsening=1) == O.hierarchy_dims(len(n), n)
+
+
+def test_square_cell_coarsening_on_ten_to_one_cells():
+    """Table 2's grid, 2000 x 500 cells of aspect 10:1: the first level
+    coarsens y alone (the paper's semi-coarsening), later levels where both
+    axes coarsen have cells within a factor 2 of square, every level is
+    smaller than the one above."""
+    Lx, Ly = 10.0, 0.25
+    dims = O.hierarchy_dims(2, (2000, 500), h=(Lx / 2000, Ly / 500), coarsening=1)
+    assert dims[1][0] == 2000 and dims[1][1] < 500
+    for a, b in zip(dims, dims[1:]):
+        assert b[0] * b[1] < a[0] * a[1]
+    both = [d for d in dims[2:] if d[0] > 8 and d[1] > 8]
+    assert both
+    for d in both:
+        assert 0.5 <= (Lx / d[0]) / (Ly / d[1]) <= 2.0
+    assert max(dims[-1][:2]) <= 8
+
+
+def test_constant_K_upscaling_with_an_unrefined_axis():
+    """Constant K on 10:1 cells: the first square-cell level keeps all 40
+    x-columns (coarsening ratio 1 in x) and the series-parallel coarse T
+    still equals the coarse-grid discretisation."""
+    Kv = 2.3
+    nf, Lx, Ly = (40, 20), 10.0, 0.25
+    h = (Lx / nf[0], Ly / nf[1])
+    nc = O.hierarchy_dims(2, nf, h=h, coarsening=1)[1][:2]
+    assert nc[0] == nf[0] and nc[1] < nf[1]
+    prob = _prob(nf, np.full(nf[0] * nf[1], Kv), h=h)
+    Tx, Ty, _ = O.face_trans(2, nf, h, prob.K, prob.bc)
+    Txc, Tyc, _ = O.upscale(2, nf, nc, Tx, Ty)
+    Hx, Hy = Lx / nc[0], Ly / nc[1]
+    ex = np.full((nc[1], nc[0] + 1), Hy / Hx * Kv)
+    ex[:, 0] *= 2
+    ex[:, -1] *= 2
+    np.testing.assert_allclose(Txc.reshape(nc[1], nc[0] + 1), ex, rtol=1e-12)
+    ey = np.full((nc[1] + 1, nc[0]), Hx / Hy * Kv)
+    ey[0] = ey[-1] = 0.0
+    np.testing.assert_allclose(Tyc.reshape(nc[1] + 1, nc[0]), ey, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("nf,nc", [(40, 10), (37, 9), (13, 7), (10, 3), (5, 5)])
+def test_piecewise_constant_table_is_containing_cell(nf, nc):
+    """Piecewise constant extension: a fine cell takes the coarse cell whose
+    interval [I/nc, (I+1)/nc) holds its centre (never on an edge: the centre
+    sits at an odd multiple of 1/(2 nf))."""
+    i0, i1, w = O.transfer_table(nf, nc, interp=1)
+    ref = np.floor((np.arange(nf) + 0.5) / nf * nc).astype(np.int32)
+    assert (i0 == ref).all() and (i1 == ref).all() and (w == 0.0).all()
+
+
+@pytest.mark.parametrize("nf", [(16, 12), (37, 11), (6, 5, 4)])
+def test_piecewise_constant_E_and_R(nf):
+    """In the hierarchy: every row of E holds a single 1, R = E^T exactly,
+    and R applied to ones counts the fine cells of each coarse cell."""
+    N = int(np.prod(nf))
+    H = O.Hierarchy(_prob(nf, np.ones(N)), interp=1)
+    nc = H.dims[1][:len(nf)]
+    Nc = int(np.prod(nc))
+    Eo = np.stack([H.prolong_add(0, np.eye(Nc)[I], np.zeros(N)) for I in range(Nc)], axis=1)
+    assert ((Eo == 0.0) | (Eo == 1.0)).all() and (Eo.sum(axis=1) == 1.0).all()
+    Ro = np.stack([H.restrict(0, np.eye(N)[i]) for i in range(N)], axis=1)
+    np.testing.assert_array_equal(Ro, Eo.T)
+    cells = [np.floor((np.arange(a) + 0.5) / a * b).astype(int) for a, b in zip(nf, nc)]
+    counts = np.ones(1)
+    for c, b in zip(cells, nc):
+        counts = np.kron(np.bincount(c, minlength=b), counts)
+    np.testing.assert_array_equal(H.restrict(0, np.ones(N)), counts)
+
+
+@pytest.mark.parametrize("coarsening,interp", [(1, 0), (0, 1), (1, 1)])
+def test_anisotropic_options_solve_matches_direct_solve(coarsening, interp):
+    """10:1 cells with random K, each option combination: the solve agrees
+    with a sparse direct solve."""
+    rng = np.random.default_rng(31)
+    n = (60, 15)
+    h = (10.0 / n[0], 0.25 / n[1])
+    N = n[0] * n[1]
+    prob = _prob(n, 10.0 ** rng.uniform(-2, 2, N), h=h)
+    H = O.Hierarchy(prob, coarsening=coarsening, interp=interp, maxit_outer=1000)
+    b = H.lift_rhs()
+    x, st = H.solve(b, 1e-13)
+    assert st["status"] == 0
+    ex = spla.spsolve(_sparse_A(H, 0), b)
+    assert np.linalg.norm(x - ex) / np.linalg.norm(ex) < 1e-10
+
+
+def test_square_cell_coarsening_converges_faster_on_ten_to_one_cells():
+    """Sec. 4.4: with 10:1 cells the method does better when coarsening aims
+    at square cells than with the same factor on both axes."""
+    rng = np.random.default_rng(31)
+    n = (60, 15)
+    h = (10.0 / n[0], 0.25 / n[1])
+    prob = _prob(n, 10.0 ** rng.uniform(-2, 2, n[0] * n[1]), h=h)
+    its = []
+    for coarsening in (0, 1):
+        H = O.Hierarchy(prob, coarsening=coarsening, maxit_outer=1000)
+        _, st = H.solve(H.lift_rhs(), 1e-8)
+        assert st["status"] == 0
+        its.append(st["iters"][0])
+    assert its[1] * 2 < its[0], its
+
+
+# --------------------------------------------------------------------------
 # Splitting and preconditioner (eqs. 2.3-2.10, Sec. 3)
 # --------------------------------------------------------------------------
 def _rb_perm(n):
