@@ -81,7 +81,12 @@ typedef struct {
                           2 = symmetric Gauss-Seidel in the natural order of the cells (a
                           wavefront over the planes i+j+k = d; single solves then run every
                           level in one CTA) */
-  int reserved[3];
+  int coarsening;      /* level sides: 0 = every axis longer than the coarsest side shrinks by
+                          `scale`; 1 = toward square cells (the coarse cell size is `scale` times the
+                          smallest cell size of the axes still coarsened; Sec. 4.4 semi-coarsening) */
+  int interp;          /* extension E (R = E^T): 0 = tensor linear interpolation with zero slope at
+                          the boundary, 1 = piecewise constant (Sec. 3) */
+  int reserved[1];
 } msrcg_opts;
 
 /* Per-solve statistics.  iters[k] = PCG iterations summed over all calls at

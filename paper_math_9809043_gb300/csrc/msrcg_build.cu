@@ -56,8 +56,10 @@ namespace {
 // longer than the coarsest side limit shrinks to max(2, floor(n/s + 1/2));
 // the hierarchy ends when no axis is longer than the limit.
 // ---------------------------------------------------------------------------
-int level_sides(int dim, const int n[3], int s, int limit, int out[][3]) {
+int level_sides(int dim, const int n[3], const double h[3], int s, int limit, int rule, int out[][3]) {
   int cur[3] = {n[0], n[1], dim == 3 ? n[2] : 1};
+  double La[3] = {0.0, 0.0, 0.0};  // axis lengths, fixed over the levels
+  for (int a = 0; a < dim; ++a) La[a] = (double)n[a] * h[a];
   int nl = 0;
   for (;;) {
     if (nl >= kMaxLev) return -1;
@@ -66,8 +68,29 @@ int level_sides(int dim, const int n[3], int s, int limit, int out[][3]) {
     bool longer = false;
     for (int a = 0; a < dim; ++a) longer = longer || cur[a] > limit;
     if (!longer) return nl;
+    // rule 1: coarse cells of size s * (smallest cell size of the axes still
+    // coarsened), each axis rounded and never refined
+    double hmin = 0.0;
+    bool first = true;
+    for (int a = 0; a < dim; ++a) {
+      const double ha = La[a] / (double)cur[a];
+      if (cur[a] > limit && (first || ha < hmin)) {
+        hmin = ha;
+        first = false;
+      }
+    }
     for (int a = 0; a < dim; ++a)
-      if (cur[a] > limit) cur[a] = std::max(2, (2 * cur[a] + s) / (2 * s));
+      if (cur[a] > limit) {
+        int c;
+        if (rule == 0) {
+          c = (2 * cur[a] + s) / (2 * s);
+        } else {
+          const double t = La[a] / ((double)s * hmin);
+          c = (int)floor(t + 0.5);
+          if (c > cur[a]) c = cur[a];
+        }
+        cur[a] = std::max(2, c);
+      }
   }
 }
 
@@ -81,7 +104,9 @@ struct Axis1D {
   int W = 1;
 };
 
-Axis1D axis_tables(int nf, int nc) {
+// interp 1: piecewise constant (Sec. 3) -- the coarse cell holding the fine
+// centre, floor((2i+1) nc / (2 nf)), weight 1.
+Axis1D axis_tables(int nf, int nc, int interp) {
   Axis1D A;
   A.c0.resize(nf);
   A.c1.resize(nf);
@@ -91,7 +116,10 @@ Axis1D axis_tables(int nf, int nc) {
     long long num = (2LL * i + 1) * nc - nf;
     int a, b;
     double w;
-    if (num <= 0) {
+    if (interp == 1) {
+      a = b = (int)(((2LL * i + 1) * nc) / den);
+      w = 0.0;
+    } else if (num <= 0) {
       a = b = 0;
       w = 0.0;
     } else if (num / den >= nc - 1) {
@@ -467,6 +495,8 @@ extern "C" int msrcg_default_opts(msrcg_opts* o) {
   o->fuse_width = 0;
   o->fuse_min_cells = 0;
   o->splitting = 0;
+  o->coarsening = 0;
+  o->interp = 0;
   return MSRCG_OK;
 }
 
@@ -503,7 +533,8 @@ int msrcg_build_ex(const msrcg_grid* grid, const double* K, int ncomp, const uin
   if (opts) o = *opts;
   else msrcg_default_opts(&o);
   if (o.scale < 2 || o.m < 1 || !(o.f > 0.0) || o.maxit_outer < 1 || o.maxit_inner < 1 || o.fuse_width < 0 ||
-      o.fuse_min_cells < 0 || o.splitting < 0 || o.splitting > 2)
+      o.fuse_min_cells < 0 || o.splitting < 0 || o.splitting > 2 || o.coarsening < 0 || o.coarsening > 1 ||
+      o.interp < 0 || o.interp > 1)
     return MSRCG_EINVAL;
   if (o.precision != 0 && o.precision != 1) return MSRCG_EINVAL;
   if (o.coarsest_max_side <= 0) o.coarsest_max_side = dim == 2 ? 8 : 4;
@@ -524,7 +555,10 @@ int msrcg_build_ex(const msrcg_grid* grid, const double* K, int ncomp, const uin
   if (cudaGetDevice(&h->device) != cudaSuccess) return fail(MSRCG_ECUDA);
   cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
   int n3[3] = {grid->n[0], grid->n[1], dim == 3 ? grid->n[2] : 1};
-  h->nlev = level_sides(dim, n3, o.scale, o.coarsest_max_side, h->dims);
+  {
+    const double h3[3] = {grid->h[0], grid->h[1], dim == 3 ? grid->h[2] : 1.0};
+    h->nlev = level_sides(dim, n3, h3, o.scale, o.coarsest_max_side, o.coarsening, h->dims);
+  }
   if (h->nlev < 1) return fail(MSRCG_EINVAL);
   for (int k = 0; k < h->nlev; ++k) h->N[k] = (long long)h->dims[k][0] * h->dims[k][1] * h->dims[k][2];
   if ((long long)(n3[0] + 2) * (n3[1] + 2) * (n3[2] + 2) >= (1LL << 31)) return fail(MSRCG_EINVAL);
@@ -608,7 +642,7 @@ int msrcg_build_ex(const msrcg_grid* grid, const double* K, int ncomp, const uin
     L.maxit = k == 0 ? o.maxit_outer : o.maxit_inner;
     if (k + 1 < h->nlev) {
       for (int a = 0; a < 3; ++a) {
-        Axis1D ax = axis_tables(h->dims[k][a], h->dims[k + 1][a]);
+        Axis1D ax = axis_tables(h->dims[k][a], h->dims[k + 1][a], o.interp);
         const void* p;
         if ((rc = upload(h, ax.c0, &p, st))) return fail(rc);
         L.c0[a] = (const int*)p;
@@ -758,11 +792,15 @@ namespace {
 // 1-D transfer tables of one axis (nf fine -> nc coarse cells) on the device:
 // prolongation corners/weights per fine cell and, per coarse cell, the window
 // of fine cells interpolating from it with their weights (row stride W).
-__global__ void k_axis_tables(int nf, int nc, int W, int* c0, int* c1, void* w, int* lo, int* hi, void* rw, int f32) {
+__global__ void k_axis_tables(int nf, int nc, int W, int* c0, int* c1, void* w, int* lo, int* hi, void* rw, int f32,
+                              int interp) {
   const long long den = 2LL * nf;
   auto corners = [&](int i, int* a, int* b, double* wt) {
     const long long num = (2LL * i + 1) * nc - nf;
-    if (num <= 0) {
+    if (interp == 1) {
+      *a = *b = (int)(((2LL * i + 1) * nc) / den);
+      *wt = 0.0;
+    } else if (num <= 0) {
       *a = *b = 0;
       *wt = 0.0;
     } else if (num / den >= nc - 1) {
@@ -849,7 +887,8 @@ int msrcg_build_into(msrcg_hier* h, const msrcg_grid* grid, const double* K, int
   if (opts) o = *opts;
   else msrcg_default_opts(&o);
   if (o.scale < 2 || o.m < 1 || !(o.f > 0.0) || o.maxit_outer < 1 || o.maxit_inner < 1 || o.fuse_width < 0 ||
-      o.fuse_min_cells < 0 || o.splitting < 0 || o.splitting > 2)
+      o.fuse_min_cells < 0 || o.splitting < 0 || o.splitting > 2 || o.coarsening < 0 || o.coarsening > 1 ||
+      o.interp < 0 || o.interp > 1)
     return MSRCG_EINVAL;
   if (o.precision != 0 && o.precision != 1) return MSRCG_EINVAL;
   if (o.coarsest_max_side <= 0) o.coarsest_max_side = dim == 2 ? 8 : 4;
@@ -860,7 +899,10 @@ int msrcg_build_into(msrcg_hier* h, const msrcg_grid* grid, const double* K, int
   cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
   int n3[3] = {grid->n[0], grid->n[1], dim == 3 ? grid->n[2] : 1};
   if ((long long)(n3[0] + 2) * (n3[1] + 2) * (n3[2] + 2) >= (1LL << 31)) return MSRCG_EINVAL;
-  h->nlev = level_sides(dim, n3, o.scale, o.coarsest_max_side, h->dims);
+  {
+    const double h3[3] = {grid->h[0], grid->h[1], dim == 3 ? grid->h[2] : 1.0};
+    h->nlev = level_sides(dim, n3, h3, o.scale, o.coarsest_max_side, o.coarsening, h->dims);
+  }
   if (h->nlev < 1) return MSRCG_EINVAL;
   for (int k = 0; k < h->nlev; ++k) h->N[k] = (long long)h->dims[k][0] * h->dims[k][1] * h->dims[k][2];
   if (h->N[h->nlev - 1] > 1024) return MSRCG_EINVAL;
@@ -941,7 +983,8 @@ int msrcg_build_into(msrcg_hier* h, const msrcg_grid* grid, const double* K, int
         int* hi = (int*)cv.take(sizeof(int) * nc);
         void* rw = cv.take(rsz * (size_t)nc * W);
         if (!cv.ok) return MSRCG_EINVAL;
-        k_axis_tables<<<grid_for(std::max(nf, nc), 128, gmax), 128, 0, st>>>(nf, nc, W, c0, c1, w, lo, hi, rw, f32);
+        k_axis_tables<<<grid_for(std::max(nf, nc), 128, gmax), 128, 0, st>>>(nf, nc, W, c0, c1, w, lo, hi, rw, f32,
+                                                                             o.interp);
         L.c0[a] = c0;
         L.c1[a] = c1;
         L.w[a] = w;

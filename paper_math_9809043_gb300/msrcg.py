@@ -32,7 +32,8 @@ class Opts(C.Structure):
                 ("precision", C.c_int), ("maxit_outer", C.c_int), ("maxit_inner", C.c_int),
                 ("timeout_ns", C.c_uint64), ("inner_floor", C.c_double), ("small_cells", C.c_int),
                 ("plain_sweeps", C.c_int), ("fuse_width", C.c_int), ("fuse_min_cells", C.c_int),
-                ("splitting", C.c_int), ("reserved", C.c_int * 3)]
+                ("splitting", C.c_int), ("coarsening", C.c_int), ("interp", C.c_int),
+                ("reserved", C.c_int * 1)]
 
 
 class Stats(C.Structure):

@@ -149,6 +149,24 @@ def grf3d_problem(side: int = 128, seed: int = 1002) -> Problem:
     return grf_problem((side, side, side), seed=seed, ell=8.0, half_span=4.5)
 
 
+def strip_problem(n=(2000, 500), aspect: float = 10.0, seed: int = 1005, ell: float = 16.0,
+                  half_span: float = 3.3, Ly: float = 0.25) -> Problem:
+    """Anisotropic cells (Sec. 4.4): a log-normal field drawn on the n_x x n_y
+    cell grid (correlation length `ell` cells, log10 K in [-half_span,
+    half_span]) and read with cells `aspect` times longer in x than in y; at
+    2000 x 500 and 10:1 the domain is 10 x 0.25, a channel 40 times longer
+    than wide, as in the paper's narrow-channel test.  N(0,1) source, lifted
+    standard boundary types."""
+    rng = np.random.default_rng(seed)
+    nx, ny = n
+    logk = rescale(gaussian_random_field((ny, nx), ell, rng), -half_span, half_span)
+    hy = Ly / ny
+    bc, gD = standard_bc(2, n)
+    return Problem(dim=2, n=(nx, ny), h=(aspect * hy, hy), K=(10.0 ** logk).reshape(1, -1), bc=bc, gD=gD,
+                   f=rng.standard_normal(nx * ny), pbf=linear_lifting(2, n), name=f"strip-{nx}x{ny}-{aspect:g}to1",
+                   meta={"seed": seed, "ell": ell, "log10K": [-half_span, half_span], "aspect": aspect})
+
+
 def channel_problem(n=(128, 128, 128), seed=1002, slab=4, k_lo=1e-9, k_hi=1.0,
                     max_channels=4, wmin=2, wmax=8) -> Problem:
     """Layered 3D channel field.

@@ -78,6 +78,22 @@ def test_transmissibility_bit_exact_full_size(M):
             assert np.array_equal(got[a].cpu().numpy(), ref[a]), (k, a)
 
 
+@pytest.mark.parametrize("n", [(200, 50), (2000, 500)])
+def test_transmissibility_bit_exact_square_cell_coarsening(M, n):
+    """10:1 cells coarsened toward square cells (an axis kept at ratio 1 on
+    the first level): same level sides as the oracle, every level's T
+    bit-exact."""
+    prob = P.strip_problem(n)
+    H = M.Hierarchy.from_problem(prob, M.default_opts(coarsening=1))
+    R = O.Hierarchy(prob, coarsening=1)
+    assert [H.dims(k)[0] for k in range(H.nlev)] == R.dims
+    for k in range(R.nlev):
+        got = H.trans(k)
+        ref = R.T(k)
+        for a in range(2):
+            assert np.array_equal(got[a].cpu().numpy(), ref[a]), (k, a)
+
+
 @pytest.mark.parametrize("n", [(32, 32), (37, 23), (9, 8, 7)])
 def test_apply_and_lift(M, n):
     prob = _prob_uniform(n, span=4.5)
@@ -249,6 +265,40 @@ def test_splitting_option_validated(M):
     prob = _prob_uniform((8, 8))
     with pytest.raises(M.MsrcgError):
         M.Hierarchy.from_problem(prob, M.default_opts(splitting=3))
+
+
+# ---------------------------------------------------------------------------
+# anisotropic cells: coarsening toward square cells, piecewise constant E
+# ---------------------------------------------------------------------------
+ANISO_CASES = [
+    ("square-linear", 1, 0, 0),
+    ("square-linear-wide", 1, 0, 256),
+    ("square-piecewise-constant", 1, 1, 0),
+    ("square-piecewise-constant-wide", 1, 1, 256),
+]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("name,coarsening,interp,small", ANISO_CASES, ids=[c[0] for c in ANISO_CASES])
+def test_anisotropic_strip_matches_oracle(M, name, coarsening, interp, small, prec):
+    """The 200 x 50 strip with 10:1 cells: single (graph) and batched solves
+    against the oracle with the same level rule and extension."""
+    prob = P.strip_problem((200, 50))
+    opts = M.default_opts(precision=prec, coarsening=coarsening, interp=interp, small_cells=small,
+                          inner_floor=1e-6 if prec else 0.0)
+    H = M.Hierarchy.from_problem(prob, opts)
+    b = H.rhs_for(prob)
+    x, st = H.solve(b, 1e-8)
+    xs, sts = M.batch_solve([H], [b], 1e-8)
+    R = O.Hierarchy(prob, coarsening=coarsening, interp=interp)
+    xr, sr = R.solve(R.lift_rhs(), 1e-8)
+    assert sr["status"] == 0, sr
+    for xg, sg in ((x, st), (xs[0], sts[0])):
+        assert sg["status"] == 0 and sg["relres_true"] < 1e-8, sg
+        err = np.linalg.norm(xg.cpu().numpy() - xr) / np.linalg.norm(xr)
+        assert err <= SOL_RTOL, err
+        if prec == 0:
+            _counts_close(sg["iters"], sr["iters"], sr["calls"])
 
 
 _ORACLE_CACHE = {}
