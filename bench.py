@@ -324,6 +324,46 @@ def run_splitting(args, M, P, dev, stream, nb, size, splitting, label):
     return out
 
 
+def run_strip(args, M, P, dev, stream, nb):
+    """Anisotropic cells (the paper's narrow-channel test): a 2000 x 500
+    log-normal field read with 10:1 cells, coarsened toward square cells;
+    linear and piecewise constant extension, FP32 preconditioner: single-solve
+    latency, nb concurrent solves, iterations per level."""
+    import numpy as np
+    import torch
+    base = P.strip_problem((2000, 500))
+    out = {"workload": "2000 x 500 cells of aspect 10:1 (domain 10 x 0.25), log10 K GRF in [-3.3, 3.3]; "
+                       "coarsening toward square cells", "concurrent_solves": nb}
+    for interp, key in ((0, "linear"), (1, "piecewise_constant")):
+        opts = M.default_opts(precision=1, inner_floor=1e-6, coarsening=1, interp=interp)
+        hs, bs = [], []
+        for j in range(nb):
+            rng = np.random.default_rng(1005 * 1000 + j)
+            prob = P.Problem(dim=2, n=base.n, h=base.h, K=base.K, bc=base.bc, gD=base.gD,
+                             f=rng.standard_normal(base.N), pbf=base.pbf)
+            h = M.Hierarchy.from_problem(prob, opts, device=dev)
+            hs.append(h)
+            bs.append(h.rhs_for(prob))
+        per, sts = _timed_batch(M, hs, bs, 1, stream, dev)
+        ms = statistics.mean(per)
+        lat = []
+        _, st1 = hs[0].solve(bs[0], TOL, stream=stream)
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            hs[0].solve(bs[0], TOL, stats=False, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            lat.append(e0.elapsed_time(e1))
+        out[key] = {"levels": [list(hs[0].dims(k)[0][:2]) for k in range(hs[0].nlev)], "iters": st1["iters"],
+                    "single_solve_ms": min(lat), "solves_per_s": nb / (ms / 1e3), "ms_per_batch": ms,
+                    "status": sorted({s["status"] for s in sts}),
+                    "relres_true_max": max(s["relres_true"] for s in sts)}
+        del hs, bs
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_3d(args, M, P, dev, stream, nb):
     """128^3 7-point problems on a 3D Gaussian random field (1e9 contrast):
     nb problems per launch with their own sources, and single-solve latency."""
@@ -518,13 +558,14 @@ def main():
         torch.cuda.empty_cache()
 
     # ---- other workloads: uneven batch and 3D (rank 0 only) ----
-    uneven = grid3d = jacobi = natural = None
+    uneven = grid3d = jacobi = natural = strip = None
     if rank == 0 and not args.no_extra:
         uneven = run_uneven(args, M, P, dev, stream)
         grid3d = run_3d(args, M, P, dev, stream, nb)
         jacobi = run_splitting(args, M, P, dev, stream, nb, args.size, 1, "modified Jacobi P = 2D")
         natural = run_splitting(args, M, P, dev, stream, nb, args.size, 2,
                                 "symmetric Gauss-Seidel in the natural order (plane wavefront)")
+        strip = run_strip(args, M, P, dev, stream, nb)
 
     # ---- serving: Poisson arrivals of mixed requests (rank 0 only) ----
     serving = None
@@ -558,7 +599,7 @@ def main():
                            "tile_shapes": TU.key_of(tuned) + (" (autotuner record)" if tuned_rec is not None else "")},
                 "status": statuses, "relres_true_max": relres, "iters": sts[0]["iters"],
                 "latency_ms": latency, "fp64_plain": fp64, "uneven_batch": uneven, "grid3d": grid3d, "jacobi": jacobi,
-                "natural_order_sgs": natural,
+                "natural_order_sgs": natural, "anisotropic_strip": strip,
                 "serving": serving, "e2e": e2e, "roofline": roofline,
                 "cpu_baseline": cpu, "clocks": ck, "gpu_launches": args.steps}
         print(json.dumps(line), flush=True)

@@ -79,11 +79,13 @@ static int64_t idx3(int i, int j, int k, int nx, int ny) {
  * Level sides.  Sec. 3 (scale factor about 4, adjusted to integer sizes).
  * rule 0: every axis longer than maxside shrinks by the factor s.
  * rule 1 (Sec. 4.4, anisotropic cells): coarsening aims at square cells --
- *   the coarse cell size is s times the smallest cell size h_min among the
- *   axes still longer than maxside, so an axis whose cells are already
- *   longer shrinks less or not at all (the "semi-coarsening" the paper
- *   describes); square cells coarsen as rule 0 up to rounding.  Axis a gets
- *   max(2, min(n_a, round(L_a / (s h_min)))), L_a = n_a h_a.
+ *   the coarse cell size is s times the smallest cell size h_min of the
+ *   level, so an axis whose cells are already longer shrinks less or not at
+ *   all (the "semi-coarsening" the paper describes); square cells coarsen as
+ *   rule 0 up to rounding.  Axis a (if longer than maxside) gets
+ *   max(2, min(n_a, round(L_a / (s h_min)))), L_a = n_a h_a; when no axis
+ *   changes, the level is the coarsest (the paper's narrow channel also ends
+ *   on a level of several hundred cells).
  * ------------------------------------------------------------------------- */
 int or_hierarchy_dims2(int dim, const int n[3], const double h[3], int s, int maxside, int rule, int maxlev,
                        int *dims_out) {
@@ -102,15 +104,12 @@ int or_hierarchy_dims2(int dim, const int n[3], const double h[3], int s, int ma
     for (int a = 0; a < dim; ++a)
       if (cur[a] > maxside) any = 1;
     if (!any) break;
-    double hmin = 0.0; /* smallest cell size among the axes still coarsened */
-    int first = 1;
+    double hmin = 0.0; /* smallest cell size over all axes */
     for (int a = 0; a < dim; ++a) {
       double ha = La[a] / (double)cur[a];
-      if (cur[a] > maxside && (first || ha < hmin)) {
-        hmin = ha;
-        first = 0;
-      }
+      if (a == 0 || ha < hmin) hmin = ha;
     }
+    int next[3] = {cur[0], cur[1], cur[2]}, moved = 0;
     for (int a = 0; a < dim; ++a) {
       if (cur[a] > maxside) {
         int c;
@@ -121,9 +120,14 @@ int or_hierarchy_dims2(int dim, const int n[3], const double h[3], int s, int ma
           c = (int)floor(t + 0.5);
           if (c > cur[a]) c = cur[a];
         }
-        cur[a] = c < 2 ? 2 : c;
+        next[a] = c < 2 ? 2 : c;
+        if (next[a] != cur[a]) moved = 1;
       }
     }
+    /* rule 1: no axis can coarsen without cells longer than s h_min -- this
+     * level is the coarsest */
+    if (rule == 1 && !moved) break;
+    for (int a = 0; a < dim; ++a) cur[a] = next[a];
   }
   return nlev;
 }

@@ -68,17 +68,16 @@ int level_sides(int dim, const int n[3], const double h[3], int s, int limit, in
     bool longer = false;
     for (int a = 0; a < dim; ++a) longer = longer || cur[a] > limit;
     if (!longer) return nl;
-    // rule 1: coarse cells of size s * (smallest cell size of the axes still
-    // coarsened), each axis rounded and never refined
+    // rule 1: coarse cells of size s * (smallest cell size of the level),
+    // each axis rounded and never refined; when no axis changes, this level
+    // is the coarsest
     double hmin = 0.0;
-    bool first = true;
     for (int a = 0; a < dim; ++a) {
       const double ha = La[a] / (double)cur[a];
-      if (cur[a] > limit && (first || ha < hmin)) {
-        hmin = ha;
-        first = false;
-      }
+      if (a == 0 || ha < hmin) hmin = ha;
     }
+    int next[3] = {cur[0], cur[1], cur[2]};
+    bool moved = false;
     for (int a = 0; a < dim; ++a)
       if (cur[a] > limit) {
         int c;
@@ -89,8 +88,11 @@ int level_sides(int dim, const int n[3], const double h[3], int s, int limit, in
           c = (int)floor(t + 0.5);
           if (c > cur[a]) c = cur[a];
         }
-        cur[a] = std::max(2, c);
+        next[a] = std::max(2, c);
+        moved = moved || next[a] != cur[a];
       }
+    if (rule == 1 && !moved) return nl;
+    for (int a = 0; a < 3; ++a) cur[a] = next[a];
   }
 }
 

@@ -348,8 +348,10 @@ def test_square_cell_coarsening_keeps_square_grids(n):
 def test_square_cell_coarsening_on_ten_to_one_cells():
     """Table 2's grid, 2000 x 500 cells of aspect 10:1: the first level
     coarsens y alone (the paper's semi-coarsening), later levels where both
-    axes coarsen have cells within a factor 2 of square, every level is
-    smaller than the one above."""
+    axes coarsen have cells within a factor 2 of square, no level has cells
+    more than s = 4 (plus rounding) times longer than wide after the first,
+    every level is smaller than the one above, and the hierarchy ends on a
+    level of a few hundred cells (the paper's ends on 160 x 4 = 640)."""
     Lx, Ly = 10.0, 0.25
     dims = O.hierarchy_dims(2, (2000, 500), h=(Lx / 2000, Ly / 500), coarsening=1)
     assert dims[1][0] == 2000 and dims[1][1] < 500
@@ -359,7 +361,10 @@ def test_square_cell_coarsening_on_ten_to_one_cells():
     assert both
     for d in both:
         assert 0.5 <= (Lx / d[0]) / (Ly / d[1]) <= 2.0
-    assert max(dims[-1][:2]) <= 8
+    for d in dims[1:]:
+        r = (Lx / d[0]) / (Ly / d[1])
+        assert max(r, 1 / r) <= 4.5
+    assert 100 <= dims[-1][0] * dims[-1][1] <= 1024
 
 
 def test_constant_K_upscaling_with_an_unrefined_axis():
