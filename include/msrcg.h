@@ -82,8 +82,9 @@ typedef struct {
                           wavefront over the planes i+j+k = d; single solves then run every
                           level in one CTA) */
   int coarsening;      /* level sides: 0 = every axis longer than the coarsest side shrinks by
-                          `scale`; 1 = toward square cells (the coarse cell size is `scale` times the
-                          smallest cell size of the axes still coarsened; Sec. 4.4 semi-coarsening) */
+                          `scale`; 1 = toward square cells (Sec. 4.4 semi-coarsening): the coarse
+                          cell size is `scale` times the level's smallest cell size, an axis is
+                          never refined, and the level where no axis changes is the coarsest */
   int interp;          /* extension E (R = E^T): 0 = tensor linear interpolation with zero slope at
                           the boundary, 1 = piecewise constant (Sec. 3) */
   int reserved[1];

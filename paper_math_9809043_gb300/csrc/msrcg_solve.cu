@@ -12,6 +12,12 @@
 //
 // Vectors use the padded layout of DevLevel (a zero ghost ring), so stencils
 // have no boundary branches, and threads map onto (column, row) directly.
+//
+// Smoothers (the splitting of Sec. 3): symmetric Gauss-Seidel in red-black
+// order (default; in the single-CTA solver a level that stays in global
+// memory runs all half-sweeps of a smoothing as one pipelined pass,
+// fused_smooth), modified Jacobi (P = 2D) and symmetric Gauss-Seidel in the
+// natural order of the cells (a plane wavefront, single CTA only).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
