@@ -55,6 +55,29 @@ def test_static_matches_allocating_solve_twice(M, n, prec):
         H.close()
 
 
+@pytest.mark.parametrize("extra", [{"splitting": 1}, {"splitting": 2}, {"coarsening": 1, "interp": 1}],
+                         ids=["jacobi", "natural-order", "square-cells-piecewise-constant"])
+def test_static_matches_allocating_solve_with_options(M, extra):
+    """The other smoothers, the square-cell level rule and the piecewise
+    constant extension (built on the device in the static path) give the
+    allocating solve's result; 10:1 cells for the level rule."""
+    n = (90, 24)
+    prob = _problem(n, 21)
+    if "coarsening" in extra:
+        prob = P.Problem(dim=2, n=n, h=(10.0 / n[0], 0.25 / n[1]), K=prob.K, bc=prob.bc, gD=prob.gD, b=prob.b)
+    opts = M.default_opts(precision=1, inner_floor=1e-6, **extra)
+    H = M.Hierarchy.from_problem(prob, opts)
+    b = torch.as_tensor(prob.b, device="cuda")
+    xa, sa = H.solve(b, 1e-8)
+    xs, ss = M.solve_static(prob.dim, prob.n, prob.h, prob.K, prob.bc, b, 1e-8, opts=opts)
+    torch.cuda.synchronize()
+    assert ss["status"] == 0 and ss["relres_true"] < 1e-8, ss
+    assert ss["levels"] == sa["levels"] and ss["dims"] == sa["dims"]
+    err = (torch.linalg.norm(xs - xa) / torch.linalg.norm(xa)).item()
+    assert err <= SOL_RTOL, err
+    H.close()
+
+
 def test_static_rejects_oversize(M):
     prob = _problem((400, 400), 3)
     b = torch.as_tensor(prob.b, device="cuda")
