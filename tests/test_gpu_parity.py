@@ -445,6 +445,24 @@ def test_uneven_batch_full_size(M):
         assert err <= SOL_RTOL, (side, err)
 
 
+@pytest.mark.parametrize("n", [(4100, 3), (8, 4096)], ids=["long-4100x3", "tall-8x4096"])
+def test_single_pass_smoothing_on_thin_levels(M, n):
+    """Single-pass smoothing on levels with fewer rows than the pipeline is
+    deep (4100 x 3) and with a single strip narrower than its halo
+    (8 x 4096), batched path, against the oracle and the plain sweeps."""
+    prob = _prob_uniform(n, seed=41)
+    R = O.Hierarchy(prob)
+    xr, sr = R.solve(R.lift_rhs(), 1e-8)
+    assert sr["status"] == 0
+    for plain in (0, 1):
+        opts = M.default_opts(precision=1, inner_floor=1e-6, plain_sweeps=plain)
+        H = M.Hierarchy.from_problem(prob, opts)
+        xs, sts = M.batch_solve([H], [H.rhs_for(prob)], 1e-8)
+        assert sts[0]["status"] == 0 and sts[0]["relres_true"] < 1e-8, sts[0]
+        err = np.linalg.norm(xs[0].cpu().numpy() - xr) / np.linalg.norm(xr)
+        assert err <= SOL_RTOL, (plain, err)
+
+
 def test_tuner_picks_a_candidate(M):
     """The autotuner times every candidate tile shape on a small batch, all of
     them solve, and it returns the fastest."""
