@@ -1810,10 +1810,8 @@ __global__ void k_prepare(DevLevel L0, const double* b, double* b0, double tol, 
                           double* partials) {
   double acc = 0.0;
   for_cells<DIM>(grid_map(), L0, [&](int i, const Row& rw) {
-      const int pc = rw.pc + i;
-      const int j = rw.j, k = rw.k;
-      (void)j;
-      (void)k;
+    const int pc = rw.pc + i;
+    const int j = rw.j, k = rw.k;
     const double v = b[i + (long long)L0.nx * (j + (long long)L0.ny * k)];
     b0[pc] = v;
     acc += v * v;
@@ -1845,10 +1843,8 @@ __global__ void k_true_residual(DevLevel L0, const double* b, double* b0, const 
   const double *Tx = L0.T64[0], *Ty = L0.T64[1], *Tz = DIM == 3 ? L0.T64[2] : nullptr;
   double acc = 0.0;
   for_cells<DIM>(grid_map(), L0, [&](int i, const Row& rw) {
-      const int pc = rw.pc + i;
-      const int j = rw.j, k = rw.k;
-      (void)j;
-      (void)k;
+    const int pc = rw.pc + i;
+    const int j = rw.j, k = rw.k;
     const double v = b[i + (long long)L0.nx * (j + (long long)L0.ny * k)] -
                      apply_value<DIM, double, double>(L0, Tx, Ty, Tz, xs, i, rw);
     b0[pc] = v;
@@ -1860,10 +1856,8 @@ __global__ void k_true_residual(DevLevel L0, const double* b, double* b0, const 
 template <int DIM>
 __global__ void k_copy_out(DevLevel L0, const double* xs, double* x) {
   for_cells<DIM>(grid_map(), L0, [&](int i, const Row& rw) {
-      const int pc = rw.pc + i;
-      const int j = rw.j, k = rw.k;
-      (void)j;
-      (void)k;
+    const int pc = rw.pc + i;
+    const int j = rw.j, k = rw.k;
     x[i + (long long)L0.nx * (j + (long long)L0.ny * k)] = xs[pc];
   });
 }
