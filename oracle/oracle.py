@@ -197,8 +197,11 @@ class Hierarchy:
         lib().or_get_T(self._h, k, Tx, Ty, Tz.ctypes.data if Tz is not None else None)
         return Tx, Ty, Tz
 
-    def lift_rhs(self):
-        p = self.prob
+    def lift_rhs(self, prob=None):
+        """Right-hand side of the lifted system (Sec. 4.1) for this hierarchy's
+        problem, or for `prob`: another problem on the same grid, permeability
+        and boundary data that differs only in its source term or lifting."""
+        p = self.prob if prob is None else prob
         if not p.lifted:
             return np.ascontiguousarray(p.b, np.float64).copy()
         b = np.zeros(p.N)

@@ -356,6 +356,43 @@ def test_batched_1024_single_pass_and_plain_sweeps(M, extra):
     assert err <= SOL_RTOL, err
 
 
+@pytest.mark.parametrize("prec", [1, 0])
+def test_bench_batch_full_launch(M, prec):
+    """The launch the benchmark times: one problem per SM, each the 1024^2
+    field with its own seeded N(0,1) source (the benchmark's seeds and, in the
+    FP32 mode, its tuned tile shapes), in one batched launch.  Every solution's
+    true residual, formed with the oracle's operator and right-hand side, meets
+    1e-8 (to the rounding of that check); the first and last problems match the
+    oracle's solutions; a problem solved alone gives the same bits as inside
+    the full batch (the CTAs do not interact)."""
+    from paper_math_9809043_gb300 import tune as TU
+    nb = torch.cuda.get_device_properties(0).multi_processor_count
+    base = P.config_problem(1)
+    probs = [P.Problem(dim=2, n=base.n, h=base.h, K=base.K, bc=base.bc, gD=base.gD,
+                       f=np.random.default_rng(1001 * 1000 + j).standard_normal(base.N), pbf=base.pbf)
+             for j in range(nb)]
+    tuned = (TU.best(torch.cuda.get_device_name(), f"grf1024x{nb}") or {}) if prec else {}
+    opts = M.default_opts(precision=prec, inner_floor=1e-6 if prec else 0.0, **tuned)
+    hs = [M.Hierarchy.from_problem(p, opts) for p in probs]
+    bs = [h.rhs_for(p) for h, p in zip(hs, probs)]
+    xs, sts = M.batch_solve(hs, bs, 1e-8)
+    R = O.Hierarchy(base)
+    for j, (p, x, st) in enumerate(zip(probs, xs, sts)):
+        assert st["status"] == 0 and st["relres_true"] < 1e-8, (j, st)
+        b = R.lift_rhs(p)
+        rel = np.linalg.norm(b - R.apply(0, x.cpu().numpy())) / np.linalg.norm(b)
+        assert rel < 1.05e-8, (j, rel)
+    for j in (0, nb - 1):
+        Rj = O.Hierarchy(probs[j])
+        xr, sr = Rj.solve(Rj.lift_rhs(), 1e-8)
+        err = np.linalg.norm(xs[j].cpu().numpy() - xr) / np.linalg.norm(xr)
+        assert err <= SOL_RTOL, (j, err)
+        if prec == 0:
+            _counts_close(sts[j]["iters"], sr["iters"], sr["calls"])
+        x1, s1 = M.batch_solve([hs[j]], [bs[j]], 1e-8)
+        assert torch.equal(x1[0], xs[j]) and s1[0]["iters"] == sts[j]["iters"], j
+
+
 def test_repeat_solves_identical(M):
     """Deterministic reductions: two solves give the same bits."""
     prob = P.config_problem(1, scale=256)
