@@ -564,6 +564,11 @@ def main():
                 "peak_source": peak_src, "traffic": traffic,
                 "algorithmic_bytes_per_launch": alg_bytes,
                 "launch_ms": launch_s * 1e3}
+    if traffic is not None and tr.get("counters"):
+        # per-SM issue counters of the same ncu capture (batch of 8): the kernel's
+        # real limit is instruction issue inside each SM, not HBM
+        roofline["sm_issue"] = dict(tr["counters"], peak_inst_per_cycle=4,
+                                    source="profiles/k_small_traffic_batch8.md")
 
     # ---- latency of single solves (graph path) ----
     lat = []
