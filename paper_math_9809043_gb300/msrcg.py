@@ -2,7 +2,8 @@
 
 Argument marshalling only: every step of the solver runs in the library's
 CUDA kernels.  PyTorch provides device memory and streams.  There is no CPU
-fallback: importing this module fails if the library is missing.
+fallback: the first call into the library raises ImportError if libmsrcg.so
+is missing.
 
 Reference: Lackner & Menikoff, "Multi-scale linear solvers for very large
 systems derived from PDEs" (arXiv math/9809043), Sec. 2.3 (recursive
@@ -120,17 +121,73 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
 
 
-def _dev(a, dtype, device):
+def _dev(a, dtype, device, n=None, what="array"):
+    """`a` as a contiguous device tensor of `dtype` (a copy only when needed);
+    with `n`, its size is checked first: the library reads and writes
+    exactly the sizes it documents through raw pointers."""
     if isinstance(a, torch.Tensor):
-        return a.to(device=device, dtype=dtype).contiguous()
-    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device=device)
+        t = a.to(device=device, dtype=dtype).contiguous()
+    else:
+        t = torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device=device)
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{what}: {t.numel()} elements, expected {n}")
+    return t
+
+
+def _out(t, dtype, device, n, what):
+    """A caller-supplied output tensor: written in place, so it must already
+    be contiguous, of `dtype`, on `device` and of `n` elements."""
+    if not (isinstance(t, torch.Tensor) and t.dtype == dtype and t.device == device and t.is_contiguous()
+            and t.numel() == n):
+        raise ValueError(f"{what}: expected a contiguous {dtype} tensor of {n} elements on {device}")
+    return t
+
+
+def _device(device) -> torch.device:
+    """`device` with its index (tensors report theirs: cuda:0, not cuda)."""
+    d = torch.device(device)
+    if d.type == "cuda" and d.index is None:
+        d = torch.device("cuda", torch.cuda.current_device())
+    return d
+
+
+def n_boundary_faces(dim, n) -> int:
+    """Entries of the boundary layout (bc, gD): x-low and x-high faces (ny nz
+    each), y-low and y-high (nx nz each), z-low and z-high (nx ny each, 3D)."""
+    nx, ny = int(n[0]), int(n[1])
+    nz = int(n[2]) if dim == 3 else 1
+    return 2 * (ny * nz + nx * nz) + (2 * nx * ny if dim == 3 else 0)
+
+
+def _valid_grid(dim, n) -> bool:
+    """Grids the library accepts; the binding checks array sizes only for
+    those and leaves every other grid to the library's own MSRCG_EINVAL."""
+    return dim in (2, 3) and len(n) >= dim and all(int(v) >= 1 for v in n[:dim])
+
+
+def _check_K(Kt, dim, N):
+    ncomp = Kt.numel() // max(N, 1)
+    if ncomp not in (1, dim) or Kt.numel() != ncomp * N:
+        raise ValueError(f"K: {Kt.numel()} elements, expected N = {N} (scalar) or dim * N = {dim * N} (diagonal)")
+    return ncomp
+
+
+def _hold(stream, *ts):
+    """Tensors that work enqueued on `stream` reads or writes: when that is
+    not the current stream, record it with the caching allocator so that
+    their memory is not handed out again before that work has run."""
+    if stream is None or stream == torch.cuda.current_stream(stream.device):
+        return
+    for t in ts:
+        if t is not None:
+            t.record_stream(stream)
 
 
 class Hierarchy:
     """Level hierarchy of one problem, resident on the GPU (msrcg_build)."""
 
     def __init__(self, dim, n, h, K, bc, opts: Opts | None = None, device="cuda", stream=None):
-        self.device = torch.device(device)
+        self.device = _device(device)
         self.dim = dim
         self.n = tuple(int(v) for v in n)
         self.N = int(np.prod(self.n))
@@ -140,8 +197,12 @@ class Hierarchy:
             g.n[a] = self.n[a] if a < min(dim, len(self.n)) else 1
             g.h[a] = float(h[a]) if a < min(dim, len(h)) else 1.0
         Kt = _dev(K, torch.float64, self.device).reshape(-1)
-        ncomp = Kt.numel() // max(self.N, 1)
-        bct = _dev(bc, torch.uint8, self.device)
+        if _valid_grid(dim, self.n):
+            ncomp = _check_K(Kt, dim, self.N)
+            bct = _dev(bc, torch.uint8, self.device, self.n_boundary_faces(), "bc")
+        else:
+            ncomp = Kt.numel() // max(self.N, 1)
+            bct = _dev(bc, torch.uint8, self.device)
         self.opts = opts or default_opts()
         hp = C.c_void_p()
         with torch.cuda.device(self.device):
@@ -151,6 +212,9 @@ class Hierarchy:
             raise MsrcgError(rc, "msrcg_build")
         self._h = hp
         self.nlev = lib().msrcg_num_levels(self._h)
+
+    def n_boundary_faces(self) -> int:
+        return n_boundary_faces(self.dim, self.n)
 
     @classmethod
     def from_problem(cls, prob, opts: Opts | None = None, device="cuda", stream=None):
@@ -183,11 +247,13 @@ class Hierarchy:
         return tuple(d), int(it.value), int(ca.value)
 
     def lift_rhs(self, bc, gD, f, pbf, stream=None):
-        bct = _dev(bc, torch.uint8, self.device)
-        gDt = _dev(gD, torch.float64, self.device)
-        ft = _dev(f, torch.float64, self.device) if f is not None else None
-        pt = _dev(pbf, torch.float64, self.device)
+        nbf = self.n_boundary_faces()
+        bct = _dev(bc, torch.uint8, self.device, nbf, "bc")
+        gDt = _dev(gD, torch.float64, self.device, nbf, "gD")
+        ft = _dev(f, torch.float64, self.device, self.N, "f") if f is not None else None
+        pt = _dev(pbf, torch.float64, self.device, self.N, "pbf")
         b = torch.empty(self.N, dtype=torch.float64, device=self.device)
+        _hold(stream, bct, gDt, ft, pt, b)
         rc = lib().msrcg_lift_rhs(self._h, _ptr(bct), _ptr(gDt), _ptr(ft), _ptr(pt), _ptr(b), _stream(stream))
         if rc != OK:
             raise MsrcgError(rc, "msrcg_lift_rhs")
@@ -200,9 +266,12 @@ class Hierarchy:
         return _dev(prob.b, torch.float64, self.device)
 
     def solve(self, b, tol=1e-8, x=None, stats=True, stream=None, check=True):
-        b = _dev(b, torch.float64, self.device)
+        b = _dev(b, torch.float64, self.device, self.N, "b")
         if x is None:
             x = torch.empty(self.N, dtype=torch.float64, device=self.device)
+        else:
+            _out(x, torch.float64, self.device, self.N, "x")
+        _hold(stream, b, x)
         st = Stats()
         rc = lib().msrcg_solve(self._h, _ptr(b), float(tol), _ptr(x), C.byref(st) if stats else None,
                                _stream(stream))
@@ -216,14 +285,17 @@ class Hierarchy:
         Tx = torch.empty((nx + 1) * ny * nz, dtype=torch.float64, device=self.device)
         Ty = torch.empty(nx * (ny + 1) * nz, dtype=torch.float64, device=self.device)
         Tz = torch.empty(nx * ny * (nz + 1), dtype=torch.float64, device=self.device) if self.dim == 3 else None
+        _hold(stream, Tx, Ty, Tz)
         rc = lib().msrcg_get_trans(self._h, k, _ptr(Tx), _ptr(Ty), _ptr(Tz), _stream(stream))
         if rc != OK:
             raise MsrcgError(rc, "msrcg_get_trans")
         return Tx, Ty, Tz
 
     def apply(self, k, x, stream=None):
-        x = _dev(x, torch.float64, self.device)
+        d, _, _ = self.dims(k)
+        x = _dev(x, torch.float64, self.device, d[0] * d[1] * d[2], "x")
         y = torch.empty_like(x)
+        _hold(stream, x, y)
         rc = lib().msrcg_apply(self._h, k, _ptr(x), _ptr(y), _stream(stream))
         if rc != OK:
             raise MsrcgError(rc, "msrcg_apply")
@@ -233,8 +305,16 @@ class Hierarchy:
 def batch_solve(hs, bs, tol=1e-8, xs=None, stream=None, check=True):
     """Solve independent problems in one persistent launch (msrcg_batch_solve)."""
     n = len(hs)
+    if len(bs) != n or (xs is not None and len(xs) != n):
+        raise ValueError("batch_solve: hs, bs and xs differ in length")
+    if any(h.handle is None for h in hs):
+        raise ValueError("batch_solve: a hierarchy has been closed")
+    bs = [_dev(b, torch.float64, h.device, h.N, f"bs[{i}]") for i, (h, b) in enumerate(zip(hs, bs))]
     if xs is None:
         xs = [torch.empty(h.N, dtype=torch.float64, device=h.device) for h in hs]
+    else:
+        for i, (h, x) in enumerate(zip(hs, xs)):
+            _out(x, torch.float64, h.device, h.N, f"xs[{i}]")
     H = (C.c_void_p * n)(*[h.handle.value for h in hs])
     B = (C.c_void_p * n)(*[b.data_ptr() for b in bs])
     X = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
@@ -254,7 +334,7 @@ def solve_static(dim, n, h, K, bc, b, tol=1e-8, x=None, opts: Opts | None = None
 
     For callers that cannot allocate device memory; the library works in a
     fixed scratch of STATIC_SCRATCH_BYTES.  Overlapping calls race."""
-    device = torch.device(device)
+    device = _device(device)
     g = Grid()
     g.dim = dim
     nn = tuple(int(v) for v in n)
@@ -263,10 +343,17 @@ def solve_static(dim, n, h, K, bc, b, tol=1e-8, x=None, opts: Opts | None = None
         g.h[a] = float(h[a]) if a < min(dim, len(h)) else 1.0
     N = int(np.prod(nn))
     Kt = _dev(K, torch.float64, device).reshape(-1)
-    bct = _dev(bc, torch.uint8, device)
-    bt = _dev(b, torch.float64, device)
+    if _valid_grid(dim, nn):
+        _check_K(Kt, dim, N)
+        bct = _dev(bc, torch.uint8, device, n_boundary_faces(dim, nn), "bc")
+        bt = _dev(b, torch.float64, device, N, "b")
+    else:
+        bct = _dev(bc, torch.uint8, device)
+        bt = _dev(b, torch.float64, device)
     if x is None:
         x = torch.empty(N, dtype=torch.float64, device=device)
+    else:
+        _out(x, torch.float64, device, N, "x")
     st = Stats()
     o = opts or default_opts()
     rc = lib().msrcg_solve_static(C.byref(g), _ptr(Kt), Kt.numel() // max(N, 1), _ptr(bct), C.byref(o), _ptr(bt),

@@ -51,9 +51,16 @@ class Server:
         K = np.ascontiguousarray(prob.K, np.float64)
         bc = np.ascontiguousarray(prob.bc, np.uint8)
         bb = np.ascontiguousarray(b, np.float64)
+        ncomp = K.shape[0] if K.ndim == 2 else 1
+        # the library copies exactly these sizes from the host pointers
+        if ncomp not in (1, prob.dim) or K.size != ncomp * prob.N:
+            raise ValueError(f"K: {K.size} elements for N = {prob.N}")
+        if bc.size != M.n_boundary_faces(prob.dim, prob.n) or bb.size != prob.N:
+            raise ValueError(f"bc / b: {bc.size} / {bb.size} elements, expected "
+                             f"{M.n_boundary_faces(prob.dim, prob.n)} / {prob.N}")
         x = np.empty(prob.N, np.float64)
         rid = C.c_int64()
-        rc = M.lib().msrcg_server_submit(self._h, C.byref(g), K.ctypes.data, K.shape[0] if K.ndim == 2 else 1,
+        rc = M.lib().msrcg_server_submit(self._h, C.byref(g), K.ctypes.data, ncomp,
                                          bc.ctypes.data, bb.ctypes.data, float(tol), x.ctypes.data, C.byref(rid))
         if rc != M.OK:
             raise M.MsrcgError(rc, "msrcg_server_submit")

@@ -433,6 +433,26 @@ def test_invalid_arguments(M):
     H = M.Hierarchy.from_problem(prob)
     with pytest.raises(M.MsrcgError):
         H.solve(torch.ones(64, dtype=torch.float64, device="cuda"), tol=-1.0)
+    # mis-sized arrays are refused on the host, before any launch
+    f64 = dict(dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        H.solve(torch.ones(63, **f64))
+    with pytest.raises(ValueError):
+        H.solve(torch.ones(64, **f64), x=torch.empty(60, **f64))
+    with pytest.raises(ValueError):
+        H.solve(torch.ones(64, **f64), x=torch.empty(64, dtype=torch.float32, device="cuda"))
+    with pytest.raises(ValueError):
+        M.batch_solve([H], [torch.ones(65, **f64)])
+    with pytest.raises(ValueError):
+        M.batch_solve([H, H], [torch.ones(64, **f64)])
+    with pytest.raises(ValueError):
+        H.apply(0, torch.ones(5, **f64))
+    with pytest.raises(ValueError):
+        H.lift_rhs(prob.bc[:-1], prob.gD, prob.f, prob.pbf)
+    with pytest.raises(ValueError):
+        M.Hierarchy(2, (8, 8), (0.1, 0.1), prob.K.reshape(-1)[:60], prob.bc)
+    with pytest.raises(ValueError):
+        M.Hierarchy(2, (8, 8), (0.1, 0.1), prob.K, prob.bc[:10])
 
 
 # ---------------------------------------------------------------------------
