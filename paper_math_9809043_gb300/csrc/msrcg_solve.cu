@@ -220,6 +220,68 @@ __device__ __forceinline__ void for_colour(const Map& m, const LV& L, int colour
     }
 }
 
+// Linear passes over a level's padded vectors: a thread visits c =
+// threadIdx.x, + blockDim.x, ...  Each group of kLinUnroll consecutive
+// visits first reads its operands (ld(c)) and then applies them in visit
+// order (st(c, v)).  The arithmetic and its order are those of the plain
+// loop, so results are bit-identical; but a thread keeps kLinUnroll loads in
+// flight instead of one (the compiler cannot move a load above an earlier
+// store through pointers that may alias).  The buffers a pass reads and the
+// ones it writes must be distinct.
+constexpr int kLinUnroll = 4;
+
+template <class A, class B>
+struct Two {
+  A a;
+  B b;
+};
+template <class V>
+struct Four {
+  V x, p, r, q;
+};
+
+template <class Ld, class St>
+__device__ __forceinline__ void for_lin(int n, Ld&& ld, St&& st) {
+  using T = decltype(ld(0));
+  const int step = blockDim.x;
+  int c = threadIdx.x;
+  for (; c + (kLinUnroll - 1) * step < n; c += kLinUnroll * step) {
+    T v[kLinUnroll];
+#pragma unroll
+    for (int u = 0; u < kLinUnroll; ++u) v[u] = ld(c + u * step);
+#pragma unroll
+    for (int u = 0; u < kLinUnroll; ++u) st(c + u * step, v[u]);
+  }
+  for (; c < n; c += step) st(c, ld(c));
+}
+
+// for_cells with the same split: calc(i, row) (loads and arithmetic, no
+// stores) for kLinUnroll consecutive rows of a thread's column, then
+// commit(i, row, value) in visit order.
+template <int DIM, class LV, class Calc, class Commit>
+__device__ __forceinline__ void for_cells_u(const Map& m, const LV& L, Calc&& calc, Commit&& commit) {
+  using T = decltype(calc(0, Row{}));
+  const int rows = L.ny * L.nz;
+  for (int i = m.x0; i < L.nx; i += m.dx) {
+    int row = m.y0;
+    for (; row + (kLinUnroll - 1) * m.dy < rows; row += kLinUnroll * m.dy) {
+      Row rw[kLinUnroll];
+      T v[kLinUnroll];
+#pragma unroll
+      for (int u = 0; u < kLinUnroll; ++u) {
+        rw[u] = make_row<DIM>(L, row + u * m.dy);
+        v[u] = calc(i, rw[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < kLinUnroll; ++u) commit(i, rw[u], v[u]);
+    }
+    for (; row < rows; row += m.dy) {
+      const Row rw = make_row<DIM>(L, row);
+      commit(i, rw, calc(i, rw));
+    }
+  }
+}
+
 template <typename R>
 __device__ __forceinline__ R quot(R a, R b);
 template <>
@@ -724,9 +786,12 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
                : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-// all groups but the newest kFuseAhead are complete
+// Step s of the pipeline commits group s + kFuseAhead (row s + kFuseAhead
+// and the face row above it); group g holds row g.  Stage 0 at step s reads
+// rows up to s + 1 (post-smoothing: the z row above, loaded from global
+// memory), so all groups but the newest kFuseAhead - 1 must be complete.
 __device__ __forceinline__ void cp_async_wait_ahead() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(kFuseAhead) : "memory");
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(kFuseAhead - 1) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
@@ -1013,11 +1078,10 @@ struct Ops {
     const V* r = (const V*)L.r;
     const int npad = (int)L.npad;
     V acc = 0;
-    for (int c = threadIdx.x; c < npad; c += blockDim.x) {
-      const V rv = r[c];
+    for_lin(npad, [&](int c) { return r[c]; }, [&](int c, V rv) {
       acc += rv * rv;
       x[c] = 0;
-    }
+    });
     return tm.sum<V>(acc);
   }
   // pre-smoothing from zero, t = r - A z, r_{k+1} = R t
@@ -1031,7 +1095,7 @@ struct Ops {
           const V* r = (const V*)L.r;
           RP* rp = (RP*)L.rp;
           const int npad = (int)L.npad;
-          for (int c = threadIdx.x; c < npad; c += blockDim.x) rp[c] = (RP)r[c];
+          for_lin(npad, [&](int c) { return r[c]; }, [&](int c, V v) { rp[c] = (RP)v; });
           tm.sync();
         }
         fused_smooth<V>(L, m, true, a.win_off, wo, nullptr);
@@ -1114,28 +1178,37 @@ struct Ops {
     const RP* z = (const RP*)L.z;
     const Geo G = geo_of(L);
     const int npad = G.npad;
-    for (int c = threadIdx.x; c < npad; c += blockDim.x) p[c] = first ? (V)z[c] : (V)z[c] + beta * p[c];
+    if (first)
+      for_lin(npad, [&](int c) { return z[c]; }, [&](int c, RP zv) { p[c] = (V)zv; });
+    else
+      for_lin(npad, [&](int c) { return Two<RP, V>{z[c], p[c]}; },
+              [&](int c, Two<RP, V> v) { p[c] = (V)v.a + beta * v.b; });
     tm.sync();
     const V *Tx = Tvec<V>(L, 0), *Ty = Tvec<V>(L, 1), *Tz = DIM == 3 ? Tvec<V>(L, 2) : nullptr;
     V acc = 0;
-    for_cells<DIM>(team_map(G.nx), G, [&](int i, const Row& rw) {
-      const V v = apply_value<DIM, V, V>(G, Tx, Ty, Tz, p, i, rw);
-      acc += p[rw.pc + i] * v;
-      q[rw.pc + i] = v;
-    });
+    // a = (A p)_c, b = p_c
+    for_cells_u<DIM>(
+        team_map(G.nx), G,
+        [&](int i, const Row& rw) {
+          return Two<V, V>{apply_value<DIM, V, V>(G, Tx, Ty, Tz, p, i, rw), p[rw.pc + i]};
+        },
+        [&](int i, const Row& rw, Two<V, V> v) {
+          acc += v.b * v.a;
+          q[rw.pc + i] = v.a;
+        });
     const V pq = tm.sum<V>(acc);
     if (!(pq > (V)0) || !isfinite(pq) || !isfinite(rho)) return false;
     const V alpha = rho / pq;
     V* x = (V*)L.x;
     V* r = (V*)L.r;
     V acc2 = 0;
-    for (int c = threadIdx.x; c < npad; c += blockDim.x) {
-      const V xv = x[c] + alpha * p[c];
-      const V rv = r[c] - alpha * q[c];
+    for_lin(npad, [&](int c) { return Four<V>{x[c], p[c], r[c], q[c]}; }, [&](int c, Four<V> v) {
+      const V xv = v.x + alpha * v.p;
+      const V rv = v.r - alpha * v.q;
       acc2 += rv * rv;
       x[c] = xv;
       r[c] = rv;
-    }
+    });
     rr_out = tm.sum<V>(acc2);
     return true;
   }
