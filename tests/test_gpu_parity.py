@@ -362,10 +362,10 @@ def test_bench_batch_full_launch(M, prec):
     field with its own seeded N(0,1) source (the benchmark's seeds and, in the
     FP32 mode, its tuned tile shapes), in one batched launch.  Every solution's
     true residual, formed with the oracle's operator and right-hand side, meets
-    1e-8 (to the rounding of that check); the first and last problems match the
-    oracle's solutions; a second solve of the whole batch and a problem solved
-    alone give the same bits as the first batch (the solver is deterministic
-    under any load, and the CTAs do not interact)."""
+    1e-8 (to the rounding of that check); the first, middle and last problems
+    match the oracle's solutions; a second solve of the whole batch and those
+    problems solved alone give the same bits as the first batch (the solver is
+    deterministic under any load, and the CTAs do not interact)."""
     from paper_math_9809043_gb300 import tune as TU
     nb = torch.cuda.get_device_properties(0).multi_processor_count
     base = P.config_problem(1)
