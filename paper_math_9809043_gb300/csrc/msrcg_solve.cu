@@ -2183,6 +2183,13 @@ void launch_small_any(int dim, bool f32, const ProblemDesc* P, const int* order,
   }
 }
 
+// Whether the batched solver may smooth HBM-resident levels in one pass.
+// Post-smoothing prefetches the r row its last stage reads kFuseAhead steps
+// ahead, starting at step 0 with row kFuseAhead - 2(S-1) = kFuseAhead - 4m:
+// for 4m < kFuseAhead the first rows would never be loaded, so m = 1 keeps
+// the per-half-sweep passes.
+bool fuse_on(const msrcg_hier* h) { return h->o.plain_sweeps == 0 && 4 * h->o.m >= kFuseAhead; }
+
 // Dynamic shared memory of a single-CTA launch for levels lo..kmax of h: the
 // levels that fit (coarsest first) and the coarsest inverse; when a 2D FP32
 // level of at least 4096 cells stays in global memory, the whole per-CTA
@@ -2204,7 +2211,7 @@ size_t levels_smem(const msrcg_hier* h, int lo, bool top_double) {
   const size_t ainv = sizeof(double) * (size_t)h->nc * h->nc;
   if (tot + ainv <= lim) tot += ainv;
   const long long fmin = h->o.fuse_min_cells > 0 ? h->o.fuse_min_cells : kFuseMinCells;
-  if (h->dim == 2 && f32 && h->o.plain_sweeps == 0)
+  if (h->dim == 2 && f32 && fuse_on(h))
     for (int k = lo; k < kfit; ++k)
       if (h->N[k] >= fmin) return lim;
   return tot;
@@ -2225,7 +2232,7 @@ ProblemDesc make_desc(msrcg_hier* h, const double* b, double* x, double tol) {
   pd.xs = h->xs;
   pd.tol = tol;
   pd.work = h->N[0];
-  pd.fuse = h->o.plain_sweeps == 0;
+  pd.fuse = fuse_on(h);
   pd.fuse_width = h->o.fuse_width;
   pd.fuse_min_cells = h->o.fuse_min_cells > 0 ? h->o.fuse_min_cells : kFuseMinCells;
   pd.splitting = h->o.splitting;

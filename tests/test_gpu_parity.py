@@ -532,3 +532,27 @@ def test_tuner_picks_a_candidate(M):
     fastest, times = TU.tune(probs, steps=1, candidates=cands)
     assert fastest in cands and set(times) == {TU.key_of(c) for c in cands}
     assert times[TU.key_of(fastest)] == min(times.values())
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_smoothing_degree_one(M, prec):
+    """m = 1 (three half-sweeps per smoothing) on a 256^2 field whose finest
+    level the batched solver keeps in global memory: the single-pass
+    smoother needs 4m >= its prefetch distance, so this runs the
+    per-half-sweep passes; batched and single solves match the oracle run
+    with the same m."""
+    prob = P.config_problem(1, scale=256)
+    opts = M.default_opts(m=1, precision=prec, inner_floor=1e-6 if prec else 0.0)
+    H = M.Hierarchy.from_problem(prob, opts)
+    b = H.rhs_for(prob)
+    R = O.Hierarchy(prob, m=1)
+    xr, sr = R.solve(R.lift_rhs(), 1e-8)
+    assert sr["status"] == 0
+    xs, sts = M.batch_solve([H], [b], 1e-8)
+    x1, s1 = H.solve(b, 1e-8)
+    for x, st in ((xs[0], sts[0]), (x1, s1)):
+        assert st["status"] == 0 and st["relres_true"] < 1e-8, st
+        err = np.linalg.norm(x.cpu().numpy() - xr) / np.linalg.norm(xr)
+        assert err <= SOL_RTOL, err
+        if prec == 0:
+            _counts_close(st["iters"], sr["iters"], sr["calls"])
