@@ -103,21 +103,30 @@ void drop_device(msrcg_server* sv, Request& r, cudaStream_t s) {
   sv->used -= std::min(sv->used, r.bytes);
 }
 
-// Build the hierarchy of a waiting request and stage its right-hand side.
-int admit(msrcg_server* sv, Request& r) {
+// Stage a request's inputs on the device (K and the boundary mask into the
+// caller's temporaries *dK, *dbc; b and the solution buffer into the
+// request) and build its hierarchy.
+int stage_and_build(msrcg_server* sv, Request& r, void** dK, void** dbc) {
   cudaStream_t s = sv->build_stream;
-  void *dK = nullptr, *dbc = nullptr;
   const int nbf = boundary_faces(r.grid);
-  MSRCG_CUDA_TRY(cudaMallocAsync(&dK, sizeof(double) * r.N * r.ncomp, s));
-  MSRCG_CUDA_TRY(cudaMallocAsync(&dbc, (size_t)nbf, s));
+  MSRCG_CUDA_TRY(cudaMallocAsync(dK, sizeof(double) * r.N * r.ncomp, s));
+  MSRCG_CUDA_TRY(cudaMallocAsync(dbc, (size_t)nbf, s));
   MSRCG_CUDA_TRY(cudaMallocAsync((void**)&r.d_b, sizeof(double) * r.N, s));
   MSRCG_CUDA_TRY(cudaMallocAsync((void**)&r.d_x, sizeof(double) * r.N, s));
-  MSRCG_CUDA_TRY(cudaMemcpyAsync(dK, r.K_host, sizeof(double) * r.N * r.ncomp, cudaMemcpyHostToDevice, s));
-  MSRCG_CUDA_TRY(cudaMemcpyAsync(dbc, r.bc_host, (size_t)nbf, cudaMemcpyHostToDevice, s));
+  MSRCG_CUDA_TRY(cudaMemcpyAsync(*dK, r.K_host, sizeof(double) * r.N * r.ncomp, cudaMemcpyHostToDevice, s));
+  MSRCG_CUDA_TRY(cudaMemcpyAsync(*dbc, r.bc_host, (size_t)nbf, cudaMemcpyHostToDevice, s));
   MSRCG_CUDA_TRY(cudaMemcpyAsync(r.d_b, r.b_host, sizeof(double) * r.N, cudaMemcpyHostToDevice, s));
-  int rc = msrcg_build_ex(&r.grid, (const double*)dK, r.ncomp, (const uint8_t*)dbc, &sv->opts, s, s, &r.h);
-  cudaFreeAsync(dK, s);
-  cudaFreeAsync(dbc, s);
+  return msrcg_build_ex(&r.grid, (const double*)*dK, r.ncomp, (const uint8_t*)*dbc, &sv->opts, s, s, &r.h);
+}
+
+// Build the hierarchy of a waiting request and stage its right-hand side.
+// The temporaries are freed on every path; on failure the caller releases
+// the request's own buffers (drop_device).
+int admit(msrcg_server* sv, Request& r) {
+  void *dK = nullptr, *dbc = nullptr;
+  const int rc = stage_and_build(sv, r, &dK, &dbc);
+  if (dK) cudaFreeAsync(dK, sv->build_stream);
+  if (dbc) cudaFreeAsync(dbc, sv->build_stream);
   if (rc) {
     r.h = nullptr;
     return rc;
