@@ -109,6 +109,47 @@ def gaussian_random_field(shape, ell_cells: float, rng: np.random.Generator) -> 
     return g
 
 
+def power_law_field(n: int, rng: np.random.Generator, cutoff=(32.0, 4.0), angle_deg: float = 15.0,
+                    big: int = 2048) -> np.ndarray:
+    """Zero-mean, unit-variance Gaussian field on an n x n grid whose
+    autocorrelation is the power law (1 + d^T Lambda d)^(-1/4) of the paper's
+    test fields (Sec. 4), d in cells.  Lambda = Rot diag(1/c1^2, 1/c2^2) Rot^T
+    with cutoff lengths (c1, c2) in cells, the long axis at `angle_deg` to x.
+    The field is synthesised on a periodic big x big grid (the spectral
+    density is the FFT of the covariance, negative parts clipped) and the
+    lower-left n x n corner is kept, as the paper truncates its 2048^2 field
+    (Sec. 4.2).  Returned shape (n, n), x fastest."""
+    if n > big:
+        raise ValueError("field larger than its synthesis grid")
+    d = np.fft.fftfreq(big) * big  # signed periodic distances
+    X, Y = np.meshgrid(d, d, indexing="xy")
+    th = np.deg2rad(angle_deg)
+    u = np.cos(th) * X + np.sin(th) * Y
+    v = -np.sin(th) * X + np.cos(th) * Y
+    cov = (1.0 + (u / cutoff[0]) ** 2 + (v / cutoff[1]) ** 2) ** -0.25
+    spec = np.real(np.fft.fft2(cov))
+    spec[spec < 0.0] = 0.0
+    w = rng.standard_normal((big, big))
+    g = np.real(np.fft.ifft2(np.fft.fft2(w) * np.sqrt(spec)))[:n, :n]
+    return (g - g.mean()) / g.std()
+
+
+def base_case_problem(n: int = 1001, seed: int = 1006, variance: float = 2.0) -> Problem:
+    """The paper's base case (Sec. 4.1): a log-normal permeability with the
+    power-law autocorrelation, variance 2 of ln K, cutoff lengths 32 x 4
+    cells at 15 degrees (0.016 and 0.002 on a quarter of the unit square at
+    1000 cells), on an n x n grid of square cells; p = 1 at x = 0, p = 0 at
+    x = 1, no flow on the other sides, no source; lifted boundary data.  The
+    paper's own field is not published: this draws a field of the same
+    statistics."""
+    rng = np.random.default_rng(seed)
+    lnk = np.sqrt(variance) * power_law_field(n, rng)
+    bc, gD = standard_bc(2, (n, n))
+    return Problem(dim=2, n=(n, n), h=(0.5 / n, 0.5 / n), K=np.exp(lnk).reshape(1, -1), bc=bc, gD=gD,
+                   f=None, pbf=linear_lifting(2, (n, n)), name=f"base-case-{n}",
+                   meta={"seed": seed, "lnK_variance": variance, "cutoff_cells": [32, 4], "angle_deg": 15})
+
+
 def rescale(g: np.ndarray, lo: float, hi: float) -> np.ndarray:
     gmin, gmax = g.min(), g.max()
     return lo + (hi - lo) * (g - gmin) / (gmax - gmin)

@@ -815,3 +815,138 @@ def test_golden_iteration_counts_reproduce():
         assert st["iters"] == case["iters"]
         assert st["calls"] == case["calls"]
         np.testing.assert_allclose(np.linalg.norm(x), case["xnorm"], rtol=1e-9)
+
+
+# --------------------------------------------------------------------------
+# The level test of Sec. 3, ||r||^2 / N_k < f^k eps^2, against the residual
+# formed outside the oracle (operator assembled here from the level's face
+# transmissibilities), iterate by iterate.
+# --------------------------------------------------------------------------
+def _A_from_T(dims, Tx, Ty, Tz=None):
+    """The 5/7-point operator of one level assembled from its face arrays:
+    A[c, c] = sum of the cell's face T, A[c, nb] = -T of the shared face."""
+    nx, ny, nz = dims
+    N = nx * ny * nz
+    idx = np.arange(N).reshape(nz, ny, nx)
+    Txa = Tx.reshape(nz, ny, nx + 1)
+    Tya = Ty.reshape(nz, ny + 1, nx)
+    diag = Txa[:, :, :-1] + Txa[:, :, 1:] + Tya[:, :-1, :] + Tya[:, 1:, :]
+    rows, cols, vals = [], [], []
+    t = Txa[:, :, 1:-1]  # interior x-faces
+    rows += [idx[:, :, :-1].ravel(), idx[:, :, 1:].ravel()]
+    cols += [idx[:, :, 1:].ravel(), idx[:, :, :-1].ravel()]
+    vals += [-t.ravel(), -t.ravel()]
+    t = Tya[:, 1:-1, :]
+    rows += [idx[:, :-1, :].ravel(), idx[:, 1:, :].ravel()]
+    cols += [idx[:, 1:, :].ravel(), idx[:, :-1, :].ravel()]
+    vals += [-t.ravel(), -t.ravel()]
+    if Tz is not None:
+        Tza = Tz.reshape(nz + 1, ny, nx)
+        diag = diag + Tza[:-1] + Tza[1:]
+        t = Tza[1:-1]
+        rows += [idx[:-1].ravel(), idx[1:].ravel()]
+        cols += [idx[1:].ravel(), idx[:-1].ravel()]
+        vals += [-t.ravel(), -t.ravel()]
+    rows.append(idx.ravel())
+    cols.append(idx.ravel())
+    vals.append(diag.ravel())
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(N, N))
+
+
+def _first_below(values, thr):
+    for j, v in enumerate(values, start=1):
+        if v < thr:
+            return j
+    return None
+
+
+@pytest.mark.parametrize("n", [(32, 32), (64, 64), (20, 16, 12)])
+def test_level_test_stops_at_first_iterate_below_threshold(n):
+    """Sec. 3: the PCG on level k stops after the first update whose residual
+    satisfies ||r||^2 / N_k < f^k eps^2.  Level k is the one above the
+    coarsest, whose preconditioner applies the exact coarsest inverse, so its
+    iterates do not depend on eps.  The level's PCG is run with its iteration
+    cap at j = 1, 2, ...; each iterate's residual b_k - A_k x_j is formed here
+    from the level's transmissibilities.  With eps placed between two
+    iterates' residuals, the uncapped call must stop at the first j below the
+    threshold, and the misreadings -- no division by N_k, f^(k+1), a
+    threshold relative to ||b_k|| instead of the level-0 eps -- would stop
+    elsewhere."""
+    prob = P.grf_problem(n, seed=31, ell=6.0, half_span=2.5)
+    f = 0.1
+    H0 = O.Hierarchy(prob, f=f)
+    k = H0.nlev - 2
+    Nk = H0.ncells(k)
+    rng = np.random.default_rng(32)
+    bk = 1e3 * rng.standard_normal(Nk)  # per-cell size far from level 0's
+    bb_k = float(bk @ bk)
+    b0 = H0.lift_rhs()
+    A = _A_from_T(H0.dims[k], *H0.T(k))
+
+    def capped(eps2, j):
+        kw = {"maxit_outer": j} if k == 0 else {"maxit_inner": j}
+        Hj = O.Hierarchy(prob, f=f, **kw)
+        Hj.set_eps2(eps2)
+        Hj.reset_stats()
+        x = Hj.pcg(k, bk)
+        it, ca = Hj.stats()
+        assert it[k + 1] == ca[k + 1]  # the coarsest call: one exact iteration
+        r = bk - A @ x
+        return float(r @ r), it[k]
+
+    seq = [capped(1e-13 * bb_k / Nk / f ** k, j)[0] for j in range(1, 8)]
+    # J: the third iterate (or later) whose residual is below every earlier
+    # one by at least 2x (CG does not make the 2-norm monotone)
+    J = next(j for j in range(3, 7) if seq[j - 1] < 0.5 * min(seq[:j - 1]))
+    thr = min(1.5 * seq[J - 1], 0.9 * min(seq[:J - 1])) / Nk  # between iterates J-1 and J
+    eps2 = thr / f ** k
+    tau2 = eps2 * H0.ncells(0) / float(b0 @ b0)  # eps^2 = tau^2 ||b_0||^2 / N_0
+    H0.set_eps2(eps2)
+    H0.reset_stats()
+    H0.pcg(k, bk)
+    jstar = H0.stats()[0][k]
+    assert H0.status() == O.OK
+    rr = []
+    for j in range(1, J + 2):
+        v, itk = capped(eps2, j)
+        assert itk == min(j, jstar)
+        rr.append(v)
+    # the iterates do not depend on eps; a cap above j* changes nothing
+    np.testing.assert_allclose(rr[:J], seq[:J], rtol=1e-12)
+    assert rr[J] == rr[J - 1]
+    rr = seq
+    assert jstar == J
+    assert _first_below([v / Nk for v in rr], thr) == jstar
+    assert _first_below(rr, thr) != jstar                        # no / N_k
+    assert _first_below([v / Nk for v in rr], f * thr) != jstar  # f^(k+1)
+    assert _first_below([v / bb_k for v in rr], f ** k * tau2) != jstar  # relative to ||b_k||
+
+
+def test_table1_reproduction_on_a_base_case_field():
+    """Table 1 (Sec. 4.1): per-level iterations 5 / 20 / 63 / 94 / 119 on the
+    base case (1001^2, power-law log-normal K of variance 2, mean squared
+    residual reduced by 1e10, i.e. tau = 1e-5).  The paper's field is not
+    published; on a field of the same statistics, with Gauss-Seidel in the
+    natural order of the unknowns (the paper's A = D + U + L), the oracle's
+    levels 0-2 land within 25% of the paper's counts and levels 3-4 within a
+    factor 2 (they take 1.3-2x: see the design notes).  The red-black
+    ordering the GPU uses by default needs more iterations on the coarse
+    levels than the natural order."""
+    import json, os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_table1.json")))
+    paper = g["iterations"]
+    prob = P.base_case_problem(1001, seed=1006)
+    H = O.Hierarchy(prob, splitting=2)
+    assert [d[0] for d in H.dims] == [1001, 250, 63, 16, 4]  # Table 1: 1001/252/63/16/4
+    b = H.lift_rhs()
+    x, st = H.solve(b, 1e-5)
+    assert st["status"] == 0 and st["relres_true"] < 1e-5
+    it = st["iters"]
+    for k in range(3):
+        assert abs(it[k] - paper[k]) <= 0.25 * paper[k], (k, it, paper)
+    for k in (3, 4):
+        assert paper[k] / 2 <= it[k] <= 2 * paper[k], (k, it, paper)
+    Hrb = O.Hierarchy(prob, splitting=0)
+    _, srb = Hrb.solve(b, 1e-5)
+    assert srb["status"] == 0
+    assert all(srb["iters"][k] > it[k] for k in (1, 2, 3))
