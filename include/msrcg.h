@@ -240,8 +240,10 @@ void msrcg_server_destroy(msrcg_server* sv);
  *  b  device, N doubles (read only).   x  device, N doubles (output).
  *  stats  host, or NULL.  The call synchronises `stream` before returning.
  * Errors: MSRCG_EINVAL also when the problem's hierarchy does not fit the
- * scratch (about 20 000 cells in 2D FP64, e.g. 128x128; 24^3 in 3D);
- * otherwise as msrcg_build and msrcg_solve.
+ * scratch (largest square grids with the default options: 230x230 in FP64,
+ * 227x227 with the FP32 preconditioner; cubes: 35^3 and 34^3), returned
+ * before anything is enqueued on `stream`; otherwise as msrcg_build and
+ * msrcg_solve, after the work already enqueued has finished.
  * The first call on a device looks up the scratch's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
  * All calls share the one scratch and keep the previous call's contents

@@ -737,6 +737,67 @@ int msrcg_build_ex(const msrcg_grid* grid, const double* K, int ncomp, const uin
   return MSRCG_OK;
 }
 
+// Device bytes msrcg_build_ex allocates for this grid and options (the same
+// allocation list, in the same sizes; 0 for arguments it would reject).  The
+// server charges this before a request is built.
+size_t msrcg_build_bytes(const msrcg_grid* grid, const msrcg_opts* opts) {
+  if (!grid || (grid->dim != 2 && grid->dim != 3)) return 0;
+  const int dim = grid->dim;
+  for (int a = 0; a < dim; ++a)
+    if (grid->n[a] < 1 || !(grid->h[a] > 0.0)) return 0;
+  msrcg_opts o;
+  if (opts) o = *opts;
+  else msrcg_default_opts(&o);
+  if (o.scale < 2) return 0;
+  if (o.coarsest_max_side <= 0) o.coarsest_max_side = dim == 2 ? 8 : 4;
+  int n3[3] = {grid->n[0], grid->n[1], dim == 3 ? grid->n[2] : 1};
+  const double h3[3] = {grid->h[0], grid->h[1], dim == 3 ? grid->h[2] : 1.0};
+  int dims[kMaxLev][3];
+  const int nlev = level_sides(dim, n3, h3, o.scale, o.coarsest_max_side, o.coarsening, dims);
+  if (nlev < 1) return 0;
+  const bool f32 = o.precision == 1;
+  const size_t rsz = f32 ? sizeof(float) : sizeof(double);
+  size_t tot = 0;
+  auto add = [&](size_t b) { tot += b ? b : 16; };
+  for (int k = 0; k < nlev; ++k)
+    for (int a = 0; a < dim; ++a) {
+      const size_t nf = (size_t)(dims[k][0] + (a == 0)) * (dims[k][1] + (a == 1)) * (dims[k][2] + (a == 2));
+      add(sizeof(double) * nf);
+      if (f32) add(sizeof(float) * nf);
+    }
+  long long npad0 = 0;
+  for (int k = 0; k < nlev; ++k) {
+    if (k + 1 < nlev)
+      for (int a = 0; a < 3; ++a) {
+        const Axis1D ax = axis_tables(dims[k][a], dims[k + 1][a], o.interp);
+        add(sizeof(int) * ax.c0.size());
+        add(sizeof(int) * ax.c1.size());
+        add(sizeof(int) * ax.lo.size());
+        add(sizeof(int) * ax.hi.size());
+        add(rsz * ax.w.size());
+        add(rsz * ax.rw.size());
+      }
+    const long long npad = (long long)(dims[k][0] + 2) * (dims[k][1] + 2) * (dim == 3 ? dims[k][2] + 2 : 1);
+    if (k == 0) npad0 = npad;
+    const size_t vsz = k == 0 ? sizeof(double) : rsz;
+    for (int v = 0; v < 4; ++v) add(vsz * npad);
+    add(rsz * npad);
+    add(rsz * npad);
+    if (vsz != rsz) add(rsz * npad);
+  }
+  const size_t nc = (size_t)dims[nlev - 1][0] * dims[nlev - 1][1] * dims[nlev - 1][2];
+  add(sizeof(double) * nc * nc);
+  add(sizeof(double) * nc * nc);
+  add(sizeof(int));
+  add(sizeof(DevLevel) * nlev);
+  add(sizeof(SolveState));
+  add(sizeof(double) * kMaxLev * (size_t)kMaxGrid);
+  add(sizeof(double) * npad0);
+  add(sizeof(double) * npad0);
+  add(sizeof(ProblemDesc));
+  return tot;
+}
+
 extern "C" int msrcg_lift_rhs(msrcg_hier* h, const uint8_t* bc, const double* gD, const double* f, const double* pbf,
                               double* b, void* stream) {
   if (!h || !bc || !gD || !pbf || !b) return MSRCG_EINVAL;
@@ -912,46 +973,18 @@ int msrcg_build_into(msrcg_hier* h, const msrcg_grid* grid, const double* K, int
   const bool f32 = o.precision == 1;
   const size_t rsz = f32 ? sizeof(float) : sizeof(double);
   const int gmax = std::min(h->sms * 8, kMaxGrid);
-  Carve cv{base, cap, 0, true};
 
-  double hh[3] = {grid->h[0], grid->h[1], dim == 3 ? grid->h[2] : 1.0};
-  double ratio[3] = {(hh[1] * hh[2]) / hh[0], (hh[0] * hh[2]) / hh[1], (hh[0] * hh[1]) / hh[2]};
-  const long long nyz = (long long)n3[1] * n3[2], nxz = (long long)n3[0] * n3[2], nxy = (long long)n3[0] * n3[1];
-  const uint8_t* blo[3] = {bc, bc + 2 * nyz, bc + 2 * nyz + 2 * nxz};
-  const uint8_t* bhi[3] = {bc + nyz, bc + 2 * nyz + nxz, bc + 2 * nyz + 2 * nxz + nxy};
+  // ---- lay out every array first: a problem that does not fit is rejected
+  // before anything is enqueued, so an MSRCG_EINVAL leaves no work behind on
+  // the stream (the scratch is shared by every call) ----
+  Carve cv{base, cap, 0, true};
+  int tabW[kMaxLev][3] = {};
   for (int k = 0; k < h->nlev; ++k)
     for (int a = 0; a < dim; ++a) {
       const int* d = h->dims[k];
       long long nf = (long long)(d[0] + (a == 0)) * (d[1] + (a == 1)) * (d[2] + (a == 2));
       h->T64[k][a] = (double*)cv.take(sizeof(double) * nf);
-    }
-  if (!cv.ok) return MSRCG_EINVAL;
-  for (int a = 0; a < dim; ++a) {
-    long long nf = (long long)(n3[0] + (a == 0)) * (n3[1] + (a == 1)) * (n3[2] + (a == 2));
-    const double* Ka = K + (ncomp > 1 ? a * h->N[0] : 0);
-    k_face_trans<<<grid_for(nf, 256, gmax), 256, 0, st>>>(a, n3[0], n3[1], n3[2], ratio[a], Ka, blo[a], bhi[a],
-                                                           h->T64[0][a]);
-  }
-  for (int k = 0; k + 1 < h->nlev; ++k) {
-    int3 nf = make_int3(h->dims[k][0], h->dims[k][1], h->dims[k][2]);
-    int3 nc = make_int3(h->dims[k + 1][0], h->dims[k + 1][1], h->dims[k + 1][2]);
-    for (int a = 0; a < dim; ++a) {
-      long long ncf = (long long)(nc.x + (a == 0)) * (nc.y + (a == 1)) * (nc.z + (a == 2));
-      k_upscale<<<grid_for(ncf, 128, gmax), 128, 0, st>>>(a, nf, nc, h->T64[k][a], h->T64[k + 1][a]);
-    }
-  }
-  for (int k = 0; k < h->nlev; ++k)
-    for (int a = 0; a < dim; ++a) {
-      const int* d = h->dims[k];
-      long long nf = (long long)(d[0] + (a == 0)) * (d[1] + (a == 1)) * (d[2] + (a == 2));
-      if (f32) {
-        void* p = cv.take(sizeof(float) * nf);
-        if (!cv.ok) return MSRCG_EINVAL;
-        k_to_float<<<grid_for(nf, 256, gmax), 256, 0, st>>>(h->T64[k][a], (float*)p, nf);
-        h->TR[k][a] = p;
-      } else {
-        h->TR[k][a] = h->T64[k][a];
-      }
+      h->TR[k][a] = f32 ? cv.take(sizeof(float) * nf) : (void*)h->T64[k][a];
     }
   double fk = 1.0;
   for (int k = 0; k < h->nlev; ++k) {
@@ -978,59 +1011,30 @@ int msrcg_build_into(msrcg_hier* h, const msrcg_grid* grid, const double* K, int
       for (int a = 0; a < 3; ++a) {
         const int nf = h->dims[k][a], nc = h->dims[k + 1][a];
         const int W = 3 * ((nf + nc - 1) / nc) + 6;
-        int* c0 = (int*)cv.take(sizeof(int) * nf);
-        int* c1 = (int*)cv.take(sizeof(int) * nf);
-        void* w = cv.take(rsz * nf);
-        int* lo = (int*)cv.take(sizeof(int) * nc);
-        int* hi = (int*)cv.take(sizeof(int) * nc);
-        void* rw = cv.take(rsz * (size_t)nc * W);
-        if (!cv.ok) return MSRCG_EINVAL;
-        k_axis_tables<<<grid_for(std::max(nf, nc), 128, gmax), 128, 0, st>>>(nf, nc, W, c0, c1, w, lo, hi, rw, f32,
-                                                                             o.interp);
-        L.c0[a] = c0;
-        L.c1[a] = c1;
-        L.w[a] = w;
-        L.lo[a] = lo;
-        L.hi[a] = hi;
-        L.rw[a] = rw;
+        tabW[k][a] = W;
+        L.c0[a] = (const int*)cv.take(sizeof(int) * nf);
+        L.c1[a] = (const int*)cv.take(sizeof(int) * nf);
+        L.w[a] = cv.take(rsz * nf);
+        L.lo[a] = (const int*)cv.take(sizeof(int) * nc);
+        L.hi[a] = (const int*)cv.take(sizeof(int) * nc);
+        L.rw[a] = cv.take(rsz * (size_t)nc * W);
         L.W[a] = W;
       }
     }
-    // padded vectors; the ghost rings must be zero, and the buffer keeps the
-    // previous call's contents, so every vector is cleared
     const size_t vsz = k == 0 ? sizeof(double) : rsz;
-    void** vv[4] = {&L.x, &L.r, &L.p, &L.q};
-    for (int v = 0; v < 4; ++v) {
-      void* p = cv.take(vsz * L.npad);
-      if (!cv.ok) return MSRCG_EINVAL;
-      MSRCG_CUDA_TRY(cudaMemsetAsync(p, 0, vsz * L.npad, st));
-      *vv[v] = p;
-    }
+    L.x = cv.take(vsz * L.npad);
+    L.r = cv.take(vsz * L.npad);
+    L.p = cv.take(vsz * L.npad);
+    L.q = cv.take(vsz * L.npad);
     L.z = cv.take(rsz * L.npad);
     L.t = cv.take(rsz * L.npad);
     L.rp = vsz != rsz ? cv.take(rsz * L.npad) : L.r;
-    if (!cv.ok) return MSRCG_EINVAL;
-    MSRCG_CUDA_TRY(cudaMemsetAsync(L.z, 0, rsz * L.npad, st));
-    MSRCG_CUDA_TRY(cudaMemsetAsync(L.t, 0, rsz * L.npad, st));
-    if (vsz != rsz) MSRCG_CUDA_TRY(cudaMemsetAsync(L.rp, 0, rsz * L.npad, st));
   }
-  {
-    const int kc = h->nlev - 1;
-    h->nc = (int)h->N[kc];
-    double* A = (double*)cv.take(sizeof(double) * h->nc * h->nc);
-    double* Ai = (double*)cv.take(sizeof(double) * h->nc * h->nc);
-    int* fl = (int*)cv.take(sizeof(int));
-    if (!cv.ok) return MSRCG_EINVAL;
-    MSRCG_CUDA_TRY(cudaMemsetAsync(fl, 0, sizeof(int), st));
-    k_dense_assemble<<<1, 512, 0, st>>>(h->dims[kc][0], h->dims[kc][1], h->dims[kc][2], h->T64[kc][0], h->T64[kc][1],
-                                        dim == 3 ? h->T64[kc][2] : nullptr, A);
-    k_chol_inverse<<<1, 512, 0, st>>>(h->nc, A, Ai, fl);
-    int hf = 0;
-    MSRCG_CUDA_TRY(cudaMemcpyAsync(&hf, fl, sizeof(int), cudaMemcpyDeviceToHost, st));
-    MSRCG_CUDA_TRY(cudaStreamSynchronize(st));
-    if (hf) return MSRCG_EBREAKDOWN;
-    h->Ainv = Ai;
-  }
+  const int kc = h->nlev - 1;
+  h->nc = (int)h->N[kc];
+  double* A = (double*)cv.take(sizeof(double) * h->nc * h->nc);
+  double* Ai = (double*)cv.take(sizeof(double) * h->nc * h->nc);
+  int* fl = (int*)cv.take(sizeof(int));
   h->dL = (DevLevel*)cv.take(sizeof(DevLevel) * h->nlev);
   h->dS = (SolveState*)cv.take(sizeof(SolveState));
   h->xs = (double*)cv.take(sizeof(double) * h->hL[0].npad);
@@ -1038,9 +1042,72 @@ int msrcg_build_into(msrcg_hier* h, const msrcg_grid* grid, const double* K, int
   h->partials = nullptr;
   h->b0 = nullptr;
   if (!cv.ok) return MSRCG_EINVAL;
-  MSRCG_CUDA_TRY(cudaMemcpyAsync(h->dL, h->hL, sizeof(DevLevel) * h->nlev, cudaMemcpyHostToDevice, st));
-  MSRCG_CUDA_TRY(cudaMemsetAsync(h->dS, 0, sizeof(SolveState), st));
-  MSRCG_CUDA_TRY(cudaGetLastError());
+
+  // ---- enqueue the build; from here on an error waits for the work
+  // already enqueued before returning ----
+  auto fail = [&](int code) {
+    cudaStreamSynchronize(st);
+    (void)cudaGetLastError();
+    return code;
+  };
+  double hh[3] = {grid->h[0], grid->h[1], dim == 3 ? grid->h[2] : 1.0};
+  double ratio[3] = {(hh[1] * hh[2]) / hh[0], (hh[0] * hh[2]) / hh[1], (hh[0] * hh[1]) / hh[2]};
+  const long long nyz = (long long)n3[1] * n3[2], nxz = (long long)n3[0] * n3[2], nxy = (long long)n3[0] * n3[1];
+  const uint8_t* blo[3] = {bc, bc + 2 * nyz, bc + 2 * nyz + 2 * nxz};
+  const uint8_t* bhi[3] = {bc + nyz, bc + 2 * nyz + nxz, bc + 2 * nyz + 2 * nxz + nxy};
+  for (int a = 0; a < dim; ++a) {
+    long long nf = (long long)(n3[0] + (a == 0)) * (n3[1] + (a == 1)) * (n3[2] + (a == 2));
+    const double* Ka = K + (ncomp > 1 ? a * h->N[0] : 0);
+    k_face_trans<<<grid_for(nf, 256, gmax), 256, 0, st>>>(a, n3[0], n3[1], n3[2], ratio[a], Ka, blo[a], bhi[a],
+                                                           h->T64[0][a]);
+  }
+  for (int k = 0; k + 1 < h->nlev; ++k) {
+    int3 nf = make_int3(h->dims[k][0], h->dims[k][1], h->dims[k][2]);
+    int3 nc = make_int3(h->dims[k + 1][0], h->dims[k + 1][1], h->dims[k + 1][2]);
+    for (int a = 0; a < dim; ++a) {
+      long long ncf = (long long)(nc.x + (a == 0)) * (nc.y + (a == 1)) * (nc.z + (a == 2));
+      k_upscale<<<grid_for(ncf, 128, gmax), 128, 0, st>>>(a, nf, nc, h->T64[k][a], h->T64[k + 1][a]);
+    }
+  }
+  for (int k = 0; k < h->nlev; ++k)
+    for (int a = 0; a < dim && f32; ++a) {
+      const int* d = h->dims[k];
+      long long nf = (long long)(d[0] + (a == 0)) * (d[1] + (a == 1)) * (d[2] + (a == 2));
+      k_to_float<<<grid_for(nf, 256, gmax), 256, 0, st>>>(h->T64[k][a], (float*)h->TR[k][a], nf);
+    }
+  for (int k = 0; k < h->nlev; ++k) {
+    DevLevel& L = h->hL[k];
+    if (k + 1 < h->nlev)
+      for (int a = 0; a < 3; ++a) {
+        const int nf = h->dims[k][a], nc = h->dims[k + 1][a];
+        k_axis_tables<<<grid_for(std::max(nf, nc), 128, gmax), 128, 0, st>>>(
+            nf, nc, tabW[k][a], (int*)L.c0[a], (int*)L.c1[a], (void*)L.w[a], (int*)L.lo[a], (int*)L.hi[a],
+            (void*)L.rw[a], f32, o.interp);
+      }
+    // padded vectors; the ghost rings must be zero, and the buffer keeps the
+    // previous call's contents, so every vector is cleared
+    const size_t vsz = k == 0 ? sizeof(double) : rsz;
+    void* vv[4] = {L.x, L.r, L.p, L.q};
+    for (int v = 0; v < 4; ++v)
+      if (cudaMemsetAsync(vv[v], 0, vsz * L.npad, st) != cudaSuccess) return fail(MSRCG_ECUDA);
+    if (cudaMemsetAsync(L.z, 0, rsz * L.npad, st) != cudaSuccess ||
+        cudaMemsetAsync(L.t, 0, rsz * L.npad, st) != cudaSuccess ||
+        (vsz != rsz && cudaMemsetAsync(L.rp, 0, rsz * L.npad, st) != cudaSuccess))
+      return fail(MSRCG_ECUDA);
+  }
+  if (cudaMemsetAsync(fl, 0, sizeof(int), st) != cudaSuccess) return fail(MSRCG_ECUDA);
+  k_dense_assemble<<<1, 512, 0, st>>>(h->dims[kc][0], h->dims[kc][1], h->dims[kc][2], h->T64[kc][0], h->T64[kc][1],
+                                      dim == 3 ? h->T64[kc][2] : nullptr, A);
+  k_chol_inverse<<<1, 512, 0, st>>>(h->nc, A, Ai, fl);
+  int hf = 0;
+  if (cudaMemcpyAsync(&hf, fl, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(MSRCG_ECUDA);
+  if (hf) return MSRCG_EBREAKDOWN;
+  h->Ainv = Ai;
+  if (cudaMemcpyAsync(h->dL, h->hL, sizeof(DevLevel) * h->nlev, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemsetAsync(h->dS, 0, sizeof(SolveState), st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+    return fail(MSRCG_ECUDA);
   h->bytes = cv.off;
   return MSRCG_OK;
 }

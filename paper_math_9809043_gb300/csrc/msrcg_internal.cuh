@@ -159,6 +159,8 @@ int msrcg_build_ex(const msrcg_grid* grid, const double* K, int ncomp, const uin
 int msrcg_batch_enqueue(int count, msrcg_hier* const* hs, const double* const* b, double tol, double* const* x,
                         cudaStream_t s, msrcg::SolveState* host_states);
 int msrcg_batch_finish(int count, msrcg_hier* const* hs, const msrcg::SolveState* host_states, msrcg_stats* stats);
+// device bytes msrcg_build_ex allocates for a grid and options (0: rejected)
+size_t msrcg_build_bytes(const msrcg_grid* grid, const msrcg_opts* opts);
 // builds h inside the device buffer [base, base + cap) without allocating
 int msrcg_build_into(msrcg_hier* h, const msrcg_grid* grid, const double* K, int ncomp, const uint8_t* bc,
                      const msrcg_opts* opts, cudaStream_t st, unsigned char* base, size_t cap);

@@ -59,20 +59,11 @@ int boundary_faces(const msrcg_grid& g) {
   return (int)(2 * (ny * nz + nx * nz) + (g.dim == 3 ? 2 * nx * ny : 0));
 }
 
-// Device bytes a request will hold: its hierarchy (transmissibilities of
-// every level in FP64 and, in FP32 mode, FP32; padded vectors; coarse levels
-// add at most a seventh in 2D) plus its right-hand side and solution.
+// Device bytes a request will hold: its hierarchy (the build's own
+// allocation plan) plus its right-hand side and solution.
 size_t estimate_bytes(const msrcg_grid& g, const msrcg_opts& o) {
-  const int dim = g.dim;
-  const double nx = g.n[0], ny = g.n[1], nz = dim == 3 ? g.n[2] : 1;
-  const double N = nx * ny * nz;
-  const double pad = (nx + 2) * (ny + 2) * (dim == 3 ? nz + 2 : 1) / N;
-  const double rsz = o.precision == 1 ? 4.0 : 8.0;
-  double per = dim * 8.0 + (o.precision == 1 ? dim * 4.0 : 0.0);    // T64, T32
-  per += pad * (4 * 8.0 + 2 * rsz + (o.precision == 1 ? rsz : 0.0));  // x r p q; z t; rp
-  per += pad * 16.0;                                                  // b0, xs
-  per *= dim == 3 ? 1.2 : 1.1;                                        // coarse levels, tables
-  return (size_t)(N * per) + (size_t)(16.0 * N) + (1u << 20);         // + b, x; slack
+  const size_t N = (size_t)g.n[0] * g.n[1] * (g.dim == 3 ? g.n[2] : 1);
+  return msrcg_build_bytes(&g, &o) + 16 * N;
 }
 
 }  // namespace
@@ -132,8 +123,14 @@ int admit(msrcg_server* sv, Request& r) {
     return rc;
   }
   // the builder synchronised the build stream: the hierarchy and the staged
-  // right-hand side are ready for any other stream
-  r.bytes = std::max(r.bytes, r.h->bytes + (size_t)(16 * r.N));
+  // right-hand side are ready for any other stream.  The request was charged
+  // its estimate; when the measured size is larger, charge the difference
+  // too, so that releasing r.bytes later returns exactly what was charged.
+  const size_t measured = r.h->bytes + (size_t)(16 * r.N);
+  if (measured > r.bytes) {
+    sv->used += measured - r.bytes;
+    r.bytes = measured;
+  }
   return MSRCG_OK;
 }
 
@@ -252,6 +249,7 @@ extern "C" int msrcg_server_submit(msrcg_server* sv, const msrcg_grid* grid, con
   r.x_host = x;
   r.tol = tol;
   r.bytes = estimate_bytes(r.grid, sv->opts);
+  if (r.bytes == 0) return MSRCG_EINVAL;
   if (r.bytes > sv->budget) return MSRCG_ENOMEM;
   sv->reqs[r.id] = r;
   sv->waiting.push_back(r.id);

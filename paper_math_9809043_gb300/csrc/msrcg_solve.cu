@@ -25,6 +25,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <numeric>
 #include <vector>
 
@@ -2138,13 +2139,22 @@ int build_graph(msrcg_hier* h) {
 }
 
 // Largest dynamic shared memory a single-CTA launch may use, after the
-// kernel's static shared memory; sets the attribute the launch needs.
+// kernel's static shared memory; sets the attribute the launch needs.  The
+// attribute belongs to the current device, so both are kept per device
+// (under a lock: host threads may launch on several devices at once).
+constexpr int kMaxDevs = 64;
 template <int DIM, typename RP>
 size_t small_smem_limit() {
-  static size_t lim = 0;
-  if (!lim) {
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
+  static std::mutex mu;
+  static size_t lims[kMaxDevs] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevs) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!lims[dev]) {
+    int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaFuncAttributes fa;
     cudaFuncGetAttributes(&fa, k_small<DIM, RP>);
@@ -2156,9 +2166,9 @@ size_t small_smem_limit() {
     size_t l = (size_t)optin > fa.sharedSizeBytes + 1024 ? (size_t)optin - fa.sharedSizeBytes - 1024 : 0;
     cudaFuncSetAttribute(k_small<DIM, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l);
     (void)cudaGetLastError();
-    lim = l;
+    lims[dev] = l;
   }
-  return lim;
+  return lims[dev];
 }
 
 size_t small_smem_limit_any(int dim, bool f32) {
@@ -2462,19 +2472,30 @@ extern "C" int msrcg_solve_static(const msrcg_grid* grid, const double* K, int n
     g_static_ptr[dev] = p;
   }
   msrcg_hier h;  // host bookkeeping only; its device arrays are carved from the scratch
+  // an MSRCG_EINVAL for a problem that does not fit comes before any work is
+  // enqueued; every other error waits for the enqueued work first
   int rc = msrcg_build_into(&h, grid, K, ncomp, bc, opts, s, (unsigned char*)g_static_ptr[dev],
                             MSRCG_STATIC_SCRATCH_BYTES);
   if (rc) return rc;
+  auto fail = [&](cudaError_t e, const char* what) {
+    cudaStreamSynchronize(s);
+    return msrcg_cuda_fail(e, what, __FILE__, __LINE__);
+  };
   const bool f32 = h.o.precision == 1;
   ProblemDesc pd = make_desc(&h, b, x, tol);
-  MSRCG_CUDA_TRY(cudaMemcpyAsync(h.dP, &pd, sizeof(pd), cudaMemcpyHostToDevice, s));
+  cudaError_t e = cudaMemcpyAsync(h.dP, &pd, sizeof(pd), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return fail(e, "cudaMemcpyAsync(desc)");
   const double floor2 = f32 ? h.o.inner_floor * h.o.inner_floor : 0.0;
-  MSRCG_CUDA_TRY(cudaMemcpyAsync(&h.dS->inner_floor2, &floor2, sizeof(double), cudaMemcpyHostToDevice, s));
+  e = cudaMemcpyAsync(&h.dS->inner_floor2, &floor2, sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return fail(e, "cudaMemcpyAsync(floor)");
   launch_small_any(h.dim, f32, h.dP, nullptr, 1, 0, 2, nullptr, 1, levels_smem(&h, 0, true), s);
-  MSRCG_CUDA_TRY(cudaGetLastError());
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(e, "k_small");
   SolveState hs;
-  MSRCG_CUDA_TRY(cudaMemcpyAsync(&hs, h.dS, sizeof(hs), cudaMemcpyDeviceToHost, s));
-  MSRCG_CUDA_TRY(cudaStreamSynchronize(s));
+  e = cudaMemcpyAsync(&hs, h.dS, sizeof(hs), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return fail(e, "cudaMemcpyAsync(state)");
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(e, "cudaStreamSynchronize");
   msrcg_stats one;
   fill_stats(&h, hs, &one, 0);
   if (stats) *stats = one;

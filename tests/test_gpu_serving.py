@@ -86,3 +86,45 @@ def test_oversize_request_rejected(S):
         sv.submit(p, p.b)
     assert ei.value.code == M.ENOMEM
     sv.close()
+
+
+def _thin(seed, n):
+    rng = np.random.default_rng(seed)
+    N = n[0] * n[1]
+    K = (10.0 ** rng.uniform(-2, 2, N)).reshape(1, -1)
+    bc, gD = P.standard_bc(2, n)
+    return P.Problem(dim=2, n=n, h=(1.0 / n[0], 1.0 / n[1]), K=K, bc=bc, gD=gD, b=rng.standard_normal(N))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_admission_charges_the_built_size(S, prec):
+    """A request is charged exactly the device memory its hierarchy, right-
+    hand side and solution take, also on thin grids whose levels shrink along
+    one axis only (coarse levels add a third, not a fifteenth); with a budget
+    for two such requests the charge never exceeds it and returns to zero."""
+    M, serve = S
+    opts = M.default_opts(precision=prec, inner_floor=1e-6 if prec else 0.0)
+    probs = [_thin(60 + j, (3000 + 100 * j, 6)) for j in range(4)]
+    sizes = []
+    for p in probs:
+        H = M.Hierarchy.from_problem(p, opts)
+        sizes.append(H.device_bytes() + 16 * p.N)
+        H.close()
+    sv = serve.Server(1 << 30, max_waves=2, opts=opts)
+    rid, _ = sv.submit(probs[0], probs[0].b)
+    assert sv.bytes_in_use() == sizes[0]
+    sv.drain()
+    assert sv.poll(rid)[0] and sv.bytes_in_use() == 0
+    sv.close()
+    budget = sizes[-1] + sizes[-2]
+    sv = serve.Server(budget, max_waves=2, opts=opts)
+    reqs = [sv.submit(p, p.b) for p in probs]
+    assert sv.bytes_in_use() <= budget
+    while sv.progress() > 0:
+        assert sv.bytes_in_use() <= budget
+    sv.drain()
+    for (rid, x), p in zip(reqs, probs):
+        done, st = sv.poll(rid)
+        assert done and st["status"] == 0 and st["relres_true"] < 1e-8
+    assert sv.bytes_in_use() == 0
+    sv.close()

@@ -78,9 +78,58 @@ def test_static_matches_allocating_solve_with_options(M, extra):
     H.close()
 
 
+@pytest.mark.parametrize("dim,prec,side", [(2, 0, 230), (2, 1, 227), (3, 0, 35), (3, 1, 34)])
+def test_static_capacity(M, dim, prec, side):
+    """The largest square / cubic grids the fixed scratch holds (the limits
+    the header states): `side` solves and matches the allocating solve, one
+    cell more per axis is rejected with MSRCG_EINVAL before anything is
+    enqueued (the stream is idle right after the call)."""
+    opts = M.default_opts(precision=prec, inner_floor=1e-6 if prec else 0.0)
+    prob = _problem((side,) * dim, 41)
+    H = M.Hierarchy.from_problem(prob, opts)
+    b = torch.as_tensor(prob.b, device="cuda")
+    xa, sa = H.solve(b, 1e-8)
+    xs, ss = M.solve_static(prob.dim, prob.n, prob.h, prob.K, prob.bc, b, 1e-8, opts=opts)
+    torch.cuda.synchronize()
+    assert ss["status"] == 0 and ss["relres_true"] < 1e-8, ss
+    err = (torch.linalg.norm(xs - xa) / torch.linalg.norm(xa)).item()
+    assert err <= SOL_RTOL, err
+    H.close()
+    big = _problem((side + 1,) * dim, 42)
+    bb = torch.as_tensor(big.b, device="cuda")
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    with pytest.raises(M.MsrcgError) as ei:
+        M.solve_static(big.dim, big.n, big.h, big.K, big.bc, bb, 1e-8, opts=opts, stream=s)
+    assert ei.value.code == M.EINVAL
+    assert s.query()  # nothing was left running on the stream
+
+
+def test_static_calls_of_different_shapes_in_a_row(M):
+    """Calls share the scratch and each lays it out for its own problem: a
+    large 2D FP32 call, a small 3D FP64 call in the space the first one used,
+    then the large one again; each matches the allocating solve."""
+    seq = [((100, 90), 1, 51), ((12, 10, 9), 0, 52), ((100, 90), 1, 53)]
+    for call, (n, prec, seed) in enumerate(seq):
+        opts = M.default_opts(precision=prec, inner_floor=1e-6 if prec else 0.0)
+        prob = _problem(n, seed)
+        H = M.Hierarchy.from_problem(prob, opts)
+        b = torch.as_tensor(prob.b, device="cuda")
+        xa, sa = H.solve(b, 1e-8)
+        xs, ss = M.solve_static(prob.dim, prob.n, prob.h, prob.K, prob.bc, b, 1e-8, opts=opts)
+        torch.cuda.synchronize()
+        assert ss["status"] == 0 and ss["relres_true"] < 1e-8, (call, ss)
+        err = (torch.linalg.norm(xs - xa) / torch.linalg.norm(xa)).item()
+        assert err <= SOL_RTOL, (call, err)
+        H.close()
+
+
 def test_static_rejects_oversize(M):
     prob = _problem((400, 400), 3)
     b = torch.as_tensor(prob.b, device="cuda")
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
     with pytest.raises(M.MsrcgError) as ei:
-        M.solve_static(prob.dim, prob.n, prob.h, prob.K, prob.bc, b, 1e-8)
+        M.solve_static(prob.dim, prob.n, prob.h, prob.K, prob.bc, b, 1e-8, stream=s)
     assert ei.value.code == M.EINVAL
+    assert s.query()
