@@ -127,6 +127,25 @@ int msrcg_default_opts(msrcg_opts* o);
 int msrcg_build(const msrcg_grid* grid, const double* K, int ncomp, const uint8_t* bc,
                 const msrcg_opts* opts, void* stream, msrcg_hier** out);
 
+/* Build the level hierarchy from face permeabilities (Sec. 3: the components
+ * of K are face centred -- K_xx half a cell off the cell centre in x, K_yy in
+ * y -- and the type of boundary condition is carried by the discretised K of
+ * the boundary faces).
+ *  grid  host; validated as msrcg_build.
+ *  Kx    device, double, (nx+1)*ny*nz: K_xx on the x-faces, x fastest, the
+ *        boundary faces i = 0 and i = nx included.  A Dirichlet boundary
+ *        face holds the K of the half cell between the face and the centre
+ *        (2 K_cell reproduces msrcg_build), a Neumann face holds 0.
+ *  Ky    device, nx*(ny+1)*nz: K_yy on the y-faces, likewise.
+ *  Kz    device, nx*ny*(nz+1) in 3D; ignored (may be NULL) in 2D.
+ *  T = (h_perp/h_par) K_face on every face (one rounding); the rest of the
+ *  hierarchy is built as by msrcg_build, which it equals bit for bit when
+ *  the faces hold msrcg_build's harmonic means.  The arrays are read before
+ *  the call returns.  Synchronises `stream`.
+ *  Errors: as msrcg_build. */
+int msrcg_build_faces(const msrcg_grid* grid, const double* Kx, const double* Ky, const double* Kz,
+                      const msrcg_opts* opts, void* stream, msrcg_hier** out);
+
 /* Right-hand side of the lifted problem, Sec. 3: with a field P_bf that
  * matches the boundary values, writes b = f*vol + g_D - A P_bf, where g_D
  * sums T_face * gD over the Dirichlet faces of each boundary cell.

@@ -208,6 +208,25 @@ void or_face_trans(int dim, const int n[3], const double h[3], const double *K, 
 }
 
 /* ---------------------------------------------------------------------------
+ * Face transmissibilities from face permeabilities.  Sec. 3: the components
+ * of K are face centred (K_xx half a cell off the centre in x), and the type
+ * of boundary condition is carried by the discretised K of the boundary
+ * faces; T_xx = (dy/dx) K_xx (times dz in 3D) on every face, boundary faces
+ * included.  Kx has (nx+1)*ny*nz entries, Ky nx*(ny+1)*nz, Kz nx*ny*(nz+1).
+ * ------------------------------------------------------------------------- */
+void or_face_trans_faces(int dim, const int n[3], const double h[3], const double *Kx, const double *Ky,
+                         const double *Kz, double *Tx, double *Ty, double *Tz) {
+  int nx = n[0], ny = n[1], nz = dim == 3 ? n[2] : 1;
+  double hx = h[0], hy = h[1], hz = dim == 3 ? h[2] : 1.0;
+  double rx = (hy * hz) / hx, ry = (hx * hz) / hy, rz = (hx * hy) / hz;
+  int64_t nfx = (int64_t)(nx + 1) * ny * nz, nfy = (int64_t)nx * (ny + 1) * nz, nfz = (int64_t)nx * ny * (nz + 1);
+  for (int64_t f = 0; f < nfx; ++f) Tx[f] = rx * Kx[f];
+  for (int64_t f = 0; f < nfy; ++f) Ty[f] = ry * Ky[f];
+  if (dim == 3)
+    for (int64_t f = 0; f < nfz; ++f) Tz[f] = rz * Kz[f];
+}
+
+/* ---------------------------------------------------------------------------
  * Coarse transmissibility, Sec. 3: 1/T^c = sum_i 1/(sum_j T(i,j)) with the
  * partial-overlap scaling (fraction of height, inverse fraction of width).
  * Lengths along an axis with nf fine and nc coarse cells on a unit interval
@@ -592,8 +611,11 @@ void or_free(or_hier *H) {
 /* opts: s, m, f, coarsest side limit, max outer / inner iterations, level-side
  * rule (0: factor s per long axis, 1: toward square cells), interpolation
  * (0: linear with zero slope at the boundary, 1: piecewise constant) */
-or_hier *or_build(int dim, const int n[3], const double h[3], const double *K, int ncomp, const unsigned char *bc,
-                  int s, int m, double f, int maxside, int maxit_outer, int maxit_inner, int coarsening, int interp) {
+/* Level-0 permeabilities: cell values with boundary types (K, ncomp, bc), or
+ * face values with the boundary conditions in them (Kf[0..2], Kf[0] set). */
+static or_hier *build_hier(int dim, const int n[3], const double h[3], const double *K, int ncomp,
+                           const unsigned char *bc, const double *const *Kf, int s, int m, double f, int maxside,
+                           int maxit_outer, int maxit_inner, int coarsening, int interp) {
   int dims[OR_MAXLEV * 3];
   int nlev = or_hierarchy_dims2(dim, n, h, s, maxside, coarsening, OR_MAXLEV, dims);
   if (interp < 0 || interp > 1) return NULL;
@@ -624,7 +646,8 @@ or_hier *or_build(int dim, const int n[3], const double h[3], const double *K, i
     L->t = calloc(L->n, sizeof(double));
     L->aw = calloc(L->n, sizeof(double));
   }
-  or_face_trans(dim, n, h, K, ncomp, bc, H->L[0].Tx, H->L[0].Ty, H->L[0].Tz);
+  if (Kf) or_face_trans_faces(dim, n, h, Kf[0], Kf[1], Kf[2], H->L[0].Tx, H->L[0].Ty, H->L[0].Tz);
+  else or_face_trans(dim, n, h, K, ncomp, bc, H->L[0].Tx, H->L[0].Ty, H->L[0].Tz);
   for (int k = 0; k + 1 < nlev; ++k) {
     or_level *F = &H->L[k], *C = &H->L[k + 1];
     int nf[3] = {F->nx, F->ny, F->nz}, nc[3] = {C->nx, C->ny, C->nz};
@@ -646,6 +669,19 @@ or_hier *or_build(int dim, const int n[3], const double h[3], const double *K, i
     return NULL;
   }
   return H;
+}
+
+or_hier *or_build(int dim, const int n[3], const double h[3], const double *K, int ncomp, const unsigned char *bc,
+                  int s, int m, double f, int maxside, int maxit_outer, int maxit_inner, int coarsening, int interp) {
+  return build_hier(dim, n, h, K, ncomp, bc, NULL, s, m, f, maxside, maxit_outer, maxit_inner, coarsening, interp);
+}
+
+/* The same hierarchy from face permeabilities (or_face_trans_faces). */
+or_hier *or_build_faces(int dim, const int n[3], const double h[3], const double *Kx, const double *Ky,
+                        const double *Kz, int s, int m, double f, int maxside, int maxit_outer, int maxit_inner,
+                        int coarsening, int interp) {
+  const double *Kf[3] = {Kx, Ky, Kz};
+  return build_hier(dim, n, h, NULL, 0, NULL, Kf, s, m, f, maxside, maxit_outer, maxit_inner, coarsening, interp);
 }
 
 int or_nlev(const or_hier *H) { return H->nlev; }

@@ -59,6 +59,11 @@ def lib():
         L.or_build.argtypes = [C.c_int, _ip, _dp, _dp, C.c_int, _u8p, C.c_int, C.c_int, C.c_double,
                                C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]
         L.or_build.restype = C.c_void_p
+        L.or_build_faces.argtypes = [C.c_int, _ip, _dp, _dp, _dp, C.c_void_p, C.c_int, C.c_int, C.c_double,
+                                     C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]
+        L.or_build_faces.restype = C.c_void_p
+        L.or_face_trans_faces.argtypes = [C.c_int, _ip, _dp, _dp, _dp, C.c_void_p, _dp, _dp, C.c_void_p]
+        L.or_face_trans_faces.restype = None
         L.or_free.argtypes = [C.c_void_p]
         L.or_free.restype = None
         L.or_nlev.argtypes = [C.c_void_p]
@@ -132,6 +137,20 @@ def face_trans(dim, n, h, K, bc):
     return Tx, Ty, Tz
 
 
+def face_trans_faces(dim, n, h, Kx, Ky, Kz=None):
+    """T = (h_perp/h_par) K_face on every face (Sec. 3, face-centred K)."""
+    n3 = list(n) + [1] * (3 - len(n))
+    nx, ny, nz = n3
+    Tx = np.zeros((nx + 1) * ny * nz)
+    Ty = np.zeros(nx * (ny + 1) * nz)
+    Tz = np.zeros(nx * ny * (nz + 1)) if dim == 3 else None
+    Kz = np.ascontiguousarray(Kz, np.float64) if dim == 3 else None
+    lib().or_face_trans_faces(dim, _i3(n, dim), _d3(h, dim), np.ascontiguousarray(Kx, np.float64),
+                              np.ascontiguousarray(Ky, np.float64), Kz.ctypes.data if Kz is not None else None,
+                              Tx, Ty, Tz.ctypes.data if Tz is not None else None)
+    return Tx, Ty, Tz
+
+
 def upscale(dim, nf, nc, Tx, Ty, Tz=None):
     f3, c3 = _i3(nf, dim), _i3(nc, dim)
     Txc = np.zeros((c3[0] + 1) * c3[1] * c3[2])
@@ -157,19 +176,28 @@ class Hierarchy:
     """Oracle level hierarchy of one problem (Sec. 2.3 / Sec. 3)."""
 
     def __init__(self, prob, s=4, m=4, f=0.1, maxside=None, maxit_outer=200, maxit_inner=500, splitting=0,
-                 coarsening=0, interp=0):
+                 coarsening=0, interp=0, Kfaces=None):
         """splitting: 0 = symmetric Gauss-Seidel (red-black), 1 = modified
         Jacobi P = 2D, 2 = symmetric Gauss-Seidel in the natural order
         (Sec. 3).  coarsening: 0 = factor s on every long axis, 1 = toward
         square cells (Sec. 4.4).  interp: 0 = linear extension, 1 = piecewise
-        constant (Sec. 3)."""
+        constant (Sec. 3).  Kfaces: (Kx, Ky[, Kz]) face permeabilities with
+        the boundary conditions in the boundary faces' values; when given,
+        they replace the problem's cell K and boundary types."""
         self.prob = prob
         self.dim = prob.dim
         maxside = maxside or (8 if prob.dim == 2 else 4)
-        K = np.ascontiguousarray(prob.K, np.float64)
-        self._h = lib().or_build(prob.dim, _i3(prob.n, prob.dim), _d3(prob.h, prob.dim), K.reshape(-1),
-                                 K.shape[0], np.ascontiguousarray(prob.bc, np.uint8), s, m, f, maxside,
-                                 maxit_outer, maxit_inner, coarsening, interp)
+        if Kfaces is not None:
+            Kf = [np.ascontiguousarray(a, np.float64) for a in Kfaces]
+            self._h = lib().or_build_faces(prob.dim, _i3(prob.n, prob.dim), _d3(prob.h, prob.dim), Kf[0], Kf[1],
+                                           Kf[2].ctypes.data if prob.dim == 3 else None, s, m, f, maxside,
+                                           maxit_outer, maxit_inner, coarsening, interp)
+            self._keep = Kf
+        else:
+            K = np.ascontiguousarray(prob.K, np.float64)
+            self._h = lib().or_build(prob.dim, _i3(prob.n, prob.dim), _d3(prob.h, prob.dim), K.reshape(-1),
+                                     K.shape[0], np.ascontiguousarray(prob.bc, np.uint8), s, m, f, maxside,
+                                     maxit_outer, maxit_inner, coarsening, interp)
         if not self._h:
             raise ValueError("oracle build failed")
         lib().or_set_splitting(self._h, int(splitting))

@@ -210,6 +210,14 @@ __global__ void k_face_trans(int ax, int nx, int ny, int nz, double ratio, const
   }
 }
 
+// Face transmissibilities from face permeabilities (Sec. 3: K is face
+// centred and its boundary faces carry the boundary condition): T =
+// (h_perp/h_par) K_face on every face.
+__global__ void k_face_scale(long long nf, double ratio, const double* __restrict__ Kf, double* __restrict__ T) {
+  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf; f += (long long)gridDim.x * blockDim.x)
+    T[f] = __dmul_rn(ratio, Kf[f]);
+}
+
 __device__ __forceinline__ long long d_overlap(long long a0, long long a1, long long b0, long long b1) {
   long long lo = a0 > b0 ? a0 : b0, hi = a1 < b1 ? a1 : b1;
   return hi > lo ? hi - lo : 0;
@@ -521,16 +529,54 @@ extern "C" int msrcg_build(const msrcg_grid* grid, const double* K, int ncomp, c
   return msrcg_build_ex(grid, K, ncomp, bc, opts, (cudaStream_t)stream, nullptr, out);
 }
 
+namespace {
+// Permeability of level 0: cell values with boundary types, or face values
+// (Kf[0] set) whose boundary faces carry the boundary condition.
+struct Level0K {
+  const double* K = nullptr;
+  int ncomp = 1;
+  const uint8_t* bc = nullptr;
+  const double* Kf[3] = {nullptr, nullptr, nullptr};
+};
+int build_hier(const msrcg_grid* grid, const Level0K& src, const msrcg_opts* opts, cudaStream_t stream,
+               cudaStream_t alloc_stream, msrcg_hier** out);
+}  // namespace
+
 int msrcg_build_ex(const msrcg_grid* grid, const double* K, int ncomp, const uint8_t* bc, const msrcg_opts* opts,
                    cudaStream_t stream, cudaStream_t alloc_stream, msrcg_hier** out) {
   if (!out) return MSRCG_EINVAL;
   *out = nullptr;
   if (!grid || !K || !bc) return MSRCG_EINVAL;
+  if (ncomp != 1 && ncomp != grid->dim) return MSRCG_EINVAL;
+  Level0K src;
+  src.K = K;
+  src.ncomp = ncomp;
+  src.bc = bc;
+  return build_hier(grid, src, opts, stream, alloc_stream, out);
+}
+
+extern "C" int msrcg_build_faces(const msrcg_grid* grid, const double* Kx, const double* Ky, const double* Kz,
+                                 const msrcg_opts* opts, void* stream, msrcg_hier** out) {
+  if (!out) return MSRCG_EINVAL;
+  *out = nullptr;
+  if (!grid || !Kx || !Ky || (grid->dim == 3 && !Kz)) return MSRCG_EINVAL;
+  Level0K src;
+  src.Kf[0] = Kx;
+  src.Kf[1] = Ky;
+  src.Kf[2] = grid->dim == 3 ? Kz : nullptr;
+  return build_hier(grid, src, opts, (cudaStream_t)stream, nullptr, out);
+}
+
+namespace {
+int build_hier(const msrcg_grid* grid, const Level0K& src, const msrcg_opts* opts, cudaStream_t stream,
+               cudaStream_t alloc_stream, msrcg_hier** out) {
+  const double* K = src.K;
+  const int ncomp = src.ncomp;
+  const uint8_t* bc = src.bc;
   const int dim = grid->dim;
   if (dim != 2 && dim != 3) return MSRCG_EINVAL;
   for (int a = 0; a < dim; ++a)
     if (grid->n[a] < 1 || !(grid->h[a] > 0.0) || !isfinite(grid->h[a])) return MSRCG_EINVAL;
-  if (ncomp != 1 && ncomp != dim) return MSRCG_EINVAL;
   msrcg_opts o;
   if (opts) o = *opts;
   else msrcg_default_opts(&o);
@@ -578,9 +624,6 @@ int msrcg_build_ex(const msrcg_grid* grid, const double* K, int ncomp, const uin
   // ---- level 0 transmissibilities from cell K (A1) ----
   double hh[3] = {grid->h[0], grid->h[1], dim == 3 ? grid->h[2] : 1.0};
   double ratio[3] = {(hh[1] * hh[2]) / hh[0], (hh[0] * hh[2]) / hh[1], (hh[0] * hh[1]) / hh[2]};
-  const long long nyz = (long long)n3[1] * n3[2], nxz = (long long)n3[0] * n3[2], nxy = (long long)n3[0] * n3[1];
-  const uint8_t* blo[3] = {bc, bc + 2 * nyz, bc + 2 * nyz + 2 * nxz};
-  const uint8_t* bhi[3] = {bc + nyz, bc + 2 * nyz + nxz, bc + 2 * nyz + 2 * nxz + nxy};
   for (int k = 0; k < h->nlev; ++k) {
     const int* d = h->dims[k];
     for (int a = 0; a < dim; ++a) {
@@ -590,11 +633,21 @@ int msrcg_build_ex(const msrcg_grid* grid, const double* K, int ncomp, const uin
       h->T64[k][a] = (double*)p;
     }
   }
-  for (int a = 0; a < dim; ++a) {
-    long long nf = (long long)(n3[0] + (a == 0)) * (n3[1] + (a == 1)) * (n3[2] + (a == 2));
-    const double* Ka = K + (ncomp > 1 ? a * h->N[0] : 0);
-    k_face_trans<<<grid_for(nf, 256, gmax), 256, 0, st>>>(a, n3[0], n3[1], n3[2], ratio[a], Ka, blo[a], bhi[a],
-                                                           h->T64[0][a]);
+  if (src.Kf[0]) {
+    for (int a = 0; a < dim; ++a) {
+      long long nf = (long long)(n3[0] + (a == 0)) * (n3[1] + (a == 1)) * (n3[2] + (a == 2));
+      k_face_scale<<<grid_for(nf, 256, gmax), 256, 0, st>>>(nf, ratio[a], src.Kf[a], h->T64[0][a]);
+    }
+  } else {
+    const long long nyz = (long long)n3[1] * n3[2], nxz = (long long)n3[0] * n3[2], nxy = (long long)n3[0] * n3[1];
+    const uint8_t* blo[3] = {bc, bc + 2 * nyz, bc + 2 * nyz + 2 * nxz};
+    const uint8_t* bhi[3] = {bc + nyz, bc + 2 * nyz + nxz, bc + 2 * nyz + 2 * nxz + nxy};
+    for (int a = 0; a < dim; ++a) {
+      long long nf = (long long)(n3[0] + (a == 0)) * (n3[1] + (a == 1)) * (n3[2] + (a == 2));
+      const double* Ka = K + (ncomp > 1 ? a * h->N[0] : 0);
+      k_face_trans<<<grid_for(nf, 256, gmax), 256, 0, st>>>(a, n3[0], n3[1], n3[2], ratio[a], Ka, blo[a], bhi[a],
+                                                             h->T64[0][a]);
+    }
   }
   // ---- coarse transmissibilities (A2) ----
   for (int k = 0; k + 1 < h->nlev; ++k) {
@@ -736,6 +789,8 @@ int msrcg_build_ex(const msrcg_grid* grid, const double* K, int ncomp, const uin
   *out = h;
   return MSRCG_OK;
 }
+
+}  // namespace
 
 // Device bytes msrcg_build_ex allocates for this grid and options (the same
 // allocation list, in the same sizes; 0 for arguments it would reject).  The

@@ -68,6 +68,7 @@ def lib():
         vp = C.c_void_p
         L.msrcg_default_opts.argtypes = [C.POINTER(Opts)]
         L.msrcg_build.argtypes = [C.POINTER(Grid), vp, C.c_int, vp, C.POINTER(Opts), vp, C.POINTER(vp)]
+        L.msrcg_build_faces.argtypes = [C.POINTER(Grid), vp, vp, vp, C.POINTER(Opts), vp, C.POINTER(vp)]
         L.msrcg_lift_rhs.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.msrcg_solve.argtypes = [vp, vp, C.c_double, vp, C.POINTER(Stats), vp]
         L.msrcg_batch_solve.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(vp), C.c_double, C.POINTER(vp),
@@ -219,6 +220,43 @@ class Hierarchy:
     @classmethod
     def from_problem(cls, prob, opts: Opts | None = None, device="cuda", stream=None):
         return cls(prob.dim, prob.n, prob.h, prob.K, prob.bc, opts, device, stream)
+
+    @classmethod
+    def from_faces(cls, dim, n, h, Kfaces, opts: Opts | None = None, device="cuda", stream=None):
+        """Hierarchy from face permeabilities (msrcg_build_faces): Kfaces =
+        (Kx, Ky[, Kz]) with (nx+1) ny nz, nx (ny+1) nz[, nx ny (nz+1)] entries,
+        boundary faces included (a Dirichlet face holds its K, a Neumann face 0)."""
+        self = cls.__new__(cls)
+        self.device = _device(device)
+        self.dim = dim
+        self.n = tuple(int(v) for v in n)
+        self.N = int(np.prod(self.n))
+        g = Grid()
+        g.dim = dim
+        for a in range(3):
+            g.n[a] = self.n[a] if a < min(dim, len(self.n)) else 1
+            g.h[a] = float(h[a]) if a < min(dim, len(h)) else 1.0
+        n3 = [g.n[0], g.n[1], g.n[2]]
+        sizes = [(n3[0] + 1) * n3[1] * n3[2], n3[0] * (n3[1] + 1) * n3[2], n3[0] * n3[1] * (n3[2] + 1)]
+        Kt = [None, None, None]
+        if _valid_grid(dim, self.n):
+            if len(Kfaces) < dim:
+                raise ValueError(f"Kfaces: {len(Kfaces)} arrays for a {dim}D grid")
+            for a in range(dim):
+                Kt[a] = _dev(Kfaces[a], torch.float64, self.device, sizes[a], f"K{'xyz'[a]}")
+        else:
+            for a in range(min(dim, len(Kfaces))):
+                Kt[a] = _dev(Kfaces[a], torch.float64, self.device)
+        self.opts = opts or default_opts()
+        hp = C.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = lib().msrcg_build_faces(C.byref(g), _ptr(Kt[0]), _ptr(Kt[1]), _ptr(Kt[2]), C.byref(self.opts),
+                                         _stream(stream), C.byref(hp))
+        if rc != OK:
+            raise MsrcgError(rc, "msrcg_build_faces")
+        self._h = hp
+        self.nlev = lib().msrcg_num_levels(self._h)
+        return self
 
     def close(self):
         if getattr(self, "_h", None):

@@ -556,3 +556,74 @@ def test_smoothing_degree_one(M, prec):
         assert err <= SOL_RTOL, err
         if prec == 0:
             _counts_close(st["iters"], sr["iters"], sr["calls"])
+
+
+# ---------------------------------------------------------------------------
+# hierarchy from face permeabilities (msrcg_build_faces, Sec. 3)
+# ---------------------------------------------------------------------------
+def _random_faces(n, seed):
+    rng = np.random.default_rng(seed)
+    dim = len(n)
+    n3 = list(n) + [1] * (3 - dim)
+    sizes = [(n3[0] + 1) * n3[1] * n3[2], n3[0] * (n3[1] + 1) * n3[2], n3[0] * n3[1] * (n3[2] + 1)][:dim]
+    Kf = [10.0 ** rng.uniform(-4, 4, m) for m in sizes]
+    # boundary faces: Dirichlet with random K on x, Neumann (0) elsewhere, a
+    # few x-high faces Neumann too
+    Ky = Kf[1].reshape(n3[2], n3[1] + 1, n3[0])
+    Ky[:, 0, :] = 0.0
+    Ky[:, -1, :] = 0.0
+    Kx = Kf[0].reshape(n3[2], n3[1], n3[0] + 1)
+    Kx[:, :, -1] *= rng.random((n3[2], n3[1])) < 0.7
+    if dim == 3:
+        Kz = Kf[2].reshape(n3[2] + 1, n3[1], n3[0])
+        Kz[0] = 0.0
+        Kz[-1] = 0.0
+    N = int(np.prod(n))
+    bc, gD = P.standard_bc(dim, n)
+    prob = P.Problem(dim=dim, n=tuple(n), h=tuple(1.0 / m for m in n), K=np.ones((1, N)), bc=bc, gD=gD,
+                     b=rng.standard_normal(N))
+    return prob, Kf
+
+
+@pytest.mark.parametrize("n", [(37, 23), (300, 200), (12, 10, 9), (40, 24, 20)])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_face_K_build_matches_oracle(M, n, prec):
+    """Face values no cell field produces: transmissibilities of every level
+    bit-exact against the oracle's face-K build, and the solve within the
+    parity tolerance, norm-wise and element-wise."""
+    prob, Kf = _random_faces(n, 81)
+    opts = M.default_opts(precision=prec, inner_floor=1e-6 if prec else 0.0)
+    H = M.Hierarchy.from_faces(prob.dim, prob.n, prob.h, Kf, opts)
+    R = O.Hierarchy(prob, Kfaces=Kf)
+    assert H.nlev == R.nlev
+    for k in range(R.nlev):
+        for tg, tr in zip(H.trans(k), R.T(k)):
+            if tr is not None:
+                assert np.array_equal(tg.cpu().numpy(), tr), k
+    x, st = H.solve(torch.as_tensor(prob.b, device="cuda"), 1e-8)
+    xr, sr = R.solve(prob.b, 1e-8)
+    assert st["status"] == 0 and sr["status"] == 0 and st["relres_true"] < 1e-8, (st, sr)
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(xg - xr) / np.linalg.norm(xr) <= SOL_RTOL
+    assert np.max(np.abs(xg - xr)) / np.max(np.abs(xr)) <= SOL_RTOL
+    if prec == 0:
+        _counts_close(st["iters"], sr["iters"], sr["calls"])
+
+
+@pytest.mark.parametrize("n", [(64, 48), (13, 9, 7)])
+def test_face_K_from_harmonic_means_equals_cell_K_build(M, n):
+    """Faces holding the harmonic means of a cell field (2 K_cell on Dirichlet
+    faces, 0 on Neumann ones) give the cell-K build's hierarchy to the bit."""
+    from faces import face_K_from_cells
+    prob = _prob_uniform(n, span=4.0)
+    Kf = face_K_from_cells(prob)
+    A = M.Hierarchy.from_problem(prob)
+    B = M.Hierarchy.from_faces(prob.dim, prob.n, prob.h, Kf)
+    for k in range(A.nlev):
+        for ta, tb in zip(A.trans(k), B.trans(k)):
+            if ta is not None:
+                assert torch.equal(ta, tb), k
+    b = A.rhs_for(prob)
+    xa, _ = A.solve(b, 1e-8)
+    xb, _ = B.solve(b, 1e-8)
+    assert torch.equal(xa, xb)
