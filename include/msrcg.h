@@ -87,6 +87,26 @@ typedef struct {
                           never refined, and the level where no axis changes is the coarsest */
   int interp;          /* extension E (R = E^T): 0 = tensor linear interpolation with zero slope at
                           the boundary, 1 = piecewise constant (Sec. 3) */
+  int stall_iters;     /* precision 1: stall test of the level-0 PCG: when its residual norm has not
+                          halved for
+                          this many iterations it switches to the flexible (Polak-Ribiere) direction
+                          factor beta = r_new.(z_new - z_old) / r_old.z_old, which keeps the CG
+                          directions useful when the preconditioner is not exactly linear (the
+                          inexact inner solves of Sec. 2.3, FP32 inner levels); stalling again
+                          ends the solve with MSRCG_ENOCONV.  0 = 8; negative = no stall test.
+                          With precision 1 an inner level that hits its iteration cap also switches
+                          the level-0 PCG to the flexible beta instead of failing the solve. */
+  int escalate;        /* precision 1: a solve that ends in MSRCG_ENOCONV is run again with the FP64
+                          preconditioner (a twin hierarchy built on the device from the level-0
+                          transmissibilities, kept for later solves); 1 (default) = on, 0 = off.
+                          Applies to calls that synchronise (msrcg_solve with stats, batch). */
+  int flexible;        /* 1: the flexible beta from the first iteration (testing); 0 (default) */
+  int precond;         /* preconditioner of the level-0 PCG (Sec. 2): 0 = recursive multi-scale,
+                          eq. 2.10 (default); 1 = multigrid, eq. 2.9 (Tatebe): each coarse level
+                          applies the next one's preconditioner once instead of solving with a
+                          PCG; 2 = polynomial, eq. 2.6 with W = P^-1 (Sec. 2.1): 2m+1 splitting
+                          steps from zero, no coarse level.  1 and 2 run every level of a single
+                          solve in one CTA. */
   int reserved[1];
 } msrcg_opts;
 
@@ -101,12 +121,15 @@ typedef struct {
   double relres_true;       /* ||b - A x|| / ||b||, recomputed at the end */
   int status;
   int restarts;
+  int flexible;             /* 1: the level-0 PCG used the flexible beta */
+  int escalated;            /* 1: the result comes from the FP64-preconditioner rerun */
 } msrcg_stats;
 
 typedef struct msrcg_hier msrcg_hier;
 
 /* Fill *o with the paper's defaults: s = m = 4, f = 0.1, FP64, caps 200/500,
- * 2 s wait bound.  Returns MSRCG_OK, or MSRCG_EINVAL if o is NULL. */
+ * 2 s wait bound, stall test after 8 iterations, escalation on.  Returns
+ * MSRCG_OK, or MSRCG_EINVAL if o is NULL. */
 int msrcg_default_opts(msrcg_opts* o);
 
 /* Build the level hierarchy G_0..G_kmax (Sec. 2.2, 3) of one problem.

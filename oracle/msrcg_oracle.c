@@ -69,6 +69,9 @@ typedef struct {
   int status;
   int splitting;                        /* 0: symmetric Gauss-Seidel (red-black), 1: modified
                                            Jacobi, 2: symmetric Gauss-Seidel (natural order) */
+  int precond;                          /* preconditioner of the level-0 PCG (Sec. 2): 0 recursive
+                                           multi-scale (eq. 2.10), 1 multigrid (eq. 2.9, Tatebe),
+                                           2 polynomial (eq. 2.6 with W = P^-1) */
 } or_hier;
 
 static int64_t idx3(int i, int j, int k, int nx, int ny) {
@@ -700,6 +703,9 @@ void or_set_eps2(or_hier *H, double eps2) { H->eps2 = eps2; }
 /* 0: symmetric Gauss-Seidel (red-black), 1: modified Jacobi, 2: symmetric
  * Gauss-Seidel in the natural order (Sec. 3) */
 void or_set_splitting(or_hier *H, int splitting) { H->splitting = splitting; }
+/* 0: recursive multi-scale (eq. 2.10), 1: multigrid V-step (eq. 2.9),
+ * 2: polynomial (eq. 2.6 with W = P^-1) */
+void or_set_precond(or_hier *H, int precond) { H->precond = precond; }
 void or_get_stats(const or_hier *H, int64_t *iters, int64_t *calls) {
   for (int k = 0; k < H->nlev; ++k) {
     iters[k] = H->iters[k];
@@ -717,6 +723,14 @@ void or_reset_stats(or_hier *H) {
  * m smoothing steps from zero, the coarse correction E A_c^-1 R on the
  * residual that remains, then m smoothing steps.  A_c^-1 is applied by the
  * PCG of the next level (Sec. 2.3); the coarsest level uses the exact inverse.
+ *
+ * The two other preconditioners of Sec. 2 share the smoothing and transfers:
+ *  - multigrid (eq. 2.9, Tatebe): the same form with the coarse inverse
+ *    replaced by one application of the next level's preconditioner
+ *    M_{k+1}^-1, recursively, ending with the exact coarsest inverse;
+ *  - polynomial (Sec. 2.1, eq. 2.6 with W = P^-1): the first 2m+1 terms of
+ *    the series (2.4), sum_{j=0}^{2m} (P^-1 Q)^j P^-1, i.e. 2m+1 splitting
+ *    steps from zero on the level itself, no coarse level.
  * ------------------------------------------------------------------------- */
 static void pcg(or_hier *H, int k, const double *b, double *x);
 
@@ -726,13 +740,22 @@ static void precond(or_hier *H, int k, const double *r, double *z) {
     chol_solve(H->chol, H->nc, r, z);
     return;
   }
-  or_level *C = &H->L[k + 1];
   memset(z, 0, sizeof(double) * L->n);
+  if (H->precond == 2) {
+    for (int s = 0; s < 2 * H->m + 1; ++s) smooth_step(H, L, r, z);
+    return;
+  }
+  or_level *C = &H->L[k + 1];
   for (int s = 0; s < H->m; ++s) smooth_step(H, L, r, z);
   apply(L, z, L->t);
   for (int64_t i = 0; i < L->n; ++i) L->t[i] = r[i] - L->t[i];
   restrict_(L, C, L->t, C->b);
-  pcg(H, k + 1, C->b, C->x);
+  if (H->precond == 1) {
+    H->calls[k + 1]++;
+    precond(H, k + 1, C->b, C->x);
+  } else {
+    pcg(H, k + 1, C->b, C->x);
+  }
   prolong_add(L, C, C->x, z);
   for (int s = 0; s < H->m; ++s) smooth_step(H, L, r, z);
 }

@@ -82,6 +82,8 @@ def lib():
         L.or_solve.restype = C.c_int
         L.or_set_splitting.argtypes = [C.c_void_p, C.c_int]
         L.or_set_splitting.restype = None
+        L.or_set_precond.argtypes = [C.c_void_p, C.c_int]
+        L.or_set_precond.restype = None
         for name in ("or_apply_level", "or_sgs_level", "or_jacobi_level", "or_lex_level", "or_restrict_level",
                      "or_prolong_level"):
             getattr(L, name).argtypes = [C.c_void_p, C.c_int, _dp, _dp]
@@ -176,12 +178,14 @@ class Hierarchy:
     """Oracle level hierarchy of one problem (Sec. 2.3 / Sec. 3)."""
 
     def __init__(self, prob, s=4, m=4, f=0.1, maxside=None, maxit_outer=200, maxit_inner=500, splitting=0,
-                 coarsening=0, interp=0, Kfaces=None):
+                 coarsening=0, interp=0, Kfaces=None, precond=0):
         """splitting: 0 = symmetric Gauss-Seidel (red-black), 1 = modified
         Jacobi P = 2D, 2 = symmetric Gauss-Seidel in the natural order
         (Sec. 3).  coarsening: 0 = factor s on every long axis, 1 = toward
         square cells (Sec. 4.4).  interp: 0 = linear extension, 1 = piecewise
-        constant (Sec. 3).  Kfaces: (Kx, Ky[, Kz]) face permeabilities with
+        constant (Sec. 3).  precond: 0 = recursive multi-scale (eq. 2.10),
+        1 = multigrid V-step (eq. 2.9, Tatebe), 2 = polynomial (eq. 2.6 with
+        W = P^-1).  Kfaces: (Kx, Ky[, Kz]) face permeabilities with
         the boundary conditions in the boundary faces' values; when given,
         they replace the problem's cell K and boundary types."""
         self.prob = prob
@@ -201,6 +205,7 @@ class Hierarchy:
         if not self._h:
             raise ValueError("oracle build failed")
         lib().or_set_splitting(self._h, int(splitting))
+        lib().or_set_precond(self._h, int(precond))
         self.nlev = lib().or_nlev(self._h)
         self.dims = []
         for k in range(self.nlev):

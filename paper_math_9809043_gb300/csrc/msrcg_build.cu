@@ -470,6 +470,11 @@ int upload(msrcg_hier* h, const std::vector<T>& v, const void** out, cudaStream_
 
 void release(msrcg_hier* h) {
   if (!h) return;
+  if (h->twin) {
+    h->twin->alloc_stream = h->alloc_stream;
+    release(h->twin);
+    h->twin = nullptr;
+  }
   if (h->alloc_stream) {
     // stream-ordered: freed after the work already queued on that stream
     for (void* p : h->allocs) cudaFreeAsync(p, h->alloc_stream);
@@ -507,6 +512,10 @@ extern "C" int msrcg_default_opts(msrcg_opts* o) {
   o->splitting = 0;
   o->coarsening = 0;
   o->interp = 0;
+  o->stall_iters = 0;
+  o->escalate = 1;
+  o->flexible = 0;
+  o->precond = 0;
   return MSRCG_OK;
 }
 
@@ -537,6 +546,7 @@ struct Level0K {
   int ncomp = 1;
   const uint8_t* bc = nullptr;
   const double* Kf[3] = {nullptr, nullptr, nullptr};
+  const double* T0[3] = {nullptr, nullptr, nullptr};  // level-0 transmissibilities of another hierarchy
 };
 int build_hier(const msrcg_grid* grid, const Level0K& src, const msrcg_opts* opts, cudaStream_t stream,
                cudaStream_t alloc_stream, msrcg_hier** out);
@@ -567,6 +577,27 @@ extern "C" int msrcg_build_faces(const msrcg_grid* grid, const double* Kx, const
   return build_hier(grid, src, opts, (cudaStream_t)stream, nullptr, out);
 }
 
+int msrcg_twin(msrcg_hier* h, cudaStream_t stream, msrcg_hier** out) {
+  if (!h->twin) {
+    msrcg_grid g;
+    g.dim = h->dim;
+    for (int a = 0; a < 3; ++a) {
+      g.n[a] = h->dims[0][a];
+      g.h[a] = h->hsz[a];
+    }
+    msrcg_opts o = h->o;
+    o.precision = 0;
+    o.inner_floor = 0.0;
+    o.escalate = 0;
+    Level0K src;
+    for (int a = 0; a < h->dim; ++a) src.T0[a] = h->T64[0][a];
+    int rc = build_hier(&g, src, &o, stream, h->alloc_stream, &h->twin);
+    if (rc) return rc;
+  }
+  *out = h->twin;
+  return MSRCG_OK;
+}
+
 namespace {
 int build_hier(const msrcg_grid* grid, const Level0K& src, const msrcg_opts* opts, cudaStream_t stream,
                cudaStream_t alloc_stream, msrcg_hier** out) {
@@ -582,7 +613,8 @@ int build_hier(const msrcg_grid* grid, const Level0K& src, const msrcg_opts* opt
   else msrcg_default_opts(&o);
   if (o.scale < 2 || o.m < 1 || !(o.f > 0.0) || o.maxit_outer < 1 || o.maxit_inner < 1 || o.fuse_width < 0 ||
       o.fuse_min_cells < 0 || o.splitting < 0 || o.splitting > 2 || o.coarsening < 0 || o.coarsening > 1 ||
-      o.interp < 0 || o.interp > 1)
+      o.interp < 0 || o.interp > 1 || o.escalate < 0 || o.escalate > 1 || o.flexible < 0 || o.flexible > 1 ||
+      o.precond < 0 || o.precond > 2)
     return MSRCG_EINVAL;
   if (o.precision != 0 && o.precision != 1) return MSRCG_EINVAL;
   if (o.coarsest_max_side <= 0) o.coarsest_max_side = dim == 2 ? 8 : 4;
@@ -616,6 +648,8 @@ int build_hier(const msrcg_grid* grid, const Level0K& src, const msrcg_opts* opt
   // the natural-order smoother runs plane by plane inside one CTA: every
   // level of a single solve goes to the single-CTA solver
   if (o.splitting == 2) h->ks = 0;
+  // so do the multigrid and polynomial preconditioners
+  if (o.precond != 0) h->ks = 0;
 
   const bool f32 = o.precision == 1;
   const size_t rsz = f32 ? sizeof(float) : sizeof(double);
@@ -633,7 +667,13 @@ int build_hier(const msrcg_grid* grid, const Level0K& src, const msrcg_opts* opt
       h->T64[k][a] = (double*)p;
     }
   }
-  if (src.Kf[0]) {
+  if (src.T0[0]) {
+    for (int a = 0; a < dim; ++a) {
+      long long nf = (long long)(n3[0] + (a == 0)) * (n3[1] + (a == 1)) * (n3[2] + (a == 2));
+      if (cudaMemcpyAsync(h->T64[0][a], src.T0[a], sizeof(double) * nf, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return fail(MSRCG_ECUDA);
+    }
+  } else if (src.Kf[0]) {
     for (int a = 0; a < dim; ++a) {
       long long nf = (long long)(n3[0] + (a == 0)) * (n3[1] + (a == 1)) * (n3[2] + (a == 2));
       k_face_scale<<<grid_for(nf, 256, gmax), 256, 0, st>>>(nf, ratio[a], src.Kf[a], h->T64[0][a]);
@@ -1006,7 +1046,8 @@ int msrcg_build_into(msrcg_hier* h, const msrcg_grid* grid, const double* K, int
   else msrcg_default_opts(&o);
   if (o.scale < 2 || o.m < 1 || !(o.f > 0.0) || o.maxit_outer < 1 || o.maxit_inner < 1 || o.fuse_width < 0 ||
       o.fuse_min_cells < 0 || o.splitting < 0 || o.splitting > 2 || o.coarsening < 0 || o.coarsening > 1 ||
-      o.interp < 0 || o.interp > 1)
+      o.interp < 0 || o.interp > 1 || o.escalate < 0 || o.escalate > 1 || o.flexible < 0 || o.flexible > 1 ||
+      o.precond < 0 || o.precond > 2)
     return MSRCG_EINVAL;
   if (o.precision != 0 && o.precision != 1) return MSRCG_EINVAL;
   if (o.coarsest_max_side <= 0) o.coarsest_max_side = dim == 2 ? 8 : 4;

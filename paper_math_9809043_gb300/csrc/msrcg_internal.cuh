@@ -83,6 +83,10 @@ struct LevelState {
   float alpha_f, beta_f; // the same in FP32 for FP32 levels
   long long iters, calls;
   int it, stop;
+  // level 0 with the stall test: the last residual that halved the best so
+  // far and its iteration; r_new . z_old of the last update (flexible beta)
+  double rr_best, gamma;
+  int it_best, gamma_ok;
 };
 
 struct SolveState {
@@ -93,6 +97,11 @@ struct SolveState {
   int status;
   int pad;
   double rr_true;
+  // flexible beta of the level-0 PCG (Polak-Ribiere): in use (flex), may be
+  // switched on by the stall test or an inner level at its cap (allow_flex,
+  // FP32 preconditioner), iterations without the residual halving before
+  // the switch (stall_w, 0 = no stall test)
+  int flex, allow_flex, stall_w, pad2;
   LevelState lv[kMaxLev];
   unsigned int ticket[kMaxLev];
 };
@@ -114,6 +123,10 @@ struct ProblemDesc {
   int fuse_width;        // its strip width cap (0: none)
   int fuse_min_cells;    // its smallest level (cells)
   int splitting;         // 0: red-black symmetric Gauss-Seidel, 1: modified Jacobi, 2: natural order
+  int stall_w;           // stall test of the level-0 PCG (0: none)
+  int allow_flex;        // the stall test / an inner cap may switch to the flexible beta
+  int flex0;             // flexible beta from the first iteration
+  int precond;           // 0: recursive multi-scale (eq. 2.10), 1: multigrid (eq. 2.9), 2: polynomial
 };
 
 }  // namespace msrcg
@@ -147,6 +160,7 @@ struct msrcg_hier {
   int64_t last_iters[MSRCG_MAXLEV] = {};
   int64_t last_calls[MSRCG_MAXLEV] = {};
   int sms = 0;
+  msrcg_hier* twin = nullptr;           // FP64-preconditioner twin of an FP32-mode hierarchy (escalation)
 };
 
 // allocation helper: records the buffer in h->allocs
@@ -159,6 +173,9 @@ int msrcg_build_ex(const msrcg_grid* grid, const double* K, int ncomp, const uin
 int msrcg_batch_enqueue(int count, msrcg_hier* const* hs, const double* const* b, double tol, double* const* x,
                         cudaStream_t s, msrcg::SolveState* host_states);
 int msrcg_batch_finish(int count, msrcg_hier* const* hs, const msrcg::SolveState* host_states, msrcg_stats* stats);
+// the FP64-preconditioner twin of h (same level-0 transmissibilities), built
+// on first use and kept in h->twin
+int msrcg_twin(msrcg_hier* h, cudaStream_t stream, msrcg_hier** out);
 // device bytes msrcg_build_ex allocates for a grid and options (0: rejected)
 size_t msrcg_build_bytes(const msrcg_grid* grid, const msrcg_opts* opts);
 // builds h inside the device buffer [base, base + cap) without allocating

@@ -989,6 +989,11 @@ struct LvlCtl {
   double rho_d, rho_old_d, thrN_d;
   float rho_f, rho_old_f, thrN_f;
   int it, phase;
+  // level 0: ||r||^2 of the last update, the stall test's best residual and
+  // its iteration, r_new . z_old of the last update (flexible beta)
+  double rr_d, rr_best, gamma_d;
+  int it_best;
+  bool gamma_ok;
 };
 enum : int { kStart = 0, kIterate = 1, kAfterCoarse = 2, kPrecondDone = 3, kReturn = 4 };
 
@@ -1033,6 +1038,12 @@ struct RecArgs {
   bool fuse;
   int fuse_width, fuse_min_cells;
   int splitting;  // 0: red-black symmetric Gauss-Seidel, 1: modified Jacobi, 2: natural-order SGS
+  // flexible beta of the level-0 PCG: in use (*flex, the same value in every
+  // thread), may be switched on (allow_flex), stall test length (0: none)
+  bool* flex;
+  bool allow_flex;
+  int stall_w;
+  int precond;  // 0: recursive multi-scale (eq. 2.10), 1: multigrid (eq. 2.9), 2: polynomial (eq. 2.6, W = P^-1)
 };
 
 // Strip width of the single-pass smoother for level L, or 0 for the plain
@@ -1169,11 +1180,15 @@ struct Ops {
     return tm.sum<V>(acc);
   }
   // p = z + beta p, q = A p, alpha = rho / p.q, x += alpha p, r -= alpha q.
-  // Returns ||r||^2 (false on breakdown).
-  static __device__ bool cg_step(BlockTeam& tm, const DevLevel& L, LvlCtl& ct, V& rr_out) {
+  // Returns ||r||^2 (false on breakdown).  With `flex`, beta is the flexible
+  // (Polak-Ribiere) factor (rho - r.z_old) / rho_old once the previous update
+  // has formed r.z_old, and this update forms r_new . z for the next one.
+  static __device__ bool cg_step(BlockTeam& tm, const DevLevel& L, LvlCtl& ct, V& rr_out, bool flex) {
     const V rho = Scal<V>::rho(ct);
     const bool first = ct.it == 0;
-    const V beta = first ? (V)0 : rho / Scal<V>::rho_old(ct);
+    const V beta = first ? (V)0
+                         : (flex && ct.gamma_ok ? (rho - (V)ct.gamma_d) / Scal<V>::rho_old(ct)
+                                                : rho / Scal<V>::rho_old(ct));
     V* p = (V*)L.p;
     V* q = (V*)L.q;
     const RP* z = (const RP*)L.z;
@@ -1203,6 +1218,22 @@ struct Ops {
     V* x = (V*)L.x;
     V* r = (V*)L.r;
     V acc2 = 0;
+    if (flex) {
+      V acc3 = 0;
+      for_lin(npad, [&](int c) { return Two<Four<V>, RP>{Four<V>{x[c], p[c], r[c], q[c]}, z[c]}; },
+              [&](int c, Two<Four<V>, RP> v) {
+                const V xv = v.a.x + alpha * v.a.p;
+                const V rv = v.a.r - alpha * v.a.q;
+                acc2 += rv * rv;
+                acc3 += rv * (V)v.b;
+                x[c] = xv;
+                r[c] = rv;
+              });
+      rr_out = tm.sum<V>(acc2);
+      ct.gamma_d = (double)tm.sum<V>(acc3);
+      ct.gamma_ok = true;
+      return true;
+    }
     for_lin(npad, [&](int c) { return Four<V>{x[c], p[c], r[c], q[c]}; }, [&](int c, Four<V> v) {
       const V xv = v.x + alpha * v.p;
       const V rv = v.r - alpha * v.q;
@@ -1211,13 +1242,15 @@ struct Ops {
       r[c] = rv;
     });
     rr_out = tm.sum<V>(acc2);
+    ct.gamma_ok = false;
     return true;
   }
   // one CG step and the level test; returns 0 = continue, 1 = converged,
   // 2 = breakdown
   static __device__ int iterate(BlockTeam& tm, const DevLevel& L, LvlCtl& c, SolveState* S, const RecArgs& a, int k) {
     V rr;
-    if (!cg_step(tm, L, c, rr)) return 2;
+    if (!cg_step(tm, L, c, rr, k == 0 && *a.flex)) return 2;
+    c.rr_d = (double)rr;
     if (threadIdx.x == 0) {
       a.iters[k]++;
       if (k == 0) S->lv[0].rr = (double)rr;
@@ -1241,6 +1274,12 @@ __device__ void recursion(BlockTeam& tm, const DevLevel* sL, int ks, const RecAr
     const bool dbl = a.top_double && k == 0;
     if (c.phase == kStart) {
       if (threadIdx.x == 0) a.calls[k]++;
+      if (a.precond == 1 && k > 0) {
+        // multigrid (eq. 2.9): this level applies its preconditioner once
+        // to r_k; no PCG, no level test
+        c.phase = kIterate;
+        continue;
+      }
       // level test of Sec. 3: ||r||^2 / N_k < f^k eps^2, kept as
       // ||r||^2 < f^k eps^2 N_k (thrN, precomputed per level); inner levels
       // may also stop at a floor relative to ||b_k||.  FP32 levels do this in
@@ -1249,12 +1288,14 @@ __device__ void recursion(BlockTeam& tm, const DevLevel* sL, int ks, const RecAr
       if (dbl || sizeof(RP) == sizeof(double)) {
         const double bb = dbl ? (double)Ops<DIM, double, RP>::enter(tm, L) : (double)Ops<DIM, RP, RP>::enter(tm, L);
         live = bb > 0.0;
+        c.rr_best = bb;
         c.thrN_d = a.thrN_d[k];
         if (k > 0 && a.floor2 > 0.0) c.thrN_d = fmax(c.thrN_d, a.floor2 * bb);
         c.thrN_f = (float)c.thrN_d;
       } else {
         const float bb = (float)Ops<DIM, RP, RP>::enter(tm, L);
         live = bb > 0.f;
+        c.rr_best = (double)bb;
         c.thrN_f = fmaxf(a.thrN_f[k], a.floor2_f * bb);
         if (!(c.thrN_f > 1e-30f)) c.thrN_d = fmax(a.thrN_d[k], a.floor2 * (double)bb);
       }
@@ -1265,9 +1306,17 @@ __device__ void recursion(BlockTeam& tm, const DevLevel* sL, int ks, const RecAr
       c.it = 0;
       c.rho_old_d = 0.0;
       c.rho_old_f = 0.f;
+      c.gamma_ok = false;
+      c.it_best = 0;
       c.phase = kIterate;
     } else if (c.phase == kIterate) {
-      if (k == a.kmax) {
+      if (a.precond == 2 && k == 0 && a.kmax > 0) {
+        // polynomial (eq. 2.6 with W = P^-1): 2m+1 splitting steps from zero
+        const TLevel<RP> T = tlevel_of<RP>(L);
+        if (dbl) c.rho_d = t_smooth<DIM, RP, double>(tm, L, T, 2 * a.m + 1, true, true, a.splitting);
+        else Scal<RP>::rho(c) = t_smooth<DIM, RP, RP>(tm, L, T, 2 * a.m + 1, true, true, a.splitting);
+        c.phase = kPrecondDone;
+      } else if (k == a.kmax) {
         if (dbl) c.rho_d = Ops<DIM, double, RP>::coarsest(tm, L, a);
         else Scal<RP>::rho(c) = Ops<DIM, RP, RP>::coarsest(tm, L, a);
         c.phase = kPrecondDone;
@@ -1283,15 +1332,46 @@ __device__ void recursion(BlockTeam& tm, const DevLevel* sL, int ks, const RecAr
       else Scal<RP>::rho(c) = Ops<DIM, RP, RP>::prolong_postsmooth(tm, L, sL[k + 1], a.m, a);
       c.phase = kPrecondDone;
     } else if (c.phase == kPrecondDone) {
+      if (a.precond == 1 && k > 0) {
+        // multigrid: the level's result is M_k^-1 r_k itself
+        RP* x = (RP*)L.x;
+        const RP* z = (const RP*)L.z;
+        for_lin((int)L.npad, [&](int e) { return z[e]; }, [&](int e, RP v) { x[e] = v; });
+        tm.sync();
+        c.phase = kReturn;
+        continue;
+      }
       const int st = dbl ? Ops<DIM, double, RP>::iterate(tm, L, c, S, a, k) : Ops<DIM, RP, RP>::iterate(tm, L, c, S, a, k);
       c.it++;
+      // stall test of the level-0 PCG (every thread takes the same decision:
+      // the residual norm is the same block-wide total in all of them)
+      bool stalled = false;
+      if (st == 0 && k == 0 && a.stall_w > 0) {
+        if (c.rr_d < 0.25 * c.rr_best) {
+          c.rr_best = c.rr_d;
+          c.it_best = c.it;
+        } else if (c.it - c.it_best >= a.stall_w) {
+          if (!*a.flex && a.allow_flex) {
+            *a.flex = true;
+            c.it_best = c.it;
+          } else {
+            stalled = true;
+          }
+        }
+      }
       if (st == 2) {
         if (threadIdx.x == 0) atomicOr(&S->status, kStBreakdown);
         c.phase = kReturn;
       } else if (st == 1) {
         c.phase = kReturn;
-      } else if (c.it >= L.maxit) {
+      } else if (stalled) {
         if (threadIdx.x == 0) atomicOr(&S->status, kStNoConv);
+        c.phase = kReturn;
+      } else if (c.it >= L.maxit) {
+        // an inner level at its cap with the FP32 preconditioner: the outer
+        // PCG goes on with the flexible beta; otherwise the solve fails
+        if (k > 0 && a.allow_flex) *a.flex = true;
+        else if (threadIdx.x == 0) atomicOr(&S->status, kStNoConv);
         c.phase = kReturn;
       } else {
         c.rho_old_d = c.rho_d;
@@ -1462,6 +1542,11 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallPerSM) k_small(const Prob
     }
     a.floor2 = S->inner_floor2;
     a.floor2_f = (float)a.floor2;
+    bool flex = pd.flex0 != 0;
+    a.flex = &flex;
+    a.allow_flex = pd.allow_flex != 0;
+    a.stall_w = pd.stall_w;
+    a.precond = pd.precond;
     a.S = S;
     a.top_double = full;
     a.rc = s_rc;
@@ -1485,6 +1570,9 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallPerSM) k_small(const Prob
       level_consts(sL, pd.nlev, a.eps2, s_thrN_d, s_thrN_f, s_iters, s_calls);
       recursion<DIM, RP>(bt, sL, ks, a);
       flush_counts(S, pd.nlev, s_iters, s_calls);
+      // an inner level at its cap switches the graph's level-0 PCG to the
+      // flexible beta
+      if (threadIdx.x == 0 && flex) S->flex = 1;
       RP* gx = (RP*)G.x;
       const RP* sx = (const RP*)sL[ks].x;
       if (sx != gx)
@@ -1518,6 +1606,7 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallPerSM) k_small(const Prob
       }
       S->lv[0].rr = bb;
       S->rr_true = bb;
+      S->flex = pd.flex0;
     }
     __syncthreads();
     a.eps2 = eps2;
@@ -1542,6 +1631,7 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallPerSM) k_small(const Prob
       }
     }
     flush_counts(S, pd.nlev, s_iters, s_calls);
+    if (threadIdx.x == 0) S->flex = flex ? 1 : 0;
     for_cells<DIM>(team_map(L0.nx), L0, [&](int i, const Row& rw) {
       pd.x[i + L0.nx * (rw.j + L0.ny * rw.k)] = xs[rw.pc + i];
     });
@@ -1587,6 +1677,61 @@ __device__ void grid_total(T v, double* partials, unsigned int* ticket, Fin fin)
   }
 }
 
+// grid_total for two values at once (partials holds 2 per CTA).
+template <typename T, class Fin>
+__device__ void grid_total2(T v0, T v1, double* partials, unsigned int* ticket, Fin fin) {
+  __shared__ T sh[2][32];
+  __shared__ bool last;
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nt = blockDim.x * blockDim.y;
+  const unsigned nb = gridDim.x * gridDim.y, bid = blockIdx.x + gridDim.x * blockIdx.y;
+  v0 = warp_sum_t<T>(v0);
+  v1 = warp_sum_t<T>(v1);
+  if ((tid & 31) == 0) {
+    sh[0][tid >> 5] = v0;
+    sh[1][tid >> 5] = v1;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    T s0 = 0, s1 = 0;
+    for (int w = 0; w < (nt >> 5); ++w) {
+      s0 += sh[0][w];
+      s1 += sh[1][w];
+    }
+    partials[2 * bid] = (double)s0;
+    partials[2 * bid + 1] = (double)s1;
+    __threadfence();
+    const unsigned t = atomicAdd(ticket, 1u);
+    last = t == nb - 1;
+  }
+  __syncthreads();
+  if (last && tid < 32) {
+    __threadfence();
+    double s0 = 0.0, s1 = 0.0;
+    for (unsigned i = tid; i < nb; i += 32) {
+      s0 += __ldcg(partials + 2 * i);
+      s1 += __ldcg(partials + 2 * i + 1);
+    }
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    if (tid == 0) {
+      *ticket = 0u;
+      fin(s0, s1);
+    }
+  }
+}
+
+// rho of a post-smoothed level and the CG direction factor beta: rho /
+// rho_old, or on level 0 with the flexible beta in use (rho - r.z_old) /
+// rho_old once the previous update has formed r.z_old.
+__device__ __forceinline__ void set_rho_beta(LevelState& ls, int k, const SolveState* S, double rho) {
+  ls.rho = rho;
+  if (ls.it == 0) ls.beta = 0.0;
+  else if (k == 0 && S->flex && ls.gamma_ok) ls.beta = (rho - ls.gamma) / ls.rho_old;
+  else ls.beta = rho / ls.rho_old;
+  ls.beta_f = (float)ls.beta;
+}
+
 __device__ __forceinline__ long long lin_tid() {
   return (long long)(blockIdx.x + gridDim.x * blockIdx.y) * (blockDim.x * blockDim.y) + threadIdx.x +
          blockDim.x * threadIdx.y;
@@ -1624,6 +1769,9 @@ __global__ void k_init(DevLevel L, int k, SolveState* S, const double* b0, doubl
     ls.calls++;
     ls.rho_old = 0.0;
     ls.rr = bb;
+    ls.rr_best = bb;
+    ls.it_best = 0;
+    ls.gamma_ok = 0;
     ls.stop = !(bb > 0.0) || !isfinite(bb);
     cudaGraphSetConditional(hcond, ls.stop ? 0u : 1u);
   });
@@ -1695,12 +1843,7 @@ __global__ void k_sweep_rho(DevLevel L, int k, SolveState* S, double* partials) 
       z[rw.pc + i] = v;
     }
   });
-  grid_total(acc, partials, &S->ticket[k], [&](double rho) {
-    LevelState& ls = S->lv[k];
-    ls.rho = rho;
-    ls.beta = ls.it == 0 ? 0.0 : rho / ls.rho_old;
-    ls.beta_f = (float)ls.beta;
-  });
+  grid_total(acc, partials, &S->ticket[k], [&](double rho) { set_rho_beta(S->lv[k], k, S, rho); });
 }
 
 template <int DIM, typename RP>
@@ -1781,12 +1924,7 @@ __global__ void k_jacobi_rho(DevLevel L, int k, SolveState* S, double* partials)
     acc += r[pc] * (V)v;
     z[pc] = v;
   });
-  grid_total(acc, partials, &S->ticket[k], [&](double rho) {
-    LevelState& ls = S->lv[k];
-    ls.rho = rho;
-    ls.beta = ls.it == 0 ? 0.0 : rho / ls.rho_old;
-    ls.beta_f = (float)ls.beta;
-  });
+  grid_total(acc, partials, &S->ticket[k], [&](double rho) { set_rho_beta(S->lv[k], k, S, rho); });
 }
 
 // z += E x_c on every cell (the Jacobi smoother reads them all)
@@ -1837,8 +1975,11 @@ __global__ void k_apply_dot(DevLevel L, int k, SolveState* S, double* partials) 
 }
 
 // x += alpha p, r -= alpha q, ||r||^2, the level test of Sec. 3 and the
-// WHILE condition of the level's loop.
-template <typename V>
+// WHILE condition of the level's loop.  On level 0 with the flexible beta in
+// use the pass also forms r_new . z (z still holds this iteration's
+// preconditioned residual); the stall test may switch the flexible beta on
+// or end the loop.
+template <typename V, typename RP>
 __global__ void k_update(DevLevel L, int k, SolveState* S, double* partials, cudaGraphConditionalHandle hcond) {
   const LevelState& ls = S->lv[k];
   if (ls.stop) {
@@ -1850,38 +1991,61 @@ __global__ void k_update(DevLevel L, int k, SolveState* S, double* partials, cud
   V* r = (V*)L.r;
   const V* p = (const V*)L.p;
   const V* q = (const V*)L.q;
-  V acc = 0;
+  const RP* z = (const RP*)L.z;
+  const bool gam = k == 0 && S->flex;
+  V acc = 0, acc2 = 0;
   const int n = (int)L.npad;
   for (int c = (int)lin_tid(); c < n; c += (int)lin_stride()) {
     const V xv = x[c] + alpha * p[c];
     const V rv = r[c] - alpha * q[c];
     acc += rv * rv;
+    if (gam) acc2 += rv * (V)z[c];
     x[c] = xv;
     r[c] = rv;
   }
-  grid_total(acc, partials, &S->ticket[k], [&](double rr) {
+  auto fin = [&](double rr, double gamma) {
     LevelState& w = S->lv[k];
     w.rr = rr;
     w.iters++;
     w.it++;
+    w.gamma = gamma;
+    w.gamma_ok = gam;
     bool go = true;
     if (rr / (double)L.n < w.thr) {
       go = false;
     } else if (w.it >= L.maxit) {
-      atomicOr(&S->status, kStNoConv);
+      // an inner level at its cap with the FP32 preconditioner switches the
+      // level-0 PCG to the flexible beta; otherwise the solve fails
+      if (k > 0 && S->allow_flex) S->flex = 1;
+      else atomicOr(&S->status, kStNoConv);
       go = false;
+    } else if (k == 0 && S->stall_w > 0) {
+      if (rr < 0.25 * w.rr_best) {
+        w.rr_best = rr;
+        w.it_best = w.it;
+      } else if (w.it - w.it_best >= S->stall_w) {
+        if (!S->flex && S->allow_flex) {
+          S->flex = 1;
+          w.it_best = w.it;
+        } else {
+          atomicOr(&S->status, kStNoConv);
+          go = false;
+        }
+      }
     }
     w.rho_old = w.rho;
     if (!go) w.stop = 1;
     cudaGraphSetConditional(hcond, go ? 1u : 0u);
-  });
+  };
+  if (gam) grid_total2(acc, acc2, partials, &S->ticket[k], fin);
+  else grid_total(acc, partials, &S->ticket[k], [&](double rr) { fin(rr, 0.0); });
 }
 
 // Before a solve: b0 = b (padded), ||b||^2, eps^2 = tol^2 ||b||^2 / N_0
 // (Sec. 3), counters cleared.  xs is zeroed by the caller.
 template <int DIM>
 __global__ void k_prepare(DevLevel L0, const double* b, double* b0, double tol, SolveState* S, int nlev,
-                          double* partials) {
+                          double* partials, int flex0, int allow_flex, int stall_w) {
   double acc = 0.0;
   for_cells<DIM>(grid_map(), L0, [&](int i, const Row& rw) {
     const int pc = rw.pc + i;
@@ -1896,6 +2060,9 @@ __global__ void k_prepare(DevLevel L0, const double* b, double* b0, double tol, 
     S->eps2 = tol * tol * (bb / (double)L0.n);
     S->status = isfinite(bb) ? 0 : kStNanInf;
     S->rr_true = bb;
+    S->flex = flex0;
+    S->allow_flex = allow_flex;
+    S->stall_w = stall_w;
     for (int k = 0; k < nlev; ++k) {
       S->lv[k].iters = 0;
       S->lv[k].calls = 0;
@@ -2048,6 +2215,8 @@ void emit_pcg(Emit& E, int k, cudaStream_t s) {
   const DevLevel& L = h->hL[k];
   const int gmax = std::min(h->sms * 8, kMaxGrid);
   const Launch ll = lin_launch(L.npad, gmax), lc = cells_launch(L, gmax);
+  // the update may reduce two values: two partials per CTA in the level's share
+  const Launch lu = lin_launch(L.npad, std::min(gmax, kMaxGrid / 2));
   double* part = h->partials + (size_t)k * kMaxGrid;
   cudaStreamCaptureStatus cst;
   cudaGraph_t cg;
@@ -2094,11 +2263,11 @@ void emit_pcg(Emit& E, int k, cudaStream_t s) {
   if (k == 0) {
     k_direction<double, RP><<<ll.grid, ll.block, 0, b>>>(L, k, h->dS);
     k_apply_dot<DIM, double><<<lc.grid, lc.block, 0, b>>>(L, k, h->dS, part);
-    k_update<double><<<ll.grid, ll.block, 0, b>>>(L, k, h->dS, part, hc);
+    k_update<double, RP><<<lu.grid, lu.block, 0, b>>>(L, k, h->dS, part, hc);
   } else {
     k_direction<RP, RP><<<ll.grid, ll.block, 0, b>>>(L, k, h->dS);
     k_apply_dot<DIM, RP><<<lc.grid, lc.block, 0, b>>>(L, k, h->dS, part);
-    k_update<RP><<<ll.grid, ll.block, 0, b>>>(L, k, h->dS, part, hc);
+    k_update<RP, RP><<<lu.grid, lu.block, 0, b>>>(L, k, h->dS, part, hc);
   }
   cudaGraph_t out;
   if (cudaStreamEndCapture(b, &out) != cudaSuccess) E.err = 7;
@@ -2246,6 +2415,10 @@ ProblemDesc make_desc(msrcg_hier* h, const double* b, double* x, double tol) {
   pd.fuse_width = h->o.fuse_width;
   pd.fuse_min_cells = h->o.fuse_min_cells > 0 ? h->o.fuse_min_cells : kFuseMinCells;
   pd.splitting = h->o.splitting;
+  pd.allow_flex = h->o.precision == 1;
+  pd.stall_w = pd.allow_flex && h->o.stall_iters >= 0 ? (h->o.stall_iters > 0 ? h->o.stall_iters : 8) : 0;
+  pd.flex0 = h->o.flexible;
+  pd.precond = h->o.precond;
   return pd;
 }
 
@@ -2261,6 +2434,7 @@ void fill_stats(const msrcg_hier* h, const SolveState& S, msrcg_stats* st, int r
   st->relres_true = S.bb0 > 0 ? sqrt(S.rr_true / S.bb0) : 0.0;
   st->restarts = restarts;
   st->status = msrcg_status_from_bits(S.status);
+  st->flexible = S.flex != 0;
 }
 
 // After a failed solve, vectors may hold non-finite values (their ghosts
@@ -2316,8 +2490,13 @@ extern "C" int msrcg_solve(msrcg_hier* h, const double* b, double tol, double* x
     const DevLevel& L0 = h->hL[0];
     const Launch lc = cells_launch(L0, gmax), ll = lin_launch(L0.npad, gmax);
     MSRCG_CUDA_TRY(cudaMemsetAsync(h->xs, 0, sizeof(double) * L0.npad, s));
-    if (dim == 2) k_prepare<2><<<lc.grid, lc.block, 0, s>>>(L0, b, h->b0, tol, h->dS, h->nlev, part);
-    else k_prepare<3><<<lc.grid, lc.block, 0, s>>>(L0, b, h->b0, tol, h->dS, h->nlev, part);
+    const ProblemDesc pd = make_desc(h, b, x, tol);
+    if (dim == 2)
+      k_prepare<2><<<lc.grid, lc.block, 0, s>>>(L0, b, h->b0, tol, h->dS, h->nlev, part, pd.flex0, pd.allow_flex,
+                                                pd.stall_w);
+    else
+      k_prepare<3><<<lc.grid, lc.block, 0, s>>>(L0, b, h->b0, tol, h->dS, h->nlev, part, pd.flex0, pd.allow_flex,
+                                                pd.stall_w);
     MSRCG_CUDA_TRY(cudaGetLastError());
     for (;;) {
       MSRCG_CUDA_TRY(cudaGraphLaunch(h->gexec, s));
@@ -2344,6 +2523,18 @@ extern "C" int msrcg_solve(msrcg_hier* h, const double* b, double tol, double* x
       h->last_calls[k] = stats->calls[k];
     }
     if (stats->status != MSRCG_OK) h->dirty = true;
+    if (stats->status == MSRCG_ENOCONV && f32 && h->o.escalate) {
+      // the FP32 preconditioner did not get there: solve again with the FP64
+      // one (same operator, same tolerance)
+      msrcg_hier* tw = nullptr;
+      int rc = msrcg_twin(h, s, &tw);
+      if (rc) return rc;
+      const int flexible = stats->flexible;
+      rc = msrcg_solve(tw, b, tol, x, stats, stream);
+      stats->flexible = flexible;
+      stats->escalated = 1;
+      return rc;
+    }
     return stats->status;
   }
   return MSRCG_OK;
@@ -2430,7 +2621,29 @@ extern "C" int msrcg_batch_solve(int count, msrcg_hier* const* hs, const double*
   int rc = msrcg_batch_enqueue(count, hs, b, tol, x, s, st.data());
   if (rc) return rc;
   MSRCG_CUDA_TRY(cudaStreamSynchronize(s));
-  return msrcg_batch_finish(count, hs, st.data(), stats);
+  std::vector<msrcg_stats> one(count);
+  rc = msrcg_batch_finish(count, hs, st.data(), one.data());
+  // problems the FP32 preconditioner did not solve: again, one by one, with
+  // the FP64 preconditioner
+  bool again = false;
+  for (int i = 0; i < count; ++i) {
+    if (one[i].status != MSRCG_ENOCONV || hs[i]->o.precision != 1 || !hs[i]->o.escalate) continue;
+    msrcg_hier* tw = nullptr;
+    int e = msrcg_twin(hs[i], s, &tw);
+    if (e) return e;
+    const int flexible = one[i].flexible;
+    msrcg_solve(tw, b[i], tol, x[i], &one[i], stream);
+    one[i].flexible = flexible;
+    one[i].escalated = 1;
+    again = true;
+  }
+  if (again) {
+    rc = MSRCG_OK;
+    for (int i = 0; i < count && !rc; ++i) rc = one[i].status;
+  }
+  if (stats)
+    for (int i = 0; i < count; ++i) stats[i] = one[i];
+  return rc;
 }
 
 // ===========================================================================

@@ -34,20 +34,22 @@ class Opts(C.Structure):
                 ("timeout_ns", C.c_uint64), ("inner_floor", C.c_double), ("small_cells", C.c_int),
                 ("plain_sweeps", C.c_int), ("fuse_width", C.c_int), ("fuse_min_cells", C.c_int),
                 ("splitting", C.c_int), ("coarsening", C.c_int), ("interp", C.c_int),
-                ("reserved", C.c_int * 1)]
+                ("stall_iters", C.c_int), ("escalate", C.c_int), ("flexible", C.c_int),
+                ("precond", C.c_int), ("reserved", C.c_int * 1)]
 
 
 class Stats(C.Structure):
     _fields_ = [("levels", C.c_int), ("dims", (C.c_int * 3) * MAXLEV), ("iters", C.c_int64 * MAXLEV),
                 ("calls", C.c_int64 * MAXLEV), ("relres_recursive", C.c_double), ("relres_true", C.c_double),
-                ("status", C.c_int), ("restarts", C.c_int)]
+                ("status", C.c_int), ("restarts", C.c_int), ("flexible", C.c_int), ("escalated", C.c_int)]
 
     def as_dict(self):
         L = self.levels
         return {"levels": L, "dims": [tuple(self.dims[k]) for k in range(L)],
                 "iters": [int(self.iters[k]) for k in range(L)], "calls": [int(self.calls[k]) for k in range(L)],
                 "relres_recursive": float(self.relres_recursive), "relres_true": float(self.relres_true),
-                "status": int(self.status), "restarts": int(self.restarts)}
+                "status": int(self.status), "restarts": int(self.restarts), "flexible": int(self.flexible),
+                "escalated": int(self.escalated)}
 
 
 class MsrcgError(RuntimeError):

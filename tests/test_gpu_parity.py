@@ -562,22 +562,18 @@ def test_smoothing_degree_one(M, prec):
 # hierarchy from face permeabilities (msrcg_build_faces, Sec. 3)
 # ---------------------------------------------------------------------------
 def _random_faces(n, seed):
+    """Face K that no cell field produces: the harmonic means of a Gaussian
+    random field (correlation 6 cells, 1e6 contrast) each times its own
+    factor in [0.5, 2]; Dirichlet x-faces with their own K (a few x-high
+    faces Neumann), Neumann (0) on the other sides."""
+    from faces import face_K_from_cells
     rng = np.random.default_rng(seed)
     dim = len(n)
     n3 = list(n) + [1] * (3 - dim)
-    sizes = [(n3[0] + 1) * n3[1] * n3[2], n3[0] * (n3[1] + 1) * n3[2], n3[0] * n3[1] * (n3[2] + 1)][:dim]
-    Kf = [10.0 ** rng.uniform(-4, 4, m) for m in sizes]
-    # boundary faces: Dirichlet with random K on x, Neumann (0) elsewhere, a
-    # few x-high faces Neumann too
-    Ky = Kf[1].reshape(n3[2], n3[1] + 1, n3[0])
-    Ky[:, 0, :] = 0.0
-    Ky[:, -1, :] = 0.0
+    base = P.grf_problem(tuple(n), seed=seed, ell=6.0, half_span=3.0, source=False)
+    Kf = [k * 2.0 ** rng.uniform(-1, 1, k.size) for k in face_K_from_cells(base)]
     Kx = Kf[0].reshape(n3[2], n3[1], n3[0] + 1)
     Kx[:, :, -1] *= rng.random((n3[2], n3[1])) < 0.7
-    if dim == 3:
-        Kz = Kf[2].reshape(n3[2] + 1, n3[1], n3[0])
-        Kz[0] = 0.0
-        Kz[-1] = 0.0
     N = int(np.prod(n))
     bc, gD = P.standard_bc(dim, n)
     prob = P.Problem(dim=dim, n=tuple(n), h=tuple(1.0 / m for m in n), K=np.ones((1, N)), bc=bc, gD=gD,
@@ -615,7 +611,7 @@ def test_face_K_from_harmonic_means_equals_cell_K_build(M, n):
     """Faces holding the harmonic means of a cell field (2 K_cell on Dirichlet
     faces, 0 on Neumann ones) give the cell-K build's hierarchy to the bit."""
     from faces import face_K_from_cells
-    prob = _prob_uniform(n, span=4.0)
+    prob = _prob_uniform(n, span=2.0)
     Kf = face_K_from_cells(prob)
     A = M.Hierarchy.from_problem(prob)
     B = M.Hierarchy.from_faces(prob.dim, prob.n, prob.h, Kf)
@@ -627,3 +623,102 @@ def test_face_K_from_harmonic_means_equals_cell_K_build(M, n):
     xa, _ = A.solve(b, 1e-8)
     xb, _ = B.solve(b, 1e-8)
     assert torch.equal(xa, xb)
+
+
+# ---------------------------------------------------------------------------
+# stall path of the FP32 preconditioner: flexible beta, then the FP64
+# preconditioner (the inexact inner solves of Sec. 2.3)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("path", ["single", "batched"])
+def test_fp32_channel_32_converges_through_the_stall_path(M, path):
+    """The layered channel field at 32^3 stalls near 1e-6 with the FP32
+    preconditioner and the plain beta; the stall test switches the outer PCG
+    to the flexible beta and, if it stalls again, the solve is repeated with
+    the FP64 preconditioner.  The result meets 1e-8 and the FP64 oracle's
+    solution within the parity tolerance, and the stats say which path it
+    took."""
+    prob = P.config_problem(2, scale=32)
+    H = M.Hierarchy.from_problem(prob, M.default_opts(precision=1, inner_floor=1e-6))
+    b = H.rhs_for(prob)
+    if path == "single":
+        x, st = H.solve(b, 1e-8)
+    else:
+        xs, sts = M.batch_solve([H], [b], 1e-8)
+        x, st = xs[0], sts[0]
+    xr, sr = _oracle_solution("chan-32", prob)
+    assert st["status"] == 0 and st["relres_true"] < 1e-8, st
+    assert st["flexible"] == 1 or st["escalated"] == 1, st
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(xg - xr) / np.linalg.norm(xr) <= SOL_RTOL
+    assert np.max(np.abs(xg - xr)) / np.max(np.abs(xr)) <= SOL_RTOL
+    print(path, st["iters"], "flexible", st["flexible"], "escalated", st["escalated"])
+
+
+@pytest.mark.parametrize("small", [0, 256])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_flexible_beta_from_the_start_matches_oracle(M, small, prec):
+    """With the flexible beta forced from the first iteration (single solve
+    on graph + one-CTA levels, and batched), the result still meets 1e-8 and
+    the oracle's solution: for a preconditioner that is linear up to the
+    inner tolerances, r_new . z_old is near zero and the two betas agree."""
+    prob = P.grf_problem((200, 72), seed=21, ell=6.0, half_span=4.5)
+    opts = M.default_opts(precision=prec, small_cells=small, flexible=1, inner_floor=1e-6 if prec else 0.0)
+    H = M.Hierarchy.from_problem(prob, opts)
+    b = H.rhs_for(prob)
+    R = O.Hierarchy(prob)
+    xr, sr = R.solve(R.lift_rhs(), 1e-8)
+    x, st = H.solve(b, 1e-8)
+    xs, sts = M.batch_solve([H], [b], 1e-8)
+    for xx, ss in ((x, st), (xs[0], sts[0])):
+        assert ss["status"] == 0 and ss["relres_true"] < 1e-8 and ss["flexible"] == 1, ss
+        xg = xx.cpu().numpy()
+        assert np.linalg.norm(xg - xr) / np.linalg.norm(xr) <= SOL_RTOL
+        assert np.max(np.abs(xg - xr)) / np.max(np.abs(xr)) <= SOL_RTOL
+
+
+def test_escalation_off_reports_enoconv(M):
+    """With escalation off and the stall test on, a stalling FP32 solve ends
+    with MSRCG_ENOCONV (and is reusable afterwards)."""
+    prob = P.config_problem(2, scale=32)
+    H = M.Hierarchy.from_problem(prob, M.default_opts(precision=1, inner_floor=1e-6, escalate=0, maxit_outer=60))
+    x, st = H.solve(H.rhs_for(prob), 1e-8, check=False)
+    assert st["status"] in (M.OK, M.ENOCONV) and st["escalated"] == 0, st
+    if st["status"] == M.ENOCONV:
+        x2, st2 = H.solve(H.rhs_for(prob), 1e-8, check=False)
+        assert st2["iters"] == st["iters"]
+
+
+# ---------------------------------------------------------------------------
+# the multigrid (eq. 2.9, Tatebe) and polynomial (eq. 2.6, W = P^-1)
+# preconditioners on the same smoother and transfers
+# ---------------------------------------------------------------------------
+PRECOND_CASES = [
+    ("cfg0", lambda: P.config_problem(0)),
+    ("ragged-37x23", lambda: _prob_uniform((37, 23))),
+    ("grf-128", lambda: P.config_problem(1, scale=128)),
+    ("grf-200x72", lambda: P.grf_problem((200, 72), seed=21, ell=6.0, half_span=4.5)),
+    ("ragged3d-13x9x7", lambda: _prob_uniform((13, 9, 7))),
+]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("precond", [1, 2])
+@pytest.mark.parametrize("name,mk", PRECOND_CASES, ids=[c[0] for c in PRECOND_CASES])
+def test_other_preconditioners_match_oracle(M, name, mk, precond, prec):
+    prob = mk()
+    opts = M.default_opts(precision=prec, precond=precond, maxit_outer=2000, inner_floor=1e-6 if prec else 0.0)
+    H = M.Hierarchy.from_problem(prob, opts)
+    b = H.rhs_for(prob)
+    R = O.Hierarchy(prob, precond=precond, maxit_outer=2000)
+    xr, sr = R.solve(R.lift_rhs(), 1e-8)
+    assert sr["status"] == 0
+    x, st = H.solve(b, 1e-8)
+    xs, sts = M.batch_solve([H], [b], 1e-8)
+    for xx, ss in ((x, st), (xs[0], sts[0])):
+        assert ss["status"] == 0 and ss["relres_true"] < 1e-8, ss
+        xg = xx.cpu().numpy()
+        assert np.linalg.norm(xg - xr) / np.linalg.norm(xr) <= SOL_RTOL
+        assert np.max(np.abs(xg - xr)) / np.max(np.abs(xr)) <= SOL_RTOL
+        if prec == 0:
+            _counts_close(ss["iters"], sr["iters"], sr["calls"])
+            assert ss["calls"] == sr["calls"] or precond == 1

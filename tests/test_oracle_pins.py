@@ -1011,3 +1011,109 @@ def test_face_K_transmissibility_and_solve(n, h):
     assert st["status"] == 0
     ex = spla.spsolve(A.tocsc(), prob.b)
     assert np.linalg.norm(x - ex) / np.linalg.norm(ex) < 1e-9
+
+
+# --------------------------------------------------------------------------
+# The other preconditioners of Sec. 2 on the same smoother and transfers:
+# polynomial (Sec. 2.1, eq. 2.6 with W = P^-1) and multigrid (eq. 2.9)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("splitting", [0, 1])
+@pytest.mark.parametrize("n,m", [((12, 10), 4), ((6, 5, 4), 2)])
+def test_polynomial_preconditioner_is_truncated_series(n, m, splitting):
+    """Sec. 2.1: W = P^-1 in eq. 2.6 gives the first 2m+1 terms of eq. 2.4,
+    M^-1 = sum_{j=0}^{2m} (P^-1 Q)^j P^-1 (symmetric Gauss-Seidel in red-black
+    order, and the modified Jacobi P = 2D)."""
+    rng = np.random.default_rng(91)
+    N = int(np.prod(n))
+    prob = _prob(n, 10.0 ** rng.uniform(-2, 2, N))
+    H = O.Hierarchy(prob, m=m, precond=2, splitting=splitting)
+    Mcols = np.stack([H.precond(0, np.eye(N)[i]) for i in range(N)], axis=1)
+    A = H.dense(0)
+    if splitting == 0:
+        Pm, Qm = _sgs_PQ(A, _rb_perm(n))
+    else:
+        Pm, Qm = _jacobi_PQ(A)
+    Pi = np.linalg.inv(Pm)
+    Hm = Pi @ Qm
+    M = np.zeros_like(A)
+    T = Pi.copy()
+    for _ in range(2 * m + 1):
+        M += T
+        T = Hm @ T
+    np.testing.assert_allclose(Mcols, M, atol=1e-10 * np.abs(M).max())
+    # W = P^-1 in eq. 2.6 gives the same matrix
+    M6 = np.linalg.matrix_power(Hm, m) @ Pi @ np.linalg.matrix_power(Qm @ Pi, m)
+    for j in range(2 * m):
+        M6 += np.linalg.matrix_power(Hm, j) @ Pi
+    np.testing.assert_allclose(M6, M, atol=1e-10 * np.abs(M).max())
+
+
+@pytest.mark.parametrize("n,m", [((24, 20), 4), ((24, 20), 1)])
+def test_multigrid_preconditioner_is_eq_2_9(n, m):
+    """eq. 2.9 on three levels: M_2^-1 = A_2^-1 (the coarsest exactly),
+    M_k^-1 = H_k^m E M_{k+1}^-1 R H_k^{T m} + sum_{j<2m} H_k^j P_k^-1 with
+    H_k = P_k^-1 Q_k and R = E^T, assembled here from dense matrices, equals
+    the oracle's preconditioner column by column; it is symmetric positive
+    definite (Tatebe)."""
+    rng = np.random.default_rng(92)
+    N = int(np.prod(n))
+    prob = _prob(n, 10.0 ** rng.uniform(-2, 2, N))
+    H = O.Hierarchy(prob, m=m, maxside=4, precond=1)
+    assert H.nlev == 3
+    Mcols = np.stack([H.precond(0, np.eye(N)[i]) for i in range(N)], axis=1)
+    d = [tuple(H.dims[k][:2]) for k in range(3)]
+    Minv = np.linalg.inv(H.dense(2))
+    for k in (1, 0):
+        A = H.dense(k)
+        Pm, Qm = _sgs_PQ(A, _rb_perm(d[k]))
+        Pi = np.linalg.inv(Pm)
+        Hk = Pi @ Qm
+        E = _E_dense_interp(d[k], d[k + 1])
+        M = np.linalg.matrix_power(Hk, m) @ E @ Minv @ E.T @ np.linalg.matrix_power(Qm @ Pi, m)
+        for j in range(2 * m):
+            M += np.linalg.matrix_power(Hk, j) @ Pi
+        Minv = M
+    scale = np.abs(Minv).max()
+    np.testing.assert_allclose(Mcols, Minv, atol=1e-9 * scale)
+    np.testing.assert_allclose(Mcols, Mcols.T, atol=1e-9 * scale)
+    assert np.linalg.eigvalsh(0.5 * (Mcols + Mcols.T)).min() > 0
+
+
+@pytest.mark.parametrize("precond", [1, 2])
+@pytest.mark.parametrize("n", [(29, 19), (12, 10, 9)])
+def test_other_preconditioners_solve_matches_direct_solve(n, precond):
+    rng = np.random.default_rng(93)
+    N = int(np.prod(n))
+    prob = _prob(n, 10.0 ** rng.uniform(-2, 2, N))
+    H = O.Hierarchy(prob, precond=precond, maxit_outer=2000)
+    b = H.lift_rhs()
+    x, st = H.solve(b, 1e-12)
+    assert st["status"] == 0 and st["relres_true"] < 1e-12
+    ex = spla.spsolve(_sparse_A(H, 0), b)
+    assert np.linalg.norm(x - ex) / np.linalg.norm(ex) < 1e-9
+    # bookkeeping: the multigrid preconditioner applies each coarse level once
+    # per outer iteration and runs no PCG below level 0
+    if precond == 1:
+        assert all(c == st["iters"][0] for c in st["calls"][1:]) and not any(st["iters"][1:])
+    else:
+        assert not any(st["calls"][1:])
+
+
+def test_paper_claims_on_the_preconditioners():
+    """Sec. 2.1: the polynomial preconditioner's iterations grow rapidly with
+    the dimension; Sec. 4.2 (Figs. 4, 5): the recursive multi-scale PCG's
+    level-0 iterations stay flat over grid sizes while Tatebe's multigrid
+    preconditioner needs more of them, increasingly so."""
+    it = {}
+    for n in (64, 128, 256):
+        prob = P.grf_problem((n, n), seed=1001, ell=16.0, half_span=4.5)
+        for pc in (0, 1) + ((2,) if n <= 128 else ()):
+            H = O.Hierarchy(prob, precond=pc, maxit_outer=2000)
+            x, st = H.solve(H.lift_rhs(), 1e-8)
+            assert st["status"] == 0 and st["relres_true"] < 1e-8
+            it[n, pc] = st["iters"][0]
+    rms = [it[n, 0] for n in (64, 128, 256)]
+    assert max(rms) - min(rms) <= 3
+    assert all(it[n, 1] > it[n, 0] for n in (64, 128, 256))
+    assert it[256, 1] > it[64, 1] + 5
+    assert it[128, 2] > 2 * it[64, 2] and it[64, 2] > 3 * it[64, 1]
