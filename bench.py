@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the uneven-batch and 3D sections")
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="length of the arrival stream")
+    ap.add_argument("--latency-samples", type=int, default=100)
+    ap.add_argument("--no-parity", action="store_true", help="skip the oracle check of sampled results")
     return ap.parse_args()
 
 
@@ -192,6 +194,17 @@ def _oracle_solve(j):
                      f=np.random.default_rng(1001 * 1000 + j).standard_normal(base.N), pbf=base.pbf)
     _, st = R.solve(R.lift_rhs(prob), TOL)
     return st["status"], st["iters"]
+
+
+def _oracle_solution(j):
+    """Problem j of the workload solved by the oracle: its solution, per-level
+    iterations and status (for the error of each GPU result)."""
+    import numpy as np
+    P, base, R = _ORACLE["P"], _ORACLE["base"], _ORACLE["R"]
+    prob = P.Problem(dim=2, n=base.n, h=base.h, K=base.K, bc=base.bc, gD=base.gD,
+                     f=np.random.default_rng(1001 * 1000 + j).standard_normal(base.N), pbf=base.pbf)
+    x, st = R.solve(R.lift_rhs(prob), TOL)
+    return x, st["iters"], st["status"]
 
 
 def host_cores():
@@ -461,6 +474,79 @@ def run_3d(args, M, P, dev, stream, nb):
     return out
 
 
+def run_preconditioners(args, M, P, dev, stream, nb):
+    """The preconditioners of Sec. 2 on the same smoother and transfers
+    (Figs. 4-5 context): the recursive multi-scale PCG (eq. 2.10) and
+    Tatebe's multigrid PCG (eq. 2.9) on the workload's field at several grid
+    sides (level-0 iterations, solves/s and ns per unknown, nb concurrent
+    solves, FP32 preconditioner), and the polynomial preconditioner (eq. 2.6
+    with W = P^-1) at 256^2, where it still converges."""
+    import numpy as np
+    import torch
+    out = {"workload": f"GRF corr. 16 cells, 1e9 contrast, N(0,1) source, {nb} concurrent solves per point",
+           "sizes": {}}
+    cases = [(n, pc) for n in (128, 256, 512, 1024) for pc in (0, 1)] + [(256, 2)]
+    for n, pc in cases:
+        base = P.config_problem(1, scale=n)
+        opts = M.default_opts(precision=1, inner_floor=1e-6, precond=pc, maxit_outer=2000)
+        hs, bs = [], []
+        for j in range(nb):
+            rng = np.random.default_rng(1001 * 1000 + j)
+            prob = P.Problem(dim=2, n=base.n, h=base.h, K=base.K, bc=base.bc, gD=base.gD,
+                             f=rng.standard_normal(base.N), pbf=base.pbf)
+            h = M.Hierarchy.from_problem(prob, opts, device=dev)
+            hs.append(h)
+            bs.append(h.rhs_for(prob))
+        per, sts = _timed_batch(M, hs, bs, 1, stream, dev)
+        ms = statistics.mean(per)
+        key = ["multiscale_eq2_10", "multigrid_eq2_9", "polynomial_eq2_6"][pc]
+        out["sizes"].setdefault(str(n), {})[key] = {
+            "iters": sts[0]["iters"], "solves_per_s": nb / (ms / 1e3), "ns_per_unknown": ms * 1e6 / (nb * base.N),
+            "status": sorted({s["status"] for s in sts}), "relres_true_max": max(s["relres_true"] for s in sts)}
+        del hs, bs
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_wide_kernels(args, M, P, dev, stream, peak):
+    """The multi-CTA kernels of the single-solve path, each launched
+    standalone on the two finest levels of a 4096^2 problem (vectors of 64 MB
+    and more, larger than L2): mean launch time, algorithmic bytes per launch,
+    GB/s and the fraction of the measured HBM peak."""
+    import torch
+    out = {"workload": "4096^2 GRF problem (corr. 16 cells, 1e9 contrast); levels 0 (4096^2) and 1 (1024^2)",
+           "peak_gbs": peak}
+    prob = P.config_problem(1, scale=4096)
+    for prec, key in ((1, "fp32_precond"), (0, "fp64_plain")):
+        H = M.Hierarchy.from_problem(prob, M.default_opts(precision=prec, inner_floor=1e-6 if prec else 0.0),
+                                     device=dev)
+        out[key] = {}
+        for k in (0, 1):
+            rows = H.profile_level(k, reps=20, stream=stream)
+            out[key][f"level{k}"] = [dict(r, frac=r["gbs"] / peak) for r in rows]
+        H.close()
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_stall_path(args, M, P, dev, stream):
+    """The layered channel field at 32^3 with the FP32 preconditioner: the
+    plain beta stalls; the stall test switches to the flexible beta and then
+    to the FP64 preconditioner (A9).  One solve; the path it took."""
+    import torch
+    prob = P.config_problem(2, scale=32)
+    out = {"workload": "3D 32^3 layered channel field (1e9 contrast), FP32 preconditioner"}
+    H = M.Hierarchy.from_problem(prob, M.default_opts(precision=1, inner_floor=1e-6), device=dev)
+    b = H.rhs_for(prob)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    _, st = H.solve(b, TOL, stream=stream, check=False)
+    out.update(status=st["status"], relres_true=st["relres_true"], iters=st["iters"], flexible=st["flexible"],
+               escalated=st["escalated"], ms=1e3 * (time.perf_counter() - t0))
+    H.close()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -533,6 +619,15 @@ def main():
         per = [e0.elapsed_time(e1) for (e0, e1) in evs]
         return per, sts, ck
 
+    # ---- oracle solutions of three sampled problems, computed on the host
+    # while the GPU runs (spawned processes: no CUDA context is inherited) ----
+    parity_jobs = None
+    if rank == 0 and not args.no_parity:
+        import multiprocessing as mp
+        sample = sorted({0, nb // 2, nb - 1})
+        ppool = mp.get_context("spawn").Pool(len(sample), initializer=_oracle_init, initargs=(args.size,))
+        parity_jobs = (sample, ppool, ppool.map_async(_oracle_solution, sample, chunksize=1))
+
     # ---- FP32 preconditioner (headline) ----
     hs, bs, xs = make_batch(1)
     clocks = Clocks(dev.index) if rank == 0 else None
@@ -570,12 +665,35 @@ def main():
         roofline["sm_issue"] = dict(tr["counters"], peak_inst_per_cycle=4,
                                     source="profiles/k_small_traffic_batch8.md")
 
+    # ---- error of sampled results against the oracle (outside the timed
+    # region: the last timed step's solutions) ----
+    parity = None
+    if parity_jobs is not None:
+        sample, ppool, job = parity_jobs
+        try:
+            res = job.get(timeout=900)
+            ppool.close()
+            errs, emax, oits = [], [], []
+            for j, (xr, its, stt) in zip(sample, res):
+                xg = xs[j].cpu().numpy()
+                errs.append(float(np.linalg.norm(xg - xr) / np.linalg.norm(xr)))
+                emax.append(float(np.max(np.abs(xg - xr)) / np.max(np.abs(xr))))
+                oits.append(its)
+            parity = {"problems": sample, "err_vs_oracle": errs, "err_max_elementwise": emax,
+                      "gpu_iters": [sts[j]["iters"] for j in sample], "oracle_iters": oits,
+                      "tolerance": 1e-6,
+                      "note": "relative 2-norm and max-norm error of the GPU solution (FP32 preconditioner) "
+                              "against the FP64 oracle at 1e-8; iterations per level, outer level first"}
+        except Exception as e:  # the oracle must not cost the GPU line
+            ppool.terminate()
+            parity = {"error": f"{type(e).__name__}: {e}"[:200]}
+
     # ---- latency of single solves (graph path) ----
     lat = []
     h0 = hs[0]
     x0 = torch.empty(base.N, dtype=torch.float64, device=dev)
     h0.solve(bs[0], TOL, x0, stats=False, stream=stream)
-    for _ in range(5):
+    for _ in range(max(1, args.latency_samples)):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         h0.solve(bs[0], TOL, x0, stats=False, stream=stream)
@@ -584,7 +702,8 @@ def main():
         lat.append(e0.elapsed_time(e1))
     lat.sort()
     latency = {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-               "samples": len(lat), "mode": "one solve at a time (wide levels as graph kernels)"}
+               "samples": len(lat), "unknowns_per_s": base.N / (float(np.percentile(lat, 50)) / 1e3),
+               "mode": "one solve at a time (wide levels as graph kernels)"}
 
     # ---- end to end through the C ABI with host buffers ----
     # Every step uploads its right-hand sides from pinned host memory and
@@ -640,12 +759,18 @@ def main():
         t64 = D.max_over_ranks(sum(per64), dev)
         fp64 = {"value": world * nb * len(per64) / (t64 / 1e3), "unit": UNIT, "ms_per_step": t64 / len(per64),
                 "iters": sts64[0]["iters"], "relres_true_max": max(s["relres_true"] for s in sts64)}
+        if parity and "oracle_iters" in parity:
+            fp64["iters_sampled"] = [sts64[j]["iters"] for j in parity["problems"]]
+            fp64["oracle_iters_sampled"] = parity["oracle_iters"]
         del hs, bs, xs
         torch.cuda.empty_cache()
 
     # ---- other workloads: uneven batch and 3D (rank 0 only) ----
-    uneven = grid3d = jacobi = natural = strip = None
+    uneven = grid3d = jacobi = natural = strip = precs = stall = wide = None
     if rank == 0 and not args.no_extra:
+        wide = run_wide_kernels(args, M, P, dev, stream, peak)
+        precs = run_preconditioners(args, M, P, dev, stream, nb)
+        stall = run_stall_path(args, M, P, dev, stream)
         uneven = run_uneven(args, M, P, dev, stream)
         grid3d = run_3d(args, M, P, dev, stream, nb)
         jacobi = run_splitting(args, M, P, dev, stream, nb, args.size, 1, "modified Jacobi P = 2D")
@@ -699,7 +824,8 @@ def main():
                            "tile_shapes": TU.key_of(tuned) + (" (autotuner record)" if tuned_rec is not None else "")},
                 "status": statuses, "relres_true_max": relres, "iters": sts[0]["iters"],
                 "latency_ms": latency, "fp64_plain": fp64, "uneven_batch": uneven, "grid3d": grid3d, "jacobi": jacobi,
-                "natural_order_sgs": natural, "anisotropic_strip": strip,
+                "natural_order_sgs": natural, "anisotropic_strip": strip, "preconditioners": precs,
+                "stall_path": stall, "parity": parity, "wide_level_kernels": wide,
                 "serving": serving, "e2e": e2e, "roofline": roofline,
                 "cpu_baseline": cpu, "clocks": ck, "gpu_launches": args.steps}
         print(json.dumps(line), flush=True)

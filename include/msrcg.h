@@ -93,13 +93,16 @@ typedef struct {
                           factor beta = r_new.(z_new - z_old) / r_old.z_old, which keeps the CG
                           directions useful when the preconditioner is not exactly linear (the
                           inexact inner solves of Sec. 2.3, FP32 inner levels); stalling again
-                          ends the solve with MSRCG_ENOCONV.  0 = 8; negative = no stall test.
+                          ends the solve with MSRCG_ENOCONV.  0 = 30 (the CG residual's 2-norm is
+                          not monotone: a short window stops slow but steady solves); negative = no
+                          stall test.
                           With precision 1 an inner level that hits its iteration cap also switches
                           the level-0 PCG to the flexible beta instead of failing the solve. */
   int escalate;        /* precision 1: a solve that ends in MSRCG_ENOCONV is run again with the FP64
                           preconditioner (a twin hierarchy built on the device from the level-0
                           transmissibilities, kept for later solves); 1 (default) = on, 0 = off.
-                          Applies to calls that synchronise (msrcg_solve with stats, batch). */
+                          Applies to calls that synchronise (msrcg_solve with stats, batch) and to
+                          the server's requests; not to msrcg_solve_static (it cannot allocate). */
   int flexible;        /* 1: the flexible beta from the first iteration (testing); 0 (default) */
   int precond;         /* preconditioner of the level-0 PCG (Sec. 2): 0 = recursive multi-scale,
                           eq. 2.10 (default); 1 = multigrid, eq. 2.9 (Tatebe): each coarse level
@@ -128,7 +131,7 @@ typedef struct {
 typedef struct msrcg_hier msrcg_hier;
 
 /* Fill *o with the paper's defaults: s = m = 4, f = 0.1, FP64, caps 200/500,
- * 2 s wait bound, stall test after 8 iterations, escalation on.  Returns
+ * 2 s wait bound, stall test after 30 iterations, escalation on.  Returns
  * MSRCG_OK, or MSRCG_EINVAL if o is NULL. */
 int msrcg_default_opts(msrcg_opts* o);
 
@@ -294,6 +297,28 @@ void msrcg_server_destroy(msrcg_server* sv);
 int msrcg_solve_static(const msrcg_grid* grid, const double* K, int ncomp, const uint8_t* bc,
                        const msrcg_opts* opts, const double* b, double tol, double* x, msrcg_stats* stats,
                        void* stream);
+
+/* ---- measurement: the multi-CTA kernels of one level, timed standalone ----
+ * Not a step of the method (the paper has no counterpart): a probe of how
+ * close each kernel of the single-solve path comes to the memory roofline.
+ * msrcg_profile_kernel_count() kernels, named by msrcg_profile_kernel_name(i)
+ * (a static string; "" for a bad index), in this order: red-black half-sweep,
+ * first half-sweep from zero, last half-sweep with r.z, residual,
+ * restriction, prolongation onto the black cells, CG direction, operator
+ * apply with p.q, CG update with r.r. */
+int msrcg_profile_kernel_count(void);
+const char* msrcg_profile_kernel_name(int i);
+
+/* Launch each kernel of level `level` (a level the single-solve path runs as
+ * multi-CTA kernels: level < the first single-CTA level, and not the
+ * coarsest) reps times back to back on `stream` after 3 warm-up launches;
+ * ms[i] = mean duration per launch (CUDA events), bytes[i] = the kernel's
+ * algorithmic bytes per launch (every array element it must read or write
+ * once, in the level's precisions).  ms and bytes are host arrays of
+ * msrcg_profile_kernel_count() entries.  The level's vectors are
+ * overwritten with garbage (the next solve clears them first).  Synchronises
+ * `stream`.  Errors: MSRCG_EINVAL (bad level or arguments), MSRCG_ECUDA. */
+int msrcg_profile_level(msrcg_hier* h, int level, int reps, double* ms, double* bytes, void* stream);
 
 /* Static description of an error code. */
 const char* msrcg_strerror(int code);

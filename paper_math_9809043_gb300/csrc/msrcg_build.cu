@@ -591,7 +591,10 @@ int msrcg_twin(msrcg_hier* h, cudaStream_t stream, msrcg_hier** out) {
     o.escalate = 0;
     Level0K src;
     for (int a = 0; a < h->dim; ++a) src.T0[a] = h->T64[0][a];
-    int rc = build_hier(&g, src, &o, stream, h->alloc_stream, &h->twin);
+    // stream-ordered allocation (the server): build on the allocation stream,
+    // so that every buffer exists before its first use; the build
+    // synchronises that stream before it returns
+    int rc = build_hier(&g, src, &o, h->alloc_stream ? h->alloc_stream : stream, h->alloc_stream, &h->twin);
     if (rc) return rc;
   }
   *out = h->twin;

@@ -148,6 +148,18 @@ int retire(msrcg_server* sv) {
       Request& r = sv->reqs[w.ids[i]];
       r.stats = st[i];
       r.status = st[i].status;
+      if (r.status == MSRCG_ENOCONV && r.h->o.precision == 1 && r.h->o.escalate) {
+        // the FP32 preconditioner did not get there: solve this request again
+        // with the FP64 one (the host waits for it; rare by design)
+        msrcg_hier* tw = nullptr;
+        if (msrcg_twin(r.h, w.s, &tw) == MSRCG_OK) {
+          const int flexible = r.stats.flexible;
+          msrcg_solve(tw, r.d_b, r.tol, r.d_x, &r.stats, w.s);
+          r.stats.flexible = flexible;
+          r.stats.escalated = 1;
+          r.status = r.stats.status;
+        }
+      }
       // the wave has finished: copy the solution into the caller's buffer
       cudaError_t e = cudaMemcpy(r.x_host, r.d_x, sizeof(double) * r.N, cudaMemcpyDeviceToHost);
       if (e != cudaSuccess && r.status == MSRCG_OK) r.status = msrcg_cuda_fail(e, "cudaMemcpy", __FILE__, __LINE__);

@@ -1744,7 +1744,7 @@ __device__ __forceinline__ long long lin_stride() {
 // counters, and the WHILE condition of the level's loop.
 template <typename V>
 __global__ void k_init(DevLevel L, int k, SolveState* S, const double* b0, double* partials,
-                       cudaGraphConditionalHandle hcond) {
+                       cudaGraphConditionalHandle hcond, int in_graph = 1) {
   V* x = (V*)L.x;
   V* r = (V*)L.r;
   V acc = 0;
@@ -1773,7 +1773,7 @@ __global__ void k_init(DevLevel L, int k, SolveState* S, const double* b0, doubl
     ls.it_best = 0;
     ls.gamma_ok = 0;
     ls.stop = !(bb > 0.0) || !isfinite(bb);
-    cudaGraphSetConditional(hcond, ls.stop ? 0u : 1u);
+    if (in_graph) cudaGraphSetConditional(hcond, ls.stop ? 0u : 1u);
   });
 }
 
@@ -1980,10 +1980,11 @@ __global__ void k_apply_dot(DevLevel L, int k, SolveState* S, double* partials) 
 // preconditioned residual); the stall test may switch the flexible beta on
 // or end the loop.
 template <typename V, typename RP>
-__global__ void k_update(DevLevel L, int k, SolveState* S, double* partials, cudaGraphConditionalHandle hcond) {
+__global__ void k_update(DevLevel L, int k, SolveState* S, double* partials, cudaGraphConditionalHandle hcond,
+                         int in_graph = 1) {
   const LevelState& ls = S->lv[k];
   if (ls.stop) {
-    if (lin_tid() == 0) cudaGraphSetConditional(hcond, 0u);
+    if (lin_tid() == 0 && in_graph) cudaGraphSetConditional(hcond, 0u);
     return;
   }
   const V alpha = alpha_of<V>(ls);
@@ -2035,7 +2036,7 @@ __global__ void k_update(DevLevel L, int k, SolveState* S, double* partials, cud
     }
     w.rho_old = w.rho;
     if (!go) w.stop = 1;
-    cudaGraphSetConditional(hcond, go ? 1u : 0u);
+    if (in_graph) cudaGraphSetConditional(hcond, go ? 1u : 0u);
   };
   if (gam) grid_total2(acc, acc2, partials, &S->ticket[k], fin);
   else grid_total(acc, partials, &S->ticket[k], [&](double rr) { fin(rr, 0.0); });
@@ -2416,7 +2417,7 @@ ProblemDesc make_desc(msrcg_hier* h, const double* b, double* x, double tol) {
   pd.fuse_min_cells = h->o.fuse_min_cells > 0 ? h->o.fuse_min_cells : kFuseMinCells;
   pd.splitting = h->o.splitting;
   pd.allow_flex = h->o.precision == 1;
-  pd.stall_w = pd.allow_flex && h->o.stall_iters >= 0 ? (h->o.stall_iters > 0 ? h->o.stall_iters : 8) : 0;
+  pd.stall_w = pd.allow_flex && h->o.stall_iters >= 0 ? (h->o.stall_iters > 0 ? h->o.stall_iters : 30) : 0;
   pd.flex0 = h->o.flexible;
   pd.precond = h->o.precond;
   return pd;
@@ -2644,6 +2645,110 @@ extern "C" int msrcg_batch_solve(int count, msrcg_hier* const* hs, const double*
   if (stats)
     for (int i = 0; i < count; ++i) stats[i] = one[i];
   return rc;
+}
+
+// ===========================================================================
+// Standalone timing of the multi-CTA kernels of one wide level
+// ===========================================================================
+namespace {
+
+const char* const kProfNames[] = {
+    "k_sweep (red-black half-sweep)", "k_sweep (first half-sweep, from zero)", "k_sweep_rho (last half-sweep + r.z)",
+    "k_residual (t = rp - A z)", "k_restrict (r_c = R t)", "k_prolong_black (z += E x_c, black cells)",
+    "k_direction (p = z + beta p)", "k_apply_dot (q = A p, p.q)", "k_update (x += alpha p, r -= alpha q, r.r)"};
+constexpr int kProfCount = (int)(sizeof(kProfNames) / sizeof(kProfNames[0]));
+
+template <int DIM, typename RP, typename V>
+int profile_level_t(msrcg_hier* h, int k, int reps, cudaStream_t s, double* ms, double* bytes) {
+  const DevLevel& L = h->hL[k];
+  const DevLevel& C = h->hL[k + 1];
+  const int gmax = std::min(h->sms * 8, kMaxGrid);
+  const Launch lc = cells_launch(L, gmax), lp = pairs_launch(L, gmax), lcc = cells_launch(C, gmax);
+  const Launch ll = lin_launch(L.npad, gmax), lu = lin_launch(L.npad, std::min(gmax, kMaxGrid / 2));
+  double* part = h->partials + (size_t)k * kMaxGrid;
+  SolveState* S = h->dS;
+  // a state in which every kernel does its full work: level k live, not the
+  // first iteration, finite scalars, a threshold that never stops it
+  SolveState st;
+  memset(&st, 0, sizeof(st));
+  LevelState& ls = st.lv[k];
+  ls.it = 1;
+  ls.rho = ls.rho_old = ls.pq = 1.0;
+  ls.alpha = ls.beta = 0.5;
+  ls.alpha_f = ls.beta_f = 0.5f;
+  ls.thr = -1.0;
+  MSRCG_CUDA_TRY(cudaMemcpyAsync(S, &st, sizeof(st), cudaMemcpyHostToDevice, s));
+  const double n = (double)L.n, nc = (double)C.n, d = DIM, rsz = sizeof(RP), vsz = sizeof(V);
+  const double bytes_of[kProfCount] = {
+      (d + 1.5) * n * rsz,                                    // T, rp and z of one colour, the other colour's z
+      d * n * rsz + n * vsz + (vsz != rsz ? n * rsz : 0.0) + n * rsz,  // T, r (-> rp), z written
+      (d + 2.0) * n * rsz + n * vsz,                          // half-sweep + z and r of every cell
+      (d + 3.0) * n * rsz,                                    // T, rp, z, t
+      (n + nc) * rsz,                                         // t, r_c
+      (n + nc) * rsz,                                         // x_c, black z read and written
+      n * rsz + 2.0 * n * vsz,                                // z, p read, p written
+      (d + 2.0) * n * vsz,                                    // T (vector precision), p, q
+      6.0 * n * vsz};                                         // x, p, r, q read; x, r written
+  cudaEvent_t e0, e1;
+  MSRCG_CUDA_TRY(cudaEventCreate(&e0));
+  MSRCG_CUDA_TRY(cudaEventCreate(&e1));
+  int rc = MSRCG_OK;
+  for (int id = 0; id < kProfCount && !rc; ++id) {
+    auto launch = [&]() {
+      switch (id) {
+        case 0: k_sweep<DIM, RP, V><<<lp.grid, lp.block, 0, s>>>(L, 0, 0); break;
+        case 1: k_sweep<DIM, RP, V><<<lc.grid, lc.block, 0, s>>>(L, 0, 1); break;
+        case 2: k_sweep_rho<DIM, RP, V><<<lp.grid, lp.block, 0, s>>>(L, k, S, part); break;
+        case 3: k_residual<DIM, RP><<<lc.grid, lc.block, 0, s>>>(L); break;
+        case 4: k_restrict<DIM, RP><<<lcc.grid, lcc.block, 0, s>>>(L, C); break;
+        case 5: k_prolong_black<DIM, RP><<<lp.grid, lp.block, 0, s>>>(L, C); break;
+        case 6: k_direction<V, RP><<<ll.grid, ll.block, 0, s>>>(L, k, S); break;
+        case 7: k_apply_dot<DIM, V><<<lc.grid, lc.block, 0, s>>>(L, k, S, part); break;
+        default: k_update<V, RP><<<lu.grid, lu.block, 0, s>>>(L, k, S, part, 0, 0); break;
+      }
+    };
+    for (int w = 0; w < 3; ++w) launch();  // warm-up
+    if (cudaEventRecord(e0, s) != cudaSuccess) rc = MSRCG_ECUDA;
+    for (int r = 0; r < reps && !rc; ++r) {
+      launch();
+      // keep the state live for the next launch (the update counts iterations)
+      if (id == 8 && cudaMemcpyAsync(S, &st, sizeof(st), cudaMemcpyHostToDevice, s) != cudaSuccess) rc = MSRCG_ECUDA;
+    }
+    if (!rc && cudaEventRecord(e1, s) != cudaSuccess) rc = MSRCG_ECUDA;
+    if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = MSRCG_ECUDA;
+    float t = 0.f;
+    if (!rc && cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) rc = MSRCG_ECUDA;
+    if (!rc && cudaGetLastError() != cudaSuccess) rc = MSRCG_ECUDA;
+    ms[id] = (double)t / reps;
+    bytes[id] = bytes_of[id];
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  (void)cudaGetLastError();
+  h->dirty = true;  // the level's vectors hold timing garbage: cleared before the next solve
+  return rc;
+}
+
+}  // namespace
+
+extern "C" int msrcg_profile_kernel_count(void) { return kProfCount; }
+
+extern "C" const char* msrcg_profile_kernel_name(int i) { return i >= 0 && i < kProfCount ? kProfNames[i] : ""; }
+
+extern "C" int msrcg_profile_level(msrcg_hier* h, int level, int reps, double* ms, double* bytes, void* stream) {
+  if (!h || !ms || !bytes || reps < 1 || level < 0 || level >= h->ks || level + 1 >= h->nlev) return MSRCG_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool f32 = h->o.precision == 1;
+  if (level == 0) {
+    if (h->dim == 2) return f32 ? profile_level_t<2, float, double>(h, 0, reps, s, ms, bytes)
+                                : profile_level_t<2, double, double>(h, 0, reps, s, ms, bytes);
+    return f32 ? profile_level_t<3, float, double>(h, 0, reps, s, ms, bytes)
+               : profile_level_t<3, double, double>(h, 0, reps, s, ms, bytes);
+  }
+  if (h->dim == 2) return f32 ? profile_level_t<2, float, float>(h, level, reps, s, ms, bytes)
+                              : profile_level_t<2, double, double>(h, level, reps, s, ms, bytes);
+  return f32 ? profile_level_t<3, float, float>(h, level, reps, s, ms, bytes)
+             : profile_level_t<3, double, double>(h, level, reps, s, ms, bytes);
 }
 
 // ===========================================================================

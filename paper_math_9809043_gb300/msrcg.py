@@ -96,6 +96,10 @@ def lib():
         L.msrcg_server_bytes_in_use.restype = C.c_size_t
         L.msrcg_server_destroy.argtypes = [vp]
         L.msrcg_server_destroy.restype = None
+        L.msrcg_profile_kernel_count.argtypes = []
+        L.msrcg_profile_kernel_name.argtypes = [C.c_int]
+        L.msrcg_profile_kernel_name.restype = C.c_char_p
+        L.msrcg_profile_level.argtypes = [vp, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
         L.msrcg_strerror.argtypes = [C.c_int]
         L.msrcg_strerror.restype = C.c_char_p
         _lib = L
@@ -330,6 +334,18 @@ class Hierarchy:
         if rc != OK:
             raise MsrcgError(rc, "msrcg_get_trans")
         return Tx, Ty, Tz
+
+    def profile_level(self, k, reps=20, stream=None):
+        """Per-kernel mean launch time (ms) and algorithmic bytes of level k's
+        multi-CTA kernels, timed standalone (msrcg_profile_level)."""
+        n = lib().msrcg_profile_kernel_count()
+        ms = (C.c_double * n)()
+        by = (C.c_double * n)()
+        rc = lib().msrcg_profile_level(self._h, k, int(reps), ms, by, _stream(stream))
+        if rc != OK:
+            raise MsrcgError(rc, "msrcg_profile_level")
+        return [{"kernel": lib().msrcg_profile_kernel_name(i).decode(), "ms": ms[i], "bytes": by[i],
+                 "gbs": by[i] / (ms[i] * 1e6) if ms[i] > 0 else 0.0} for i in range(n)]
 
     def apply(self, k, x, stream=None):
         d, _, _ = self.dims(k)
