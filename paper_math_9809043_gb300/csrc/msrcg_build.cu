@@ -739,6 +739,28 @@ int build_hier(const msrcg_grid* grid, const Level0K& src, const msrcg_opts* opt
     fk *= o.f;
     L.maxit = k == 0 ? o.maxit_outer : o.maxit_inner;
     if (k + 1 < h->nlev) {
+      if (dim == 2) {
+        // fine extent of the widest tile of the tiled restriction (kRestrictTI
+        // x rtj coarse cells): the tables' windows are monotone, so a tile of
+        // coarse cells I0..I1 reads fine cells lo[I0] .. hi[I1]
+        const Axis1D tx = axis_tables(h->dims[k][0], h->dims[k + 1][0], o.interp);
+        const Axis1D ty = axis_tables(h->dims[k][1], h->dims[k + 1][1], o.interp);
+        h->rtj = f32 ? 8 : 4;
+        int fx = 0, fy = 0;
+        for (int I0 = 0; I0 < h->dims[k + 1][0]; I0 += kRestrictTI) {
+          const int I1 = std::min(I0 + kRestrictTI, h->dims[k + 1][0]) - 1;
+          fx = std::max(fx, tx.hi[I1] - tx.lo[I0] + 1);
+        }
+        for (int J0 = 0; J0 < h->dims[k + 1][1]; J0 += h->rtj) {
+          const int J1 = std::min(J0 + h->rtj, h->dims[k + 1][1]) - 1;
+          fy = std::max(fy, ty.hi[J1] - ty.lo[J0] + 1);
+        }
+        const size_t smem = rsz * ((size_t)fx * fy + (size_t)fy * kRestrictTI);
+        if (smem <= 48 * 1024) {
+          h->rfx[k] = fx;
+          h->rfy[k] = fy;
+        }
+      }
       for (int a = 0; a < 3; ++a) {
         Axis1D ax = axis_tables(h->dims[k][a], h->dims[k + 1][a], o.interp);
         const void* p;
@@ -787,6 +809,12 @@ int build_hier(const msrcg_grid* grid, const Level0K& src, const msrcg_opts* opt
       L.rp = p;
     } else {
       L.rp = L.r;
+    }
+    if (k < h->ks) {
+      // a multi-CTA level writes each new direction into the other buffer
+      if ((rc = msrcg_alloc(h, &p, vsz * L.npad))) return fail(rc);
+      MSRCG_CUDA_TRY(cudaMemsetAsync(p, 0, vsz * L.npad, st));
+      L.p2 = p;
     }
   }
   // ---- coarsest exact inverse (A3) ----
@@ -855,6 +883,11 @@ size_t msrcg_build_bytes(const msrcg_grid* grid, const msrcg_opts* opts) {
   if (nlev < 1) return 0;
   const bool f32 = o.precision == 1;
   const size_t rsz = f32 ? sizeof(float) : sizeof(double);
+  // first single-CTA level, as the build chooses it
+  const int small = o.small_cells > 0 ? o.small_cells : 4096;
+  int ks = nlev - 1;
+  while (ks > 0 && (long long)dims[ks - 1][0] * dims[ks - 1][1] * dims[ks - 1][2] <= small) --ks;
+  if (o.splitting == 2 || o.precond != 0) ks = 0;
   size_t tot = 0;
   auto add = [&](size_t b) { tot += b ? b : 16; };
   for (int k = 0; k < nlev; ++k)
@@ -882,6 +915,7 @@ size_t msrcg_build_bytes(const msrcg_grid* grid, const msrcg_opts* opts) {
     add(rsz * npad);
     add(rsz * npad);
     if (vsz != rsz) add(rsz * npad);
+    if (k < ks) add(vsz * npad);
   }
   const size_t nc = (size_t)dims[nlev - 1][0] * dims[nlev - 1][1] * dims[nlev - 1][2];
   add(sizeof(double) * nc * nc);

@@ -31,6 +31,7 @@ constexpr int kThreads = 256;        // block size of the multi-CTA level kernel
 constexpr int kSmallThreads = MSRCG_SMALL_THREADS;  // block size of the single-CTA solver
 constexpr int kSmallPerSM = MSRCG_SMALL_PER_SM;     // single-CTA solvers resident per SM
 constexpr int kMaxGrid = 4096;       // upper bound of blocks per multi-CTA launch
+constexpr int kRestrictTI = 32;      // coarse columns per tile of the tiled restriction
 
 // status bits written on the device (host maps them to MSRCG_E*)
 constexpr int kStBreakdown = 1;
@@ -72,6 +73,7 @@ struct DevLevel {
   void* z;
   void* t;
   void* rp;              // r in smoother precision (aliases r when the types agree)
+  void* p2;              // multi-CTA levels: the second direction buffer (iterations alternate)
   double fk;             // f^k of the level test
   int maxit;
   int pad;
@@ -161,6 +163,11 @@ struct msrcg_hier {
   int64_t last_calls[MSRCG_MAXLEV] = {};
   int sms = 0;
   msrcg_hier* twin = nullptr;           // FP64-preconditioner twin of an FP32-mode hierarchy (escalation)
+  // tiled restriction of a wide 2D level k into k+1: the largest fine extent
+  // (columns, rows) of a tile of msrcg::kRestrictTI x rtj coarse cells, 0 = no
+  // tiled kernel (3D, or the tile does not fit the shared memory)
+  int rfx[MSRCG_MAXLEV] = {}, rfy[MSRCG_MAXLEV] = {};
+  int rtj = 0;
 };
 
 // allocation helper: records the buffer in h->allocs

@@ -1857,6 +1857,50 @@ __global__ void k_residual(DevLevel L) {
   });
 }
 
+// r_{k+1} = R t on a 2D level, by tiles of kRestrictTI x TJ coarse cells: the
+// CTA copies the tile's fine window of t into shared memory (coalesced rows),
+// forms for every fine row the x-sums of each coarse column, then the
+// y-sums: the products and their order are those of restrict_value, so the
+// result is the gather's, bit for bit, with every fine value read once.
+template <typename R>
+__global__ void k_restrict2d(DevLevel L, DevLevel C, int TJ, int FXM, int FYM) {
+  extern __shared__ __align__(16) unsigned char rsm[];
+  R* tile = (R*)rsm;           // FYM rows of FXM
+  R* hx = tile + FYM * FXM;    // FYM rows of kRestrictTI x-sums
+  const int I0 = blockIdx.x * kRestrictTI, J0 = blockIdx.y * TJ;
+  const int nI = min(kRestrictTI, C.nx - I0), nJ = min(TJ, C.ny - J0);
+  const int fx0 = __ldg(L.lo[0] + I0), fx1 = __ldg(L.hi[0] + I0 + nI - 1);
+  const int fy0 = __ldg(L.lo[1] + J0), fy1 = __ldg(L.hi[1] + J0 + nJ - 1);
+  const int FX = fx1 - fx0 + 1, FY = fy1 - fy0 + 1;
+  const R* t = (const R*)L.t + (int)L.off + L.px * fy0 + fx0;
+  for (int e = threadIdx.x; e < FX * FY; e += blockDim.x) {
+    const int r = e / FX, c = e - r * FX;
+    tile[r * FXM + c] = t[L.px * r + c];
+  }
+  __syncthreads();
+  const R* rwx = (const R*)L.rw[0];
+  const R* rwy = (const R*)L.rw[1];
+  for (int e = threadIdx.x; e < FY * nI; e += blockDim.x) {
+    const int r = e / nI, il = e - r * nI, I = I0 + il;
+    const int lo = __ldg(L.lo[0] + I), hi = __ldg(L.hi[0] + I);
+    const R* w = rwx + I * L.W[0] - lo;
+    const R* row = tile + r * FXM - fx0;
+    R acc = 0;
+    for (int ii = lo; ii <= hi; ++ii) acc += __ldg(w + ii) * row[ii];
+    hx[r * kRestrictTI + il] = acc;
+  }
+  __syncthreads();
+  R* rc = (R*)C.r + (int)C.off;
+  for (int e = threadIdx.x; e < nJ * nI; e += blockDim.x) {
+    const int jl = e / nI, il = e - jl * nI, J = J0 + jl;
+    const int lo = __ldg(L.lo[1] + J), hi = __ldg(L.hi[1] + J);
+    const R* w = rwy + J * L.W[1] - lo;
+    R acc = 0;
+    for (int jj = lo; jj <= hi; ++jj) acc += __ldg(w + jj) * hx[(jj - fy0) * kRestrictTI + il];
+    rc[C.px * J + I0 + il] = acc;
+  }
+}
+
 template <int DIM, typename RP>
 __global__ void k_restrict(DevLevel L, DevLevel C) {
   const RP* t = (const RP*)L.t;
@@ -1936,41 +1980,49 @@ __global__ void k_prolong_all(DevLevel L, DevLevel C) {
                  [&](int i, const Row& rw) { z[rw.pc + i] += prolong_value<DIM, RP>(L, C, xc, i, rw.j, rw.k); });
 }
 
-// p = z (first iteration) or z + beta p
-template <typename V, typename RP>
-__global__ void k_direction(DevLevel L, int k, SolveState* S) {
+// The CG direction and the operator in one pass: p = z (first iteration) or
+// z + beta p_old, q = A p, p . q, alpha = rho / p.q and the breakdown check.
+// The new direction goes to the other of the level's two direction buffers
+// (iteration parity), so that every thread can form its neighbours' new
+// directions from z and the old ones; same expressions as the direction
+// pass followed by the operator, so the same values.
+template <int DIM, typename V, typename RP>
+__global__ void k_direction_apply(DevLevel L, int k, SolveState* S, double* partials) {
   const LevelState& ls = S->lv[k];
   if (ls.stop) return;
   const bool first = ls.it == 0;
   const V beta = beta_of<V>(ls);
-  V* p = (V*)L.p;
+  V* pn = (V*)((ls.it & 1) ? L.p2 : L.p);
+  const V* po = (const V*)((ls.it & 1) ? L.p : L.p2);
   const RP* z = (const RP*)L.z;
-  const int n = (int)L.npad;
-  for (int c = (int)lin_tid(); c < n; c += (int)lin_stride()) p[c] = first ? (V)z[c] : (V)z[c] + beta * p[c];
-}
-
-// q = A p, pq = p . q, alpha = rho / pq; breakdown check
-template <int DIM, typename V>
-__global__ void k_apply_dot(DevLevel L, int k, SolveState* S, double* partials) {
-  if (S->lv[k].stop) return;
   const V *Tx = Tvec<V>(L, 0), *Ty = Tvec<V>(L, 1), *Tz = DIM == 3 ? Tvec<V>(L, 2) : nullptr;
-  const V* p = (const V*)L.p;
   V* q = (V*)L.q;
   V acc = 0;
   for_cells<DIM>(grid_map(), L, [&](int i, const Row& rw) {
-    const V v = apply_value<DIM, V, V>(L, Tx, Ty, Tz, p, i, rw);
-    acc += p[rw.pc + i] * v;
-    q[rw.pc + i] = v;
+    const int c = rw.pc + i;
+    // a ghost has z = 0 and p_old = 0, so its direction is 0
+    auto dir = [&](int e) __attribute__((always_inline)) { return first ? (V)z[e] : (V)z[e] + beta * po[e]; };
+    const V pc = dir(c);
+    V v = apply_terms2<V>(Tx[rw.fx + i], Tx[rw.fx + i + 1], Ty[rw.fy + i], Ty[rw.fy + i + L.nx], pc, dir(c - 1),
+                          dir(c + 1), dir(c - L.px), dir(c + L.px));
+    if (DIM == 3) {
+      const int pl = (int)L.plane;
+      v += Tz[rw.fz + i] * (pc - dir(c - pl));
+      v += Tz[rw.fz + i + L.nx * L.ny] * (pc - dir(c + pl));
+    }
+    acc += pc * v;
+    pn[c] = pc;
+    q[c] = v;
   });
   grid_total(acc, partials, &S->ticket[k], [&](double pq) {
-    LevelState& ls = S->lv[k];
-    ls.pq = pq;
-    if (!(pq > 0.0) || !isfinite(pq) || !isfinite(ls.rho)) {
-      ls.stop = 1;
+    LevelState& w = S->lv[k];
+    w.pq = pq;
+    if (!(pq > 0.0) || !isfinite(pq) || !isfinite(w.rho)) {
+      w.stop = 1;
       atomicOr(&S->status, kStBreakdown);
     }
-    ls.alpha = ls.rho / pq;
-    ls.alpha_f = (float)ls.alpha;
+    w.alpha = w.rho / pq;
+    w.alpha_f = (float)w.alpha;
   });
 }
 
@@ -1990,7 +2042,7 @@ __global__ void k_update(DevLevel L, int k, SolveState* S, double* partials, cud
   const V alpha = alpha_of<V>(ls);
   V* x = (V*)L.x;
   V* r = (V*)L.r;
-  const V* p = (const V*)L.p;
+  const V* p = (const V*)((ls.it & 1) ? L.p2 : L.p);  // this iteration's direction
   const V* q = (const V*)L.q;
   const RP* z = (const RP*)L.z;
   const bool gam = k == 0 && S->flex;
@@ -2153,6 +2205,23 @@ struct Emit {
 template <int DIM, typename RP>
 void emit_pcg(Emit& E, int k, cudaStream_t s);
 
+// r_{k+1} = R t of a wide level: by tiles (2D, when the build sized one),
+// else the per-cell gather
+template <int DIM, typename RP>
+void launch_restrict(const msrcg_hier* h, int k, int gmax, cudaStream_t s) {
+  const DevLevel& L = h->hL[k];
+  const DevLevel& C = h->hL[k + 1];
+  if (DIM == 2 && h->rfx[k] > 0) {
+    const int tj = h->rtj;
+    const dim3 grid((C.nx + kRestrictTI - 1) / kRestrictTI, (C.ny + tj - 1) / tj);
+    const size_t smem = sizeof(RP) * ((size_t)h->rfx[k] * h->rfy[k] + (size_t)h->rfy[k] * kRestrictTI);
+    k_restrict2d<RP><<<grid, 256, smem, s>>>(L, C, tj, h->rfx[k], h->rfy[k]);
+  } else {
+    const Launch lcc = cells_launch(C, gmax);
+    k_restrict<DIM, RP><<<lcc.grid, lcc.block, 0, s>>>(L, C);
+  }
+}
+
 template <int DIM, typename RP, typename V>
 void emit_smooth(const DevLevel& L, int m, bool from_zero, bool with_rho, int k, msrcg_hier* h, int gmax, cudaStream_t s) {
   const Launch lp = pairs_launch(L, gmax), lc = cells_launch(L, gmax);
@@ -2188,7 +2257,7 @@ void emit_precond(Emit& E, int k, cudaStream_t s) {
   const DevLevel& L = h->hL[k];
   const DevLevel& C = h->hL[k + 1];
   const int gmax = std::min(h->sms * 8, kMaxGrid);
-  const Launch lc = cells_launch(L, gmax), lp = pairs_launch(L, gmax), lcc = cells_launch(C, gmax);
+  const Launch lc = cells_launch(L, gmax), lp = pairs_launch(L, gmax);
   const int m = h->o.m;
   // pre-smoothing from zero, residual, restriction
   if (k == 0) {
@@ -2198,7 +2267,7 @@ void emit_precond(Emit& E, int k, cudaStream_t s) {
     emit_smooth<DIM, RP, RP>(L, m, true, false, k, h, gmax, s);
     k_residual<DIM, RP><<<lc.grid, lc.block, 0, s>>>(L);
   }
-  k_restrict<DIM, RP><<<lcc.grid, lcc.block, 0, s>>>(L, C);
+  launch_restrict<DIM, RP>(h, k, gmax, s);
   // coarse solve: A_c^-1 applied by the PCG one level down (Sec. 2.3)
   if (k + 1 < h->ks) emit_pcg<DIM, RP>(E, k + 1, s);
   else k_small<DIM, RP><<<1, kSmallThreads, h->sub_smem, s>>>(h->dP, nullptr, 1, k + 1, 0, nullptr, h->sub_smem);
@@ -2262,12 +2331,10 @@ void emit_pcg(Emit& E, int k, cudaStream_t s) {
   }
   emit_precond<DIM, RP>(E, k, b);
   if (k == 0) {
-    k_direction<double, RP><<<ll.grid, ll.block, 0, b>>>(L, k, h->dS);
-    k_apply_dot<DIM, double><<<lc.grid, lc.block, 0, b>>>(L, k, h->dS, part);
+    k_direction_apply<DIM, double, RP><<<lc.grid, lc.block, 0, b>>>(L, k, h->dS, part);
     k_update<double, RP><<<lu.grid, lu.block, 0, b>>>(L, k, h->dS, part, hc);
   } else {
-    k_direction<RP, RP><<<ll.grid, ll.block, 0, b>>>(L, k, h->dS);
-    k_apply_dot<DIM, RP><<<lc.grid, lc.block, 0, b>>>(L, k, h->dS, part);
+    k_direction_apply<DIM, RP, RP><<<lc.grid, lc.block, 0, b>>>(L, k, h->dS, part);
     k_update<RP, RP><<<lu.grid, lu.block, 0, b>>>(L, k, h->dS, part, hc);
   }
   cudaGraph_t out;
@@ -2449,6 +2516,7 @@ int scrub(msrcg_hier* h, cudaStream_t s) {
     for (int v = 0; v < 4; ++v) MSRCG_CUDA_TRY(cudaMemsetAsync(v4[v], 0, vsz * L.npad, s));
     MSRCG_CUDA_TRY(cudaMemsetAsync(L.z, 0, rsz * L.npad, s));
     MSRCG_CUDA_TRY(cudaMemsetAsync(L.t, 0, rsz * L.npad, s));
+    if (L.p2) MSRCG_CUDA_TRY(cudaMemsetAsync(L.p2, 0, vsz * L.npad, s));
   }
   MSRCG_CUDA_TRY(cudaMemsetAsync(h->b0, 0, sizeof(double) * h->hL[0].npad, s));
   return MSRCG_OK;
@@ -2652,10 +2720,28 @@ extern "C" int msrcg_batch_solve(int count, msrcg_hier* const* hs, const double*
 // ===========================================================================
 namespace {
 
+// Interior cells of every vector of a level (and of the coarse level's x) set
+// to 1 for the timing runs: finite values, p . A p > 0 (the Dirichlet faces),
+// so that every kernel does its whole work.
+template <int DIM, typename RP, typename V>
+__global__ void k_fill_ones(DevLevel L, DevLevel C) {
+  for_cells<DIM>(grid_map(), L, [&](int i, const Row& rw) {
+    const int c = rw.pc + i;
+    ((V*)L.x)[c] = (V)1;
+    ((V*)L.r)[c] = (V)1;
+    ((V*)L.p)[c] = (V)1;
+    ((V*)L.q)[c] = (V)1;
+    ((RP*)L.z)[c] = (RP)1;
+    ((RP*)L.t)[c] = (RP)1;
+    ((RP*)L.rp)[c] = (RP)1;
+  });
+  for_cells<DIM>(grid_map(), C, [&](int i, const Row& rw) { ((RP*)C.x)[rw.pc + i] = (RP)1; });
+}
+
 const char* const kProfNames[] = {
     "k_sweep (red-black half-sweep)", "k_sweep (first half-sweep, from zero)", "k_sweep_rho (last half-sweep + r.z)",
     "k_residual (t = rp - A z)", "k_restrict (r_c = R t)", "k_prolong_black (z += E x_c, black cells)",
-    "k_direction (p = z + beta p)", "k_apply_dot (q = A p, p.q)", "k_update (x += alpha p, r -= alpha q, r.r)"};
+    "k_direction_apply (p = z + beta p, q = A p, p.q)", "k_update (x += alpha p, r -= alpha q, r.r)"};
 constexpr int kProfCount = (int)(sizeof(kProfNames) / sizeof(kProfNames[0]));
 
 template <int DIM, typename RP, typename V>
@@ -2663,7 +2749,7 @@ int profile_level_t(msrcg_hier* h, int k, int reps, cudaStream_t s, double* ms, 
   const DevLevel& L = h->hL[k];
   const DevLevel& C = h->hL[k + 1];
   const int gmax = std::min(h->sms * 8, kMaxGrid);
-  const Launch lc = cells_launch(L, gmax), lp = pairs_launch(L, gmax), lcc = cells_launch(C, gmax);
+  const Launch lc = cells_launch(L, gmax), lp = pairs_launch(L, gmax);
   const Launch ll = lin_launch(L.npad, gmax), lu = lin_launch(L.npad, std::min(gmax, kMaxGrid / 2));
   double* part = h->partials + (size_t)k * kMaxGrid;
   SolveState* S = h->dS;
@@ -2686,8 +2772,7 @@ int profile_level_t(msrcg_hier* h, int k, int reps, cudaStream_t s, double* ms, 
       (d + 3.0) * n * rsz,                                    // T, rp, z, t
       (n + nc) * rsz,                                         // t, r_c
       (n + nc) * rsz,                                         // x_c, black z read and written
-      n * rsz + 2.0 * n * vsz,                                // z, p read, p written
-      (d + 2.0) * n * vsz,                                    // T (vector precision), p, q
+      n * rsz + (d + 3.0) * n * vsz,                          // z, old p, T (vector precision); p, q written
       6.0 * n * vsz};                                         // x, p, r, q read; x, r written
   cudaEvent_t e0, e1;
   MSRCG_CUDA_TRY(cudaEventCreate(&e0));
@@ -2700,19 +2785,20 @@ int profile_level_t(msrcg_hier* h, int k, int reps, cudaStream_t s, double* ms, 
         case 1: k_sweep<DIM, RP, V><<<lc.grid, lc.block, 0, s>>>(L, 0, 1); break;
         case 2: k_sweep_rho<DIM, RP, V><<<lp.grid, lp.block, 0, s>>>(L, k, S, part); break;
         case 3: k_residual<DIM, RP><<<lc.grid, lc.block, 0, s>>>(L); break;
-        case 4: k_restrict<DIM, RP><<<lcc.grid, lcc.block, 0, s>>>(L, C); break;
+        case 4: launch_restrict<DIM, RP>(h, k, gmax, s); break;
         case 5: k_prolong_black<DIM, RP><<<lp.grid, lp.block, 0, s>>>(L, C); break;
-        case 6: k_direction<V, RP><<<ll.grid, ll.block, 0, s>>>(L, k, S); break;
-        case 7: k_apply_dot<DIM, V><<<lc.grid, lc.block, 0, s>>>(L, k, S, part); break;
+        case 6: k_direction_apply<DIM, V, RP><<<lc.grid, lc.block, 0, s>>>(L, k, S, part); break;
         default: k_update<V, RP><<<lu.grid, lu.block, 0, s>>>(L, k, S, part, 0, 0); break;
       }
     };
+    k_fill_ones<DIM, RP, V><<<lc.grid, lc.block, 0, s>>>(L, C);
+    if (cudaMemcpyAsync(S, &st, sizeof(st), cudaMemcpyHostToDevice, s) != cudaSuccess) rc = MSRCG_ECUDA;
     for (int w = 0; w < 3; ++w) launch();  // warm-up
     if (cudaEventRecord(e0, s) != cudaSuccess) rc = MSRCG_ECUDA;
     for (int r = 0; r < reps && !rc; ++r) {
       launch();
       // keep the state live for the next launch (the update counts iterations)
-      if (id == 8 && cudaMemcpyAsync(S, &st, sizeof(st), cudaMemcpyHostToDevice, s) != cudaSuccess) rc = MSRCG_ECUDA;
+      if (id == 7 && cudaMemcpyAsync(S, &st, sizeof(st), cudaMemcpyHostToDevice, s) != cudaSuccess) rc = MSRCG_ECUDA;
     }
     if (!rc && cudaEventRecord(e1, s) != cudaSuccess) rc = MSRCG_ECUDA;
     if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = MSRCG_ECUDA;
