@@ -810,12 +810,7 @@ int build_hier(const msrcg_grid* grid, const Level0K& src, const msrcg_opts* opt
     } else {
       L.rp = L.r;
     }
-    if (k < h->ks) {
-      // a multi-CTA level writes each new direction into the other buffer
-      if ((rc = msrcg_alloc(h, &p, vsz * L.npad))) return fail(rc);
-      MSRCG_CUDA_TRY(cudaMemsetAsync(p, 0, vsz * L.npad, st));
-      L.p2 = p;
-    }
+
   }
   // ---- coarsest exact inverse (A3) ----
   {
@@ -883,11 +878,6 @@ size_t msrcg_build_bytes(const msrcg_grid* grid, const msrcg_opts* opts) {
   if (nlev < 1) return 0;
   const bool f32 = o.precision == 1;
   const size_t rsz = f32 ? sizeof(float) : sizeof(double);
-  // first single-CTA level, as the build chooses it
-  const int small = o.small_cells > 0 ? o.small_cells : 4096;
-  int ks = nlev - 1;
-  while (ks > 0 && (long long)dims[ks - 1][0] * dims[ks - 1][1] * dims[ks - 1][2] <= small) --ks;
-  if (o.splitting == 2 || o.precond != 0) ks = 0;
   size_t tot = 0;
   auto add = [&](size_t b) { tot += b ? b : 16; };
   for (int k = 0; k < nlev; ++k)
@@ -915,7 +905,6 @@ size_t msrcg_build_bytes(const msrcg_grid* grid, const msrcg_opts* opts) {
     add(rsz * npad);
     add(rsz * npad);
     if (vsz != rsz) add(rsz * npad);
-    if (k < ks) add(vsz * npad);
   }
   const size_t nc = (size_t)dims[nlev - 1][0] * dims[nlev - 1][1] * dims[nlev - 1][2];
   add(sizeof(double) * nc * nc);

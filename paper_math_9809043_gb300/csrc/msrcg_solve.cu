@@ -1873,32 +1873,35 @@ __global__ void k_restrict2d(DevLevel L, DevLevel C, int TJ, int FXM, int FYM) {
   const int fy0 = __ldg(L.lo[1] + J0), fy1 = __ldg(L.hi[1] + J0 + nJ - 1);
   const int FX = fx1 - fx0 + 1, FY = fy1 - fy0 + 1;
   const R* t = (const R*)L.t + (int)L.off + L.px * fy0 + fx0;
-  for (int e = threadIdx.x; e < FX * FY; e += blockDim.x) {
-    const int r = e / FX, c = e - r * FX;
-    tile[r * FXM + c] = t[L.px * r + c];
-  }
+  // warps walk rows, lanes columns (kRestrictTI = 32 coarse columns per tile)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int r = warp; r < FY; r += nw)
+    for (int c = lane; c < FX; c += 32) tile[r * FXM + c] = t[L.px * r + c];
   __syncthreads();
   const R* rwx = (const R*)L.rw[0];
   const R* rwy = (const R*)L.rw[1];
-  for (int e = threadIdx.x; e < FY * nI; e += blockDim.x) {
-    const int r = e / nI, il = e - r * nI, I = I0 + il;
+  if (lane < nI) {
+    const int I = I0 + lane;
     const int lo = __ldg(L.lo[0] + I), hi = __ldg(L.hi[0] + I);
     const R* w = rwx + I * L.W[0] - lo;
-    const R* row = tile + r * FXM - fx0;
-    R acc = 0;
-    for (int ii = lo; ii <= hi; ++ii) acc += __ldg(w + ii) * row[ii];
-    hx[r * kRestrictTI + il] = acc;
+    for (int r = warp; r < FY; r += nw) {
+      const R* row = tile + r * FXM - fx0;
+      R acc = 0;
+      for (int ii = lo; ii <= hi; ++ii) acc += __ldg(w + ii) * row[ii];
+      hx[r * kRestrictTI + lane] = acc;
+    }
   }
   __syncthreads();
   R* rc = (R*)C.r + (int)C.off;
-  for (int e = threadIdx.x; e < nJ * nI; e += blockDim.x) {
-    const int jl = e / nI, il = e - jl * nI, J = J0 + jl;
-    const int lo = __ldg(L.lo[1] + J), hi = __ldg(L.hi[1] + J);
-    const R* w = rwy + J * L.W[1] - lo;
-    R acc = 0;
-    for (int jj = lo; jj <= hi; ++jj) acc += __ldg(w + jj) * hx[(jj - fy0) * kRestrictTI + il];
-    rc[C.px * J + I0 + il] = acc;
-  }
+  if (lane < nI)
+    for (int jl = warp; jl < nJ; jl += nw) {
+      const int J = J0 + jl;
+      const int lo = __ldg(L.lo[1] + J), hi = __ldg(L.hi[1] + J);
+      const R* w = rwy + J * L.W[1] - lo;
+      R acc = 0;
+      for (int jj = lo; jj <= hi; ++jj) acc += __ldg(w + jj) * hx[(jj - fy0) * kRestrictTI + lane];
+      rc[C.px * J + I0 + lane] = acc;
+    }
 }
 
 template <int DIM, typename RP>
@@ -1907,6 +1910,147 @@ __global__ void k_restrict(DevLevel L, DevLevel C) {
   RP* rc = (RP*)C.r;
   for_cells<DIM>(grid_map(), C,
                  [&](int i, const Row& rw) { rc[rw.pc + i] = restrict_value<DIM, RP>(L, t, i, rw.j, rw.k); });
+}
+
+// ---------------------------------------------------------------------------
+// Temporally blocked smoothing of a wide 2D level (red-black SGS)
+// ---------------------------------------------------------------------------
+// One CTA smooths a tile of TW x TW cells: it copies the tile and a halo of
+// H = 2m+2 cells (face transmissibilities, right-hand side, iterate) into
+// shared memory, runs all 2m+1 half-sweeps there -- each on the cells that
+// can still influence the tile, a ring narrower per half-sweep -- and writes
+// the tile's results.  A halo value goes stale one cell further inward per
+// half-sweep, and the tile lies H > 2m+1 cells inside the copied region, so
+// every tile cell takes exactly the values of the plain half-sweep order
+// (same arithmetic helpers, same order of terms).  Each array crosses HBM
+// about once per smoothing instead of once per half-sweep.
+//   pre  (from zero): z = rp/D on red cells (rp = r rounded into the smoother
+//        precision, written out), 2m more half-sweeps; writes z, t = rp - A z.
+//   post: reads the prolonged iterate from t (written by k_prolong_to_t, so
+//        that no tile reads a halo another tile has overwritten), 2m+1
+//        half-sweeps; writes z and returns rho = r . z (and beta).
+// The CTA loops over tiles (grid <= tiles).
+template <typename RP>
+__host__ __device__ __forceinline__ size_t tile_smem_bytes(int TW, int m) {
+  const int WM = TW + 2 * (2 * m + 2);
+  return sizeof(RP) * (2 * (size_t)(WM + 2) * (WM + 2) + 2 * (size_t)WM * (WM + 1));
+}
+
+template <typename RP, typename V, bool PRE>
+__global__ void __launch_bounds__(512) k_smooth_tile(DevLevel L, int m, int TW, int k, SolveState* S,
+                                                    double* partials) {
+  extern __shared__ __align__(16) unsigned char tsm[];
+  const int H = 2 * m + 2, WM = TW + 2 * H, SM = WM + 2;
+  RP* sz = (RP*)tsm;              // iterate, with a zero ring: (b+1)*SW + a+1
+  RP* srp = sz + SM * SM;         // right-hand side, same layout
+  RP* stx = srp + SM * SM;        // x-faces of the region rows: b*(WR+1) + a
+  RP* sty = stx + WM * (WM + 1);  // y-faces: b*WR + a, b = 0..HR
+  const int nx = L.nx, ny = L.ny, px = L.px, off = (int)L.off;
+  const RP* gTx = (const RP*)L.T[0];
+  const RP* gTy = (const RP*)L.T[1];
+  const V* gr = (const V*)L.r;
+  RP* grp = (RP*)L.rp;
+  const RP* gin = PRE ? nullptr : (const RP*)L.t;
+  RP* gz = (RP*)L.z;
+  RP* gt = (RP*)L.t;
+  const int tx = (nx + TW - 1) / TW, ntiles = tx * ((ny + TW - 1) / TW);
+  V acc = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int X0 = (tile % tx) * TW, Y0 = (tile / tx) * TW;
+    const int X1 = min(nx, X0 + TW), Y1 = min(ny, Y0 + TW);  // the tile: [X0, X1) x [Y0, Y1)
+    const int x0 = max(0, X0 - H), x1 = min(nx, X1 + H), y0 = max(0, Y0 - H), y1 = min(ny, Y1 + H);
+    const int WR = x1 - x0, HR = y1 - y0, SW = WR + 2;
+    __syncthreads();  // the previous tile's last reads are done
+    // ---- copy the region (and zero the ring of z / rp) ----
+    for (int e = threadIdx.x; e < (WR + 1) * HR; e += blockDim.x) {
+      const int b = e / (WR + 1), a = e - b * (WR + 1);
+      stx[e] = gTx[(nx + 1) * (y0 + b) + x0 + a];
+    }
+    for (int e = threadIdx.x; e < WR * (HR + 1); e += blockDim.x) {
+      const int b = e / WR, a = e - b * WR;
+      sty[e] = gTy[nx * (y0 + b) + x0 + a];
+    }
+    for (int e = threadIdx.x; e < SW * (HR + 2); e += blockDim.x) {
+      const int b = e / SW - 1, a = e - (b + 1) * SW - 1;
+      const bool in = a >= 0 && a < WR && b >= 0 && b < HR;
+      const int g = off + px * (y0 + b) + x0 + a;
+      RP rv = 0, zv = 0;
+      if (in) {
+        if (PRE) {
+          rv = (RP)gr[g];  // r rounded into the smoother precision (or rp itself)
+        } else {
+          rv = grp[g];
+          zv = gin[g];
+        }
+      }
+      srp[e] = rv;
+      sz[e] = zv;
+    }
+    __syncthreads();
+    // ---- half-sweeps: h = 0 red (from zero in pre), then black, red, ... ----
+    for (int h = 0; h <= 2 * m; ++h) {
+      const int colour = h & 1;
+      // cells within distance 2m+1-h of the tile still matter
+      const int reach = 2 * m + 1 - h;
+      const int ax0 = max(x0, X0 - reach) - x0, ax1 = min(x1, X1 + reach) - x0;
+      const int by0 = max(y0, Y0 - reach) - y0, by1 = min(y1, Y1 + reach) - y0;
+      const int w = ax1 - ax0, hw = (w + 1) >> 1, rows = by1 - by0;
+      for (int e = threadIdx.x; e < hw * rows; e += blockDim.x) {
+        const int bb = e / hw, b = by0 + bb;
+        // cells of `colour` in region row b: global parity (x + y) & 1
+        const int a = ax0 + 2 * (e - bb * hw) + ((x0 + ax0 + y0 + b + colour) & 1);
+        if (a >= ax1) continue;
+        const int c = (b + 1) * SW + a + 1;
+        const RP tw = stx[b * (WR + 1) + a], te = stx[b * (WR + 1) + a + 1];
+        const RP ts = sty[b * WR + a], tn = sty[(b + 1) * WR + a];
+        RP v;
+        if (PRE && h == 0) {
+          RP d = tw;
+          d += te;
+          d += ts;
+          d += tn;
+          v = quot<RP>(srp[c], d);
+        } else {
+          RP d, sm = srp[c];
+          gs_terms2<RP>(d, sm, tw, te, ts, tn, sz[c - 1], sz[c + 1], sz[c - SW], sz[c + SW]);
+          v = quot<RP>(sm, d);
+        }
+        sz[c] = v;
+      }
+      __syncthreads();
+    }
+    // ---- the tile's results ----
+    for (int e = threadIdx.x; e < (X1 - X0) * (Y1 - Y0); e += blockDim.x) {
+      const int yy = e / (X1 - X0), xx = e - yy * (X1 - X0);
+      const int a = X0 - x0 + xx, b = Y0 - y0 + yy;
+      const int c = (b + 1) * SW + a + 1, g = off + px * (Y0 + yy) + X0 + xx;
+      const RP zc = sz[c];
+      gz[g] = zc;
+      if (PRE) {
+        const RP av = apply_terms2<RP>(stx[b * (WR + 1) + a], stx[b * (WR + 1) + a + 1], sty[b * WR + a],
+                                       sty[(b + 1) * WR + a], zc, sz[c - 1], sz[c + 1], sz[c - SW], sz[c + SW]);
+        gt[g] = srp[c] - av;
+        if (sizeof(V) != sizeof(RP)) grp[g] = srp[c];
+      } else {
+        acc += gr[g] * (V)zc;
+      }
+    }
+  }
+  if (!PRE) grid_total(acc, partials, &S->ticket[k], [&](double rho) { set_rho_beta(S->lv[k], k, S, rho); });
+}
+
+// t = z + E x_c on the black cells, t = z on the red ones: the prolonged
+// iterate that the blocked post-smoothing reads (see k_smooth_tile)
+template <int DIM, typename RP>
+__global__ void k_prolong_to_t(DevLevel L, DevLevel C) {
+  const RP* xc = (const RP*)C.x;
+  const RP* z = (const RP*)L.z;
+  RP* t = (RP*)L.t;
+  for_cells<DIM>(grid_map(), L, [&](int i, const Row& rw) {
+    const int c = rw.pc + i;
+    const RP zv = z[c];
+    t[c] = ((i + rw.j + rw.k) & 1) ? zv + prolong_value<DIM, RP>(L, C, xc, i, rw.j, rw.k) : zv;
+  });
 }
 
 // z += E x_c on the black cells (see Ops::prolong_postsmooth)
@@ -1980,49 +2124,41 @@ __global__ void k_prolong_all(DevLevel L, DevLevel C) {
                  [&](int i, const Row& rw) { z[rw.pc + i] += prolong_value<DIM, RP>(L, C, xc, i, rw.j, rw.k); });
 }
 
-// The CG direction and the operator in one pass: p = z (first iteration) or
-// z + beta p_old, q = A p, p . q, alpha = rho / p.q and the breakdown check.
-// The new direction goes to the other of the level's two direction buffers
-// (iteration parity), so that every thread can form its neighbours' new
-// directions from z and the old ones; same expressions as the direction
-// pass followed by the operator, so the same values.
-template <int DIM, typename V, typename RP>
-__global__ void k_direction_apply(DevLevel L, int k, SolveState* S, double* partials) {
+// p = z (first iteration) or z + beta p
+template <typename V, typename RP>
+__global__ void k_direction(DevLevel L, int k, SolveState* S) {
   const LevelState& ls = S->lv[k];
   if (ls.stop) return;
   const bool first = ls.it == 0;
   const V beta = beta_of<V>(ls);
-  V* pn = (V*)((ls.it & 1) ? L.p2 : L.p);
-  const V* po = (const V*)((ls.it & 1) ? L.p : L.p2);
+  V* p = (V*)L.p;
   const RP* z = (const RP*)L.z;
+  const int n = (int)L.npad;
+  for (int c = (int)lin_tid(); c < n; c += (int)lin_stride()) p[c] = first ? (V)z[c] : (V)z[c] + beta * p[c];
+}
+
+// q = A p, pq = p . q, alpha = rho / pq; breakdown check
+template <int DIM, typename V>
+__global__ void k_apply_dot(DevLevel L, int k, SolveState* S, double* partials) {
+  if (S->lv[k].stop) return;
   const V *Tx = Tvec<V>(L, 0), *Ty = Tvec<V>(L, 1), *Tz = DIM == 3 ? Tvec<V>(L, 2) : nullptr;
+  const V* p = (const V*)L.p;
   V* q = (V*)L.q;
   V acc = 0;
   for_cells<DIM>(grid_map(), L, [&](int i, const Row& rw) {
-    const int c = rw.pc + i;
-    // a ghost has z = 0 and p_old = 0, so its direction is 0
-    auto dir = [&](int e) __attribute__((always_inline)) { return first ? (V)z[e] : (V)z[e] + beta * po[e]; };
-    const V pc = dir(c);
-    V v = apply_terms2<V>(Tx[rw.fx + i], Tx[rw.fx + i + 1], Ty[rw.fy + i], Ty[rw.fy + i + L.nx], pc, dir(c - 1),
-                          dir(c + 1), dir(c - L.px), dir(c + L.px));
-    if (DIM == 3) {
-      const int pl = (int)L.plane;
-      v += Tz[rw.fz + i] * (pc - dir(c - pl));
-      v += Tz[rw.fz + i + L.nx * L.ny] * (pc - dir(c + pl));
-    }
-    acc += pc * v;
-    pn[c] = pc;
-    q[c] = v;
+    const V v = apply_value<DIM, V, V>(L, Tx, Ty, Tz, p, i, rw);
+    acc += p[rw.pc + i] * v;
+    q[rw.pc + i] = v;
   });
   grid_total(acc, partials, &S->ticket[k], [&](double pq) {
-    LevelState& w = S->lv[k];
-    w.pq = pq;
-    if (!(pq > 0.0) || !isfinite(pq) || !isfinite(w.rho)) {
-      w.stop = 1;
+    LevelState& ls = S->lv[k];
+    ls.pq = pq;
+    if (!(pq > 0.0) || !isfinite(pq) || !isfinite(ls.rho)) {
+      ls.stop = 1;
       atomicOr(&S->status, kStBreakdown);
     }
-    w.alpha = w.rho / pq;
-    w.alpha_f = (float)w.alpha;
+    ls.alpha = ls.rho / pq;
+    ls.alpha_f = (float)ls.alpha;
   });
 }
 
@@ -2042,7 +2178,7 @@ __global__ void k_update(DevLevel L, int k, SolveState* S, double* partials, cud
   const V alpha = alpha_of<V>(ls);
   V* x = (V*)L.x;
   V* r = (V*)L.r;
-  const V* p = (const V*)((ls.it & 1) ? L.p2 : L.p);  // this iteration's direction
+  const V* p = (const V*)L.p;
   const V* q = (const V*)L.q;
   const RP* z = (const RP*)L.z;
   const bool gam = k == 0 && S->flex;
@@ -2259,8 +2395,14 @@ void emit_precond(Emit& E, int k, cudaStream_t s) {
   const int gmax = std::min(h->sms * 8, kMaxGrid);
   const Launch lc = cells_launch(L, gmax), lp = pairs_launch(L, gmax);
   const int m = h->o.m;
+  const int tw = h->tile_tw[k];
+  const size_t tsm = tw ? tile_smem_bytes<RP>(tw, m) : 0;
+  double* part = h->partials + (size_t)k * kMaxGrid;
   // pre-smoothing from zero, residual, restriction
-  if (k == 0) {
+  if (tw) {
+    if (k == 0) k_smooth_tile<RP, double, true><<<h->tile_grid[k], 512, tsm, s>>>(L, m, tw, k, h->dS, part);
+    else k_smooth_tile<RP, RP, true><<<h->tile_grid[k], 512, tsm, s>>>(L, m, tw, k, h->dS, part);
+  } else if (k == 0) {
     emit_smooth<DIM, RP, double>(L, m, true, false, k, h, gmax, s);
     k_residual<DIM, RP><<<lc.grid, lc.block, 0, s>>>(L);
   } else {
@@ -2273,6 +2415,12 @@ void emit_precond(Emit& E, int k, cudaStream_t s) {
   else k_small<DIM, RP><<<1, kSmallThreads, h->sub_smem, s>>>(h->dP, nullptr, 1, k + 1, 0, nullptr, h->sub_smem);
   // prolongation (black cells; every cell for the Jacobi smoother) and
   // post-smoothing with rho = r . z
+  if (tw) {
+    k_prolong_to_t<DIM, RP><<<lc.grid, lc.block, 0, s>>>(L, C);
+    if (k == 0) k_smooth_tile<RP, double, false><<<h->tile_grid[k], 512, tsm, s>>>(L, m, tw, k, h->dS, part);
+    else k_smooth_tile<RP, RP, false><<<h->tile_grid[k], 512, tsm, s>>>(L, m, tw, k, h->dS, part);
+    return;
+  }
   if (h->o.splitting == 1) k_prolong_all<DIM, RP><<<lc.grid, lc.block, 0, s>>>(L, C);
   else k_prolong_black<DIM, RP><<<lp.grid, lp.block, 0, s>>>(L, C);
   if (k == 0) emit_smooth<DIM, RP, double>(L, m, false, true, k, h, gmax, s);
@@ -2331,10 +2479,12 @@ void emit_pcg(Emit& E, int k, cudaStream_t s) {
   }
   emit_precond<DIM, RP>(E, k, b);
   if (k == 0) {
-    k_direction_apply<DIM, double, RP><<<lc.grid, lc.block, 0, b>>>(L, k, h->dS, part);
+    k_direction<double, RP><<<ll.grid, ll.block, 0, b>>>(L, k, h->dS);
+    k_apply_dot<DIM, double><<<lc.grid, lc.block, 0, b>>>(L, k, h->dS, part);
     k_update<double, RP><<<lu.grid, lu.block, 0, b>>>(L, k, h->dS, part, hc);
   } else {
-    k_direction_apply<DIM, RP, RP><<<lc.grid, lc.block, 0, b>>>(L, k, h->dS, part);
+    k_direction<RP, RP><<<ll.grid, ll.block, 0, b>>>(L, k, h->dS);
+    k_apply_dot<DIM, RP><<<lc.grid, lc.block, 0, b>>>(L, k, h->dS, part);
     k_update<RP, RP><<<lu.grid, lu.block, 0, b>>>(L, k, h->dS, part, hc);
   }
   cudaGraph_t out;
@@ -2368,8 +2518,50 @@ int build_graph_t(msrcg_hier* h) {
   return rc;
 }
 
+// Tile side and grid of the blocked smoothing of each wide level (2D, red-black
+// SGS, 1 <= m <= 4, not disabled by plain_sweeps): the larger side while it
+// gives at least two tiles per SM, the half side for levels of 16384 cells
+// and more, else one pass per half-sweep.  Sets the kernels' shared-memory
+// attribute on the current device.
+template <typename RP>
+int plan_tiles(msrcg_hier* h) {
+  const int m = h->o.m;
+  for (int k = 0; k < h->nlev; ++k) h->tile_tw[k] = 0;
+  if (h->dim != 2 || h->o.splitting != 0 || h->o.plain_sweeps || m < 1 || m > 4) return MSRCG_OK;
+  const int big = sizeof(RP) == 4 ? 64 : 48;
+  for (int k = 0; k < h->ks && k + 1 < h->nlev; ++k) {
+    const int nx = h->dims[k][0], ny = h->dims[k][1];
+    auto tiles = [&](int tw) { return (long long)((nx + tw - 1) / tw) * ((ny + tw - 1) / tw); };
+    int tw = 0;
+    if (tiles(big) >= 2LL * h->sms) tw = big;
+    else if ((long long)nx * ny >= 16384) tw = big / 2;
+    if (!tw) continue;
+    const size_t smem = tile_smem_bytes<RP>(tw, m);
+    int per = 0;
+    if (k == 0) {
+      MSRCG_CUDA_TRY(cudaFuncSetAttribute(k_smooth_tile<RP, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      MSRCG_CUDA_TRY(cudaFuncSetAttribute(k_smooth_tile<RP, double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      MSRCG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_smooth_tile<RP, double, false>, 512, smem));
+    } else {
+      MSRCG_CUDA_TRY(cudaFuncSetAttribute(k_smooth_tile<RP, RP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      MSRCG_CUDA_TRY(cudaFuncSetAttribute(k_smooth_tile<RP, RP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      MSRCG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_smooth_tile<RP, RP, false>, 512, smem));
+    }
+    if (per < 1) continue;
+    // one partial per CTA in the level's share of the reduction buffer
+    const long long grid = std::min<long long>({tiles(tw), (long long)h->sms * per, (long long)kMaxGrid});
+    h->tile_tw[k] = tw;
+    h->tile_grid[k] = (int)grid;
+  }
+  return MSRCG_OK;
+}
+
 int build_graph(msrcg_hier* h) {
   const bool f32 = h->o.precision == 1;
+  {
+    const int rc = f32 ? plan_tiles<float>(h) : plan_tiles<double>(h);
+    if (rc) return rc;
+  }
   h->sub_smem = levels_smem(h, h->ks, false);
   if (h->dim == 2) return f32 ? build_graph_t<2, float>(h) : build_graph_t<2, double>(h);
   return f32 ? build_graph_t<3, float>(h) : build_graph_t<3, double>(h);
@@ -2516,7 +2708,6 @@ int scrub(msrcg_hier* h, cudaStream_t s) {
     for (int v = 0; v < 4; ++v) MSRCG_CUDA_TRY(cudaMemsetAsync(v4[v], 0, vsz * L.npad, s));
     MSRCG_CUDA_TRY(cudaMemsetAsync(L.z, 0, rsz * L.npad, s));
     MSRCG_CUDA_TRY(cudaMemsetAsync(L.t, 0, rsz * L.npad, s));
-    if (L.p2) MSRCG_CUDA_TRY(cudaMemsetAsync(L.p2, 0, vsz * L.npad, s));
   }
   MSRCG_CUDA_TRY(cudaMemsetAsync(h->b0, 0, sizeof(double) * h->hL[0].npad, s));
   return MSRCG_OK;
@@ -2741,7 +2932,9 @@ __global__ void k_fill_ones(DevLevel L, DevLevel C) {
 const char* const kProfNames[] = {
     "k_sweep (red-black half-sweep)", "k_sweep (first half-sweep, from zero)", "k_sweep_rho (last half-sweep + r.z)",
     "k_residual (t = rp - A z)", "k_restrict (r_c = R t)", "k_prolong_black (z += E x_c, black cells)",
-    "k_direction_apply (p = z + beta p, q = A p, p.q)", "k_update (x += alpha p, r -= alpha q, r.r)"};
+    "k_direction (p = z + beta p)", "k_apply_dot (q = A p, p.q)", "k_update (x += alpha p, r -= alpha q, r.r)",
+    "k_smooth_tile pre (2m+1 half-sweeps from zero + residual, blocked)",
+    "k_prolong_to_t (t = z + E x_c on black cells)", "k_smooth_tile post (2m+1 half-sweeps + r.z, blocked)"};
 constexpr int kProfCount = (int)(sizeof(kProfNames) / sizeof(kProfNames[0]));
 
 template <int DIM, typename RP, typename V>
@@ -2772,13 +2965,25 @@ int profile_level_t(msrcg_hier* h, int k, int reps, cudaStream_t s, double* ms, 
       (d + 3.0) * n * rsz,                                    // T, rp, z, t
       (n + nc) * rsz,                                         // t, r_c
       (n + nc) * rsz,                                         // x_c, black z read and written
-      n * rsz + (d + 3.0) * n * vsz,                          // z, old p, T (vector precision); p, q written
-      6.0 * n * vsz};                                         // x, p, r, q read; x, r written
+      n * rsz + 2.0 * n * vsz,                                // z, p read, p written
+      (d + 2.0) * n * vsz,                                    // T (vector precision), p, q
+      6.0 * n * vsz,                                          // x, p, r, q read; x, r written
+      d * n * rsz + n * vsz + (vsz != rsz ? n * rsz : 0.0) + 2.0 * n * rsz,  // T, r; (rp), z, t written
+      (2.0 * n + nc) * rsz,                                   // z, x_c read; t written
+      (d + 3.0) * n * rsz + n * vsz};                         // T, rp, t, r read; z written
   cudaEvent_t e0, e1;
   MSRCG_CUDA_TRY(cudaEventCreate(&e0));
   MSRCG_CUDA_TRY(cudaEventCreate(&e1));
   int rc = MSRCG_OK;
+  const int m = h->o.m;
+  if (DIM == 2 && !rc) rc = plan_tiles<RP>(h);
+  const int tw = DIM == 2 ? h->tile_tw[k] : 0;
   for (int id = 0; id < kProfCount && !rc; ++id) {
+    if ((id == 9 || id == 11) && !tw) {  // no blocked smoothing on this level
+      ms[id] = 0.0;
+      bytes[id] = 0.0;
+      continue;
+    }
     auto launch = [&]() {
       switch (id) {
         case 0: k_sweep<DIM, RP, V><<<lp.grid, lp.block, 0, s>>>(L, 0, 0); break;
@@ -2787,8 +2992,16 @@ int profile_level_t(msrcg_hier* h, int k, int reps, cudaStream_t s, double* ms, 
         case 3: k_residual<DIM, RP><<<lc.grid, lc.block, 0, s>>>(L); break;
         case 4: launch_restrict<DIM, RP>(h, k, gmax, s); break;
         case 5: k_prolong_black<DIM, RP><<<lp.grid, lp.block, 0, s>>>(L, C); break;
-        case 6: k_direction_apply<DIM, V, RP><<<lc.grid, lc.block, 0, s>>>(L, k, S, part); break;
-        default: k_update<V, RP><<<lu.grid, lu.block, 0, s>>>(L, k, S, part, 0, 0); break;
+        case 6: k_direction<V, RP><<<ll.grid, ll.block, 0, s>>>(L, k, S); break;
+        case 7: k_apply_dot<DIM, V><<<lc.grid, lc.block, 0, s>>>(L, k, S, part); break;
+        case 8: k_update<V, RP><<<lu.grid, lu.block, 0, s>>>(L, k, S, part, 0, 0); break;
+        case 9:
+          k_smooth_tile<RP, V, true><<<h->tile_grid[k], 512, tile_smem_bytes<RP>(tw, m), s>>>(L, m, tw, k, S, part);
+          break;
+        case 10: k_prolong_to_t<DIM, RP><<<lc.grid, lc.block, 0, s>>>(L, C); break;
+        default:
+          k_smooth_tile<RP, V, false><<<h->tile_grid[k], 512, tile_smem_bytes<RP>(tw, m), s>>>(L, m, tw, k, S, part);
+          break;
       }
     };
     k_fill_ones<DIM, RP, V><<<lc.grid, lc.block, 0, s>>>(L, C);
@@ -2798,7 +3011,7 @@ int profile_level_t(msrcg_hier* h, int k, int reps, cudaStream_t s, double* ms, 
     for (int r = 0; r < reps && !rc; ++r) {
       launch();
       // keep the state live for the next launch (the update counts iterations)
-      if (id == 7 && cudaMemcpyAsync(S, &st, sizeof(st), cudaMemcpyHostToDevice, s) != cudaSuccess) rc = MSRCG_ECUDA;
+      if (id == 8 && cudaMemcpyAsync(S, &st, sizeof(st), cudaMemcpyHostToDevice, s) != cudaSuccess) rc = MSRCG_ECUDA;
     }
     if (!rc && cudaEventRecord(e1, s) != cudaSuccess) rc = MSRCG_ECUDA;
     if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = MSRCG_ECUDA;
