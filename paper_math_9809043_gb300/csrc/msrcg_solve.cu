@@ -1962,16 +1962,14 @@ __global__ void __launch_bounds__(512) k_smooth_tile(DevLevel L, int m, int TW, 
     const int WR = x1 - x0, HR = y1 - y0, SW = WR + 2;
     __syncthreads();  // the previous tile's last reads are done
     // ---- copy the region (and zero the ring of z / rp) ----
-    for (int e = threadIdx.x; e < (WR + 1) * HR; e += blockDim.x) {
-      const int b = e / (WR + 1), a = e - b * (WR + 1);
-      stx[e] = gTx[(nx + 1) * (y0 + b) + x0 + a];
-    }
-    for (int e = threadIdx.x; e < WR * (HR + 1); e += blockDim.x) {
-      const int b = e / WR, a = e - b * WR;
-      sty[e] = gTy[nx * (y0 + b) + x0 + a];
-    }
-    for (int e = threadIdx.x; e < SW * (HR + 2); e += blockDim.x) {
-      const int b = e / SW - 1, a = e - (b + 1) * SW - 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int b = warp; b < HR; b += nw)
+      for (int a = lane; a <= WR; a += 32) stx[b * (WR + 1) + a] = gTx[(nx + 1) * (y0 + b) + x0 + a];
+    for (int b = warp; b <= HR; b += nw)
+      for (int a = lane; a < WR; a += 32) sty[b * WR + a] = gTy[nx * (y0 + b) + x0 + a];
+    for (int bq = warp; bq < HR + 2; bq += nw)
+      for (int aq = lane; aq < SW; aq += 32) {
+      const int e = bq * SW + aq, b = bq - 1, a = aq - 1;
       const bool in = a >= 0 && a < WR && b >= 0 && b < HR;
       const int g = off + px * (y0 + b) + x0 + a;
       RP rv = 0, zv = 0;
@@ -1985,7 +1983,7 @@ __global__ void __launch_bounds__(512) k_smooth_tile(DevLevel L, int m, int TW, 
       }
       srp[e] = rv;
       sz[e] = zv;
-    }
+      }
     __syncthreads();
     // ---- half-sweeps: h = 0 red (from zero in pre), then black, red, ... ----
     for (int h = 0; h <= 2 * m; ++h) {
@@ -1994,11 +1992,11 @@ __global__ void __launch_bounds__(512) k_smooth_tile(DevLevel L, int m, int TW, 
       const int reach = 2 * m + 1 - h;
       const int ax0 = max(x0, X0 - reach) - x0, ax1 = min(x1, X1 + reach) - x0;
       const int by0 = max(y0, Y0 - reach) - y0, by1 = min(y1, Y1 + reach) - y0;
-      const int w = ax1 - ax0, hw = (w + 1) >> 1, rows = by1 - by0;
-      for (int e = threadIdx.x; e < hw * rows; e += blockDim.x) {
-        const int bb = e / hw, b = by0 + bb;
+      const int w = ax1 - ax0, hw = (w + 1) >> 1;
+      for (int b = by0 + warp; b < by1; b += nw)
+        for (int col = lane; col < hw; col += 32) {
         // cells of `colour` in region row b: global parity (x + y) & 1
-        const int a = ax0 + 2 * (e - bb * hw) + ((x0 + ax0 + y0 + b + colour) & 1);
+        const int a = ax0 + 2 * col + ((x0 + ax0 + y0 + b + colour) & 1);
         if (a >= ax1) continue;
         const int c = (b + 1) * SW + a + 1;
         const RP tw = stx[b * (WR + 1) + a], te = stx[b * (WR + 1) + a + 1];
@@ -2016,12 +2014,12 @@ __global__ void __launch_bounds__(512) k_smooth_tile(DevLevel L, int m, int TW, 
           v = quot<RP>(sm, d);
         }
         sz[c] = v;
-      }
+        }
       __syncthreads();
     }
     // ---- the tile's results ----
-    for (int e = threadIdx.x; e < (X1 - X0) * (Y1 - Y0); e += blockDim.x) {
-      const int yy = e / (X1 - X0), xx = e - yy * (X1 - X0);
+    for (int yy = warp; yy < Y1 - Y0; yy += nw)
+      for (int xx = lane; xx < X1 - X0; xx += 32) {
       const int a = X0 - x0 + xx, b = Y0 - y0 + yy;
       const int c = (b + 1) * SW + a + 1, g = off + px * (Y0 + yy) + X0 + xx;
       const RP zc = sz[c];
@@ -2034,7 +2032,7 @@ __global__ void __launch_bounds__(512) k_smooth_tile(DevLevel L, int m, int TW, 
       } else {
         acc += gr[g] * (V)zc;
       }
-    }
+      }
   }
   if (!PRE) grid_total(acc, partials, &S->ticket[k], [&](double rho) { set_rho_beta(S->lv[k], k, S, rho); });
 }
@@ -2529,6 +2527,16 @@ int plan_tiles(msrcg_hier* h) {
   for (int k = 0; k < h->nlev; ++k) h->tile_tw[k] = 0;
   if (h->dim != 2 || h->o.splitting != 0 || h->o.plain_sweeps || m < 1 || m > 4) return MSRCG_OK;
   const int big = sizeof(RP) == 4 ? 64 : 48;
+  // one attribute per kernel instantiation, which several levels share (in
+  // FP64 mode level 0 and the inner levels launch the same one): the
+  // largest tile's
+  {
+    const int smax = (int)tile_smem_bytes<RP>(big, m);
+    MSRCG_CUDA_TRY(cudaFuncSetAttribute(k_smooth_tile<RP, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
+    MSRCG_CUDA_TRY(cudaFuncSetAttribute(k_smooth_tile<RP, double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
+    MSRCG_CUDA_TRY(cudaFuncSetAttribute(k_smooth_tile<RP, RP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
+    MSRCG_CUDA_TRY(cudaFuncSetAttribute(k_smooth_tile<RP, RP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
+  }
   for (int k = 0; k < h->ks && k + 1 < h->nlev; ++k) {
     const int nx = h->dims[k][0], ny = h->dims[k][1];
     auto tiles = [&](int tw) { return (long long)((nx + tw - 1) / tw) * ((ny + tw - 1) / tw); };
@@ -2538,15 +2546,10 @@ int plan_tiles(msrcg_hier* h) {
     if (!tw) continue;
     const size_t smem = tile_smem_bytes<RP>(tw, m);
     int per = 0;
-    if (k == 0) {
-      MSRCG_CUDA_TRY(cudaFuncSetAttribute(k_smooth_tile<RP, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      MSRCG_CUDA_TRY(cudaFuncSetAttribute(k_smooth_tile<RP, double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (k == 0)
       MSRCG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_smooth_tile<RP, double, false>, 512, smem));
-    } else {
-      MSRCG_CUDA_TRY(cudaFuncSetAttribute(k_smooth_tile<RP, RP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      MSRCG_CUDA_TRY(cudaFuncSetAttribute(k_smooth_tile<RP, RP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    else
       MSRCG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_smooth_tile<RP, RP, false>, 512, smem));
-    }
     if (per < 1) continue;
     // one partial per CTA in the level's share of the reduction buffer
     const long long grid = std::min<long long>({tiles(tw), (long long)h->sms * per, (long long)kMaxGrid});
