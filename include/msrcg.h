@@ -305,10 +305,7 @@ int msrcg_solve_static(const msrcg_grid* grid, const double* K, int ncomp, const
  * (a static string; "" for a bad index), in this order: red-black half-sweep,
  * first half-sweep from zero, last half-sweep with r.z, residual,
  * restriction, prolongation onto the black cells, CG direction, operator
- * apply with p.q, CG update with r.r, and the blocked smoothing of a
- * 2D level: pre-smoothing with the residual, prolongation into t,
- * post-smoothing with r.z (these three report 0 ms and 0 bytes on a level
- * without blocked smoothing). */
+ * apply with p.q, CG update with r.r. */
 int msrcg_profile_kernel_count(void);
 const char* msrcg_profile_kernel_name(int i);
 

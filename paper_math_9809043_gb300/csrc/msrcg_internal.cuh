@@ -167,10 +167,6 @@ struct msrcg_hier {
   // tiled kernel (3D, or the tile does not fit the shared memory)
   int rfx[MSRCG_MAXLEV] = {}, rfy[MSRCG_MAXLEV] = {};
   int rtj = 0;
-  // blocked smoothing of a wide 2D level: tile side (0 = one pass per
-  // half-sweep) and CTAs of its launch
-  int tile_tw[MSRCG_MAXLEV] = {};
-  int tile_grid[MSRCG_MAXLEV] = {};
 };
 
 // allocation helper: records the buffer in h->allocs

@@ -1912,145 +1912,6 @@ __global__ void k_restrict(DevLevel L, DevLevel C) {
                  [&](int i, const Row& rw) { rc[rw.pc + i] = restrict_value<DIM, RP>(L, t, i, rw.j, rw.k); });
 }
 
-// ---------------------------------------------------------------------------
-// Temporally blocked smoothing of a wide 2D level (red-black SGS)
-// ---------------------------------------------------------------------------
-// One CTA smooths a tile of TW x TW cells: it copies the tile and a halo of
-// H = 2m+2 cells (face transmissibilities, right-hand side, iterate) into
-// shared memory, runs all 2m+1 half-sweeps there -- each on the cells that
-// can still influence the tile, a ring narrower per half-sweep -- and writes
-// the tile's results.  A halo value goes stale one cell further inward per
-// half-sweep, and the tile lies H > 2m+1 cells inside the copied region, so
-// every tile cell takes exactly the values of the plain half-sweep order
-// (same arithmetic helpers, same order of terms).  Each array crosses HBM
-// about once per smoothing instead of once per half-sweep.
-//   pre  (from zero): z = rp/D on red cells (rp = r rounded into the smoother
-//        precision, written out), 2m more half-sweeps; writes z, t = rp - A z.
-//   post: reads the prolonged iterate from t (written by k_prolong_to_t, so
-//        that no tile reads a halo another tile has overwritten), 2m+1
-//        half-sweeps; writes z and returns rho = r . z (and beta).
-// The CTA loops over tiles (grid <= tiles).
-template <typename RP>
-__host__ __device__ __forceinline__ size_t tile_smem_bytes(int TW, int m) {
-  const int WM = TW + 2 * (2 * m + 2);
-  return sizeof(RP) * (2 * (size_t)(WM + 2) * (WM + 2) + 2 * (size_t)WM * (WM + 1));
-}
-
-template <typename RP, typename V, bool PRE>
-__global__ void __launch_bounds__(512) k_smooth_tile(DevLevel L, int m, int TW, int k, SolveState* S,
-                                                    double* partials) {
-  extern __shared__ __align__(16) unsigned char tsm[];
-  const int H = 2 * m + 2, WM = TW + 2 * H, SM = WM + 2;
-  RP* sz = (RP*)tsm;              // iterate, with a zero ring: (b+1)*SW + a+1
-  RP* srp = sz + SM * SM;         // right-hand side, same layout
-  RP* stx = srp + SM * SM;        // x-faces of the region rows: b*(WR+1) + a
-  RP* sty = stx + WM * (WM + 1);  // y-faces: b*WR + a, b = 0..HR
-  const int nx = L.nx, ny = L.ny, px = L.px, off = (int)L.off;
-  const RP* gTx = (const RP*)L.T[0];
-  const RP* gTy = (const RP*)L.T[1];
-  const V* gr = (const V*)L.r;
-  RP* grp = (RP*)L.rp;
-  const RP* gin = PRE ? nullptr : (const RP*)L.t;
-  RP* gz = (RP*)L.z;
-  RP* gt = (RP*)L.t;
-  const int tx = (nx + TW - 1) / TW, ntiles = tx * ((ny + TW - 1) / TW);
-  V acc = 0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int X0 = (tile % tx) * TW, Y0 = (tile / tx) * TW;
-    const int X1 = min(nx, X0 + TW), Y1 = min(ny, Y0 + TW);  // the tile: [X0, X1) x [Y0, Y1)
-    const int x0 = max(0, X0 - H), x1 = min(nx, X1 + H), y0 = max(0, Y0 - H), y1 = min(ny, Y1 + H);
-    const int WR = x1 - x0, HR = y1 - y0, SW = WR + 2;
-    __syncthreads();  // the previous tile's last reads are done
-    // ---- copy the region (and zero the ring of z / rp) ----
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int b = warp; b < HR; b += nw)
-      for (int a = lane; a <= WR; a += 32) stx[b * (WR + 1) + a] = gTx[(nx + 1) * (y0 + b) + x0 + a];
-    for (int b = warp; b <= HR; b += nw)
-      for (int a = lane; a < WR; a += 32) sty[b * WR + a] = gTy[nx * (y0 + b) + x0 + a];
-    for (int bq = warp; bq < HR + 2; bq += nw)
-      for (int aq = lane; aq < SW; aq += 32) {
-      const int e = bq * SW + aq, b = bq - 1, a = aq - 1;
-      const bool in = a >= 0 && a < WR && b >= 0 && b < HR;
-      const int g = off + px * (y0 + b) + x0 + a;
-      RP rv = 0, zv = 0;
-      if (in) {
-        if (PRE) {
-          rv = (RP)gr[g];  // r rounded into the smoother precision (or rp itself)
-        } else {
-          rv = grp[g];
-          zv = gin[g];
-        }
-      }
-      srp[e] = rv;
-      sz[e] = zv;
-      }
-    __syncthreads();
-    // ---- half-sweeps: h = 0 red (from zero in pre), then black, red, ... ----
-    for (int h = 0; h <= 2 * m; ++h) {
-      const int colour = h & 1;
-      // cells within distance 2m+1-h of the tile still matter
-      const int reach = 2 * m + 1 - h;
-      const int ax0 = max(x0, X0 - reach) - x0, ax1 = min(x1, X1 + reach) - x0;
-      const int by0 = max(y0, Y0 - reach) - y0, by1 = min(y1, Y1 + reach) - y0;
-      const int w = ax1 - ax0, hw = (w + 1) >> 1;
-      for (int b = by0 + warp; b < by1; b += nw)
-        for (int col = lane; col < hw; col += 32) {
-        // cells of `colour` in region row b: global parity (x + y) & 1
-        const int a = ax0 + 2 * col + ((x0 + ax0 + y0 + b + colour) & 1);
-        if (a >= ax1) continue;
-        const int c = (b + 1) * SW + a + 1;
-        const RP tw = stx[b * (WR + 1) + a], te = stx[b * (WR + 1) + a + 1];
-        const RP ts = sty[b * WR + a], tn = sty[(b + 1) * WR + a];
-        RP v;
-        if (PRE && h == 0) {
-          RP d = tw;
-          d += te;
-          d += ts;
-          d += tn;
-          v = quot<RP>(srp[c], d);
-        } else {
-          RP d, sm = srp[c];
-          gs_terms2<RP>(d, sm, tw, te, ts, tn, sz[c - 1], sz[c + 1], sz[c - SW], sz[c + SW]);
-          v = quot<RP>(sm, d);
-        }
-        sz[c] = v;
-        }
-      __syncthreads();
-    }
-    // ---- the tile's results ----
-    for (int yy = warp; yy < Y1 - Y0; yy += nw)
-      for (int xx = lane; xx < X1 - X0; xx += 32) {
-      const int a = X0 - x0 + xx, b = Y0 - y0 + yy;
-      const int c = (b + 1) * SW + a + 1, g = off + px * (Y0 + yy) + X0 + xx;
-      const RP zc = sz[c];
-      gz[g] = zc;
-      if (PRE) {
-        const RP av = apply_terms2<RP>(stx[b * (WR + 1) + a], stx[b * (WR + 1) + a + 1], sty[b * WR + a],
-                                       sty[(b + 1) * WR + a], zc, sz[c - 1], sz[c + 1], sz[c - SW], sz[c + SW]);
-        gt[g] = srp[c] - av;
-        if (sizeof(V) != sizeof(RP)) grp[g] = srp[c];
-      } else {
-        acc += gr[g] * (V)zc;
-      }
-      }
-  }
-  if (!PRE) grid_total(acc, partials, &S->ticket[k], [&](double rho) { set_rho_beta(S->lv[k], k, S, rho); });
-}
-
-// t = z + E x_c on the black cells, t = z on the red ones: the prolonged
-// iterate that the blocked post-smoothing reads (see k_smooth_tile)
-template <int DIM, typename RP>
-__global__ void k_prolong_to_t(DevLevel L, DevLevel C) {
-  const RP* xc = (const RP*)C.x;
-  const RP* z = (const RP*)L.z;
-  RP* t = (RP*)L.t;
-  for_cells<DIM>(grid_map(), L, [&](int i, const Row& rw) {
-    const int c = rw.pc + i;
-    const RP zv = z[c];
-    t[c] = ((i + rw.j + rw.k) & 1) ? zv + prolong_value<DIM, RP>(L, C, xc, i, rw.j, rw.k) : zv;
-  });
-}
-
 // z += E x_c on the black cells (see Ops::prolong_postsmooth)
 template <int DIM, typename RP>
 __global__ void k_prolong_black(DevLevel L, DevLevel C) {
@@ -2393,14 +2254,8 @@ void emit_precond(Emit& E, int k, cudaStream_t s) {
   const int gmax = std::min(h->sms * 8, kMaxGrid);
   const Launch lc = cells_launch(L, gmax), lp = pairs_launch(L, gmax);
   const int m = h->o.m;
-  const int tw = h->tile_tw[k];
-  const size_t tsm = tw ? tile_smem_bytes<RP>(tw, m) : 0;
-  double* part = h->partials + (size_t)k * kMaxGrid;
   // pre-smoothing from zero, residual, restriction
-  if (tw) {
-    if (k == 0) k_smooth_tile<RP, double, true><<<h->tile_grid[k], 512, tsm, s>>>(L, m, tw, k, h->dS, part);
-    else k_smooth_tile<RP, RP, true><<<h->tile_grid[k], 512, tsm, s>>>(L, m, tw, k, h->dS, part);
-  } else if (k == 0) {
+  if (k == 0) {
     emit_smooth<DIM, RP, double>(L, m, true, false, k, h, gmax, s);
     k_residual<DIM, RP><<<lc.grid, lc.block, 0, s>>>(L);
   } else {
@@ -2413,12 +2268,6 @@ void emit_precond(Emit& E, int k, cudaStream_t s) {
   else k_small<DIM, RP><<<1, kSmallThreads, h->sub_smem, s>>>(h->dP, nullptr, 1, k + 1, 0, nullptr, h->sub_smem);
   // prolongation (black cells; every cell for the Jacobi smoother) and
   // post-smoothing with rho = r . z
-  if (tw) {
-    k_prolong_to_t<DIM, RP><<<lc.grid, lc.block, 0, s>>>(L, C);
-    if (k == 0) k_smooth_tile<RP, double, false><<<h->tile_grid[k], 512, tsm, s>>>(L, m, tw, k, h->dS, part);
-    else k_smooth_tile<RP, RP, false><<<h->tile_grid[k], 512, tsm, s>>>(L, m, tw, k, h->dS, part);
-    return;
-  }
   if (h->o.splitting == 1) k_prolong_all<DIM, RP><<<lc.grid, lc.block, 0, s>>>(L, C);
   else k_prolong_black<DIM, RP><<<lp.grid, lp.block, 0, s>>>(L, C);
   if (k == 0) emit_smooth<DIM, RP, double>(L, m, false, true, k, h, gmax, s);
@@ -2516,55 +2365,8 @@ int build_graph_t(msrcg_hier* h) {
   return rc;
 }
 
-// Tile side and grid of the blocked smoothing of each wide level (2D, red-black
-// SGS, 1 <= m <= 4, not disabled by plain_sweeps): the larger side while it
-// gives at least two tiles per SM, the half side for levels of 16384 cells
-// and more, else one pass per half-sweep.  Sets the kernels' shared-memory
-// attribute on the current device.
-template <typename RP>
-int plan_tiles(msrcg_hier* h) {
-  const int m = h->o.m;
-  for (int k = 0; k < h->nlev; ++k) h->tile_tw[k] = 0;
-  if (h->dim != 2 || h->o.splitting != 0 || h->o.plain_sweeps || m < 1 || m > 4) return MSRCG_OK;
-  const int big = sizeof(RP) == 4 ? 64 : 48;
-  // one attribute per kernel instantiation, which several levels share (in
-  // FP64 mode level 0 and the inner levels launch the same one): the
-  // largest tile's
-  {
-    const int smax = (int)tile_smem_bytes<RP>(big, m);
-    MSRCG_CUDA_TRY(cudaFuncSetAttribute(k_smooth_tile<RP, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
-    MSRCG_CUDA_TRY(cudaFuncSetAttribute(k_smooth_tile<RP, double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
-    MSRCG_CUDA_TRY(cudaFuncSetAttribute(k_smooth_tile<RP, RP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
-    MSRCG_CUDA_TRY(cudaFuncSetAttribute(k_smooth_tile<RP, RP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
-  }
-  for (int k = 0; k < h->ks && k + 1 < h->nlev; ++k) {
-    const int nx = h->dims[k][0], ny = h->dims[k][1];
-    auto tiles = [&](int tw) { return (long long)((nx + tw - 1) / tw) * ((ny + tw - 1) / tw); };
-    int tw = 0;
-    if (tiles(big) >= 2LL * h->sms) tw = big;
-    else if ((long long)nx * ny >= 16384) tw = big / 2;
-    if (!tw) continue;
-    const size_t smem = tile_smem_bytes<RP>(tw, m);
-    int per = 0;
-    if (k == 0)
-      MSRCG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_smooth_tile<RP, double, false>, 512, smem));
-    else
-      MSRCG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_smooth_tile<RP, RP, false>, 512, smem));
-    if (per < 1) continue;
-    // one partial per CTA in the level's share of the reduction buffer
-    const long long grid = std::min<long long>({tiles(tw), (long long)h->sms * per, (long long)kMaxGrid});
-    h->tile_tw[k] = tw;
-    h->tile_grid[k] = (int)grid;
-  }
-  return MSRCG_OK;
-}
-
 int build_graph(msrcg_hier* h) {
   const bool f32 = h->o.precision == 1;
-  {
-    const int rc = f32 ? plan_tiles<float>(h) : plan_tiles<double>(h);
-    if (rc) return rc;
-  }
   h->sub_smem = levels_smem(h, h->ks, false);
   if (h->dim == 2) return f32 ? build_graph_t<2, float>(h) : build_graph_t<2, double>(h);
   return f32 ? build_graph_t<3, float>(h) : build_graph_t<3, double>(h);
@@ -2935,9 +2737,7 @@ __global__ void k_fill_ones(DevLevel L, DevLevel C) {
 const char* const kProfNames[] = {
     "k_sweep (red-black half-sweep)", "k_sweep (first half-sweep, from zero)", "k_sweep_rho (last half-sweep + r.z)",
     "k_residual (t = rp - A z)", "k_restrict (r_c = R t)", "k_prolong_black (z += E x_c, black cells)",
-    "k_direction (p = z + beta p)", "k_apply_dot (q = A p, p.q)", "k_update (x += alpha p, r -= alpha q, r.r)",
-    "k_smooth_tile pre (2m+1 half-sweeps from zero + residual, blocked)",
-    "k_prolong_to_t (t = z + E x_c on black cells)", "k_smooth_tile post (2m+1 half-sweeps + r.z, blocked)"};
+    "k_direction (p = z + beta p)", "k_apply_dot (q = A p, p.q)", "k_update (x += alpha p, r -= alpha q, r.r)"};
 constexpr int kProfCount = (int)(sizeof(kProfNames) / sizeof(kProfNames[0]));
 
 template <int DIM, typename RP, typename V>
@@ -2970,23 +2770,12 @@ int profile_level_t(msrcg_hier* h, int k, int reps, cudaStream_t s, double* ms, 
       (n + nc) * rsz,                                         // x_c, black z read and written
       n * rsz + 2.0 * n * vsz,                                // z, p read, p written
       (d + 2.0) * n * vsz,                                    // T (vector precision), p, q
-      6.0 * n * vsz,                                          // x, p, r, q read; x, r written
-      d * n * rsz + n * vsz + (vsz != rsz ? n * rsz : 0.0) + 2.0 * n * rsz,  // T, r; (rp), z, t written
-      (2.0 * n + nc) * rsz,                                   // z, x_c read; t written
-      (d + 3.0) * n * rsz + n * vsz};                         // T, rp, t, r read; z written
+      6.0 * n * vsz};                                         // x, p, r, q read; x, r written
   cudaEvent_t e0, e1;
   MSRCG_CUDA_TRY(cudaEventCreate(&e0));
   MSRCG_CUDA_TRY(cudaEventCreate(&e1));
   int rc = MSRCG_OK;
-  const int m = h->o.m;
-  if (DIM == 2 && !rc) rc = plan_tiles<RP>(h);
-  const int tw = DIM == 2 ? h->tile_tw[k] : 0;
   for (int id = 0; id < kProfCount && !rc; ++id) {
-    if ((id == 9 || id == 11) && !tw) {  // no blocked smoothing on this level
-      ms[id] = 0.0;
-      bytes[id] = 0.0;
-      continue;
-    }
     auto launch = [&]() {
       switch (id) {
         case 0: k_sweep<DIM, RP, V><<<lp.grid, lp.block, 0, s>>>(L, 0, 0); break;
@@ -2997,14 +2786,7 @@ int profile_level_t(msrcg_hier* h, int k, int reps, cudaStream_t s, double* ms, 
         case 5: k_prolong_black<DIM, RP><<<lp.grid, lp.block, 0, s>>>(L, C); break;
         case 6: k_direction<V, RP><<<ll.grid, ll.block, 0, s>>>(L, k, S); break;
         case 7: k_apply_dot<DIM, V><<<lc.grid, lc.block, 0, s>>>(L, k, S, part); break;
-        case 8: k_update<V, RP><<<lu.grid, lu.block, 0, s>>>(L, k, S, part, 0, 0); break;
-        case 9:
-          k_smooth_tile<RP, V, true><<<h->tile_grid[k], 512, tile_smem_bytes<RP>(tw, m), s>>>(L, m, tw, k, S, part);
-          break;
-        case 10: k_prolong_to_t<DIM, RP><<<lc.grid, lc.block, 0, s>>>(L, C); break;
-        default:
-          k_smooth_tile<RP, V, false><<<h->tile_grid[k], 512, tile_smem_bytes<RP>(tw, m), s>>>(L, m, tw, k, S, part);
-          break;
+        default: k_update<V, RP><<<lu.grid, lu.block, 0, s>>>(L, k, S, part, 0, 0); break;
       }
     };
     k_fill_ones<DIM, RP, V><<<lc.grid, lc.block, 0, s>>>(L, C);
