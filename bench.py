@@ -529,6 +529,39 @@ def run_wide_kernels(args, M, P, dev, stream, peak):
     return out
 
 
+def run_laplace(args, M, P, dev, stream, nb):
+    """The constant-coefficient solver (msrcg_build_laplace, Sec. 4.1): nb
+    concurrent 1024^2 problems, K = 1, the headline's boundary types and
+    N(0,1) sources, both precisions: solves/s, ns per unknown, iterations and
+    the device bytes of one hierarchy (against the cell-K build's)."""
+    import numpy as np
+    import torch
+    n = args.size
+    bc, gD = P.standard_bc(2, (n, n))
+    out = {"workload": f"{nb} concurrent {n}^2 problems, constant K = 1, Dirichlet x / no-flow y (lifted), "
+                       "N(0,1) source"}
+    for prec, key in ((1, "fp32_precond"), (0, "fp64_plain")):
+        if prec == 0 and args.no_fp64:
+            continue
+        opts = M.default_opts(precision=prec, inner_floor=1e-6 if prec else 0.0)
+        hs, bs = [], []
+        for j in range(nb):
+            prob = P.Problem(dim=2, n=(n, n), h=(1.0 / n, 1.0 / n), K=np.ones((1, n * n)), bc=bc, gD=gD,
+                             f=np.random.default_rng(1007 * 1000 + j).standard_normal(n * n),
+                             pbf=P.linear_lifting(2, (n, n)))
+            h = M.Hierarchy.laplace(2, prob.n, prob.h, 1.0, [1, 1, 0, 0, 0, 0], opts, device=dev)
+            hs.append(h)
+            bs.append(h.rhs_for(prob))
+        per, sts = _timed_batch(M, hs, bs, 2, stream, dev)
+        ms = statistics.mean(per)
+        out[key] = {"solves_per_s": nb / (ms / 1e3), "ns_per_unknown": ms * 1e6 / (nb * n * n), "ms_per_batch": ms,
+                    "iters": sts[0]["iters"], "status": sorted({s["status"] for s in sts}),
+                    "relres_true_max": max(s["relres_true"] for s in sts), "device_bytes": hs[0].device_bytes()}
+        del hs, bs
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_stall_path(args, M, P, dev, stream):
     """The layered channel field at 32^3 with the FP32 preconditioner: the
     plain beta stalls; the stall test switches to the flexible beta and then
@@ -766,10 +799,11 @@ def main():
         torch.cuda.empty_cache()
 
     # ---- other workloads: uneven batch and 3D (rank 0 only) ----
-    uneven = grid3d = jacobi = natural = strip = precs = stall = wide = None
+    uneven = grid3d = jacobi = natural = strip = precs = stall = wide = laplace = None
     if rank == 0 and not args.no_extra:
         wide = run_wide_kernels(args, M, P, dev, stream, peak)
         precs = run_preconditioners(args, M, P, dev, stream, nb)
+        laplace = run_laplace(args, M, P, dev, stream, nb)
         stall = run_stall_path(args, M, P, dev, stream)
         uneven = run_uneven(args, M, P, dev, stream)
         grid3d = run_3d(args, M, P, dev, stream, nb)
@@ -825,7 +859,7 @@ def main():
                 "status": statuses, "relres_true_max": relres, "iters": sts[0]["iters"],
                 "latency_ms": latency, "fp64_plain": fp64, "uneven_batch": uneven, "grid3d": grid3d, "jacobi": jacobi,
                 "natural_order_sgs": natural, "anisotropic_strip": strip, "preconditioners": precs,
-                "stall_path": stall, "parity": parity, "wide_level_kernels": wide,
+                "stall_path": stall, "parity": parity, "wide_level_kernels": wide, "laplace": laplace,
                 "serving": serving, "e2e": e2e, "roofline": roofline,
                 "cpu_baseline": cpu, "clocks": ck, "gpu_launches": args.steps}
         print(json.dumps(line), flush=True)

@@ -172,6 +172,28 @@ int msrcg_build(const msrcg_grid* grid, const double* K, int ncomp, const uint8_
 int msrcg_build_faces(const msrcg_grid* grid, const double* Kx, const double* Ky, const double* Kz,
                       const msrcg_opts* opts, void* stream, msrcg_hier** out);
 
+/* Build the hierarchy of a constant-coefficient problem (Sec. 4.1, the
+ * solver specialised to the Laplace operator): K the same in every cell,
+ * each side of the domain entirely Dirichlet or entirely Neumann.
+ *  grid     host; validated as msrcg_build.
+ *  K        host, 3 doubles: K_xx, K_yy (, K_zz) of every cell, > 0 (the
+ *           third ignored in 2D).
+ *  side_bc  host, 6 bytes: the boundary type of the sides x-low, x-high,
+ *           y-low, y-high, z-low, z-high (1 = Dirichlet, 0 = Neumann; the
+ *           z entries ignored in 2D).
+ *  Level k's interior faces all carry (h_perp/h_par) K of its cells (the
+ *  domain fixed, cells of size L/n_k), a Dirichlet face twice that, a Neumann
+ *  face 0: what the series-parallel coarsening of a constant field gives.
+ *  No face array is stored in full -- one x row, four y rows (and z planes)
+ *  per level -- so the smoother and the operator read almost no coefficient
+ *  data.  The result solves, applies and lifts as any hierarchy
+ *  (msrcg_get_trans returns the full arrays); msrcg_lift_rhs takes the
+ *  usual per-face boundary layout.  Synchronises `stream`.
+ *  Errors: MSRCG_EINVAL (bad grid, K <= 0, a side_bc entry > 1),
+ *  MSRCG_ENOMEM, MSRCG_ECUDA. */
+int msrcg_build_laplace(const msrcg_grid* grid, const double K[3], const uint8_t side_bc[6], const msrcg_opts* opts,
+                        void* stream, msrcg_hier** out);
+
 /* Right-hand side of the lifted problem, Sec. 3: with a field P_bf that
  * matches the boundary values, writes b = f*vol + g_D - A P_bf, where g_D
  * sums T_face * gD over the Dirichlet faces of each boundary cell.

@@ -307,35 +307,34 @@ __global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, 
 }
 
 // Dense operator of a (small) level: A[c][c] = sum of its face T,
-// A[c][nb] = -T_face.  Row-major n x n.
-__global__ void k_dense_assemble(int nx, int ny, int nz, const double* __restrict__ Tx, const double* __restrict__ Ty,
-                                 const double* __restrict__ Tz, double* __restrict__ A) {
+// A[c][nb] = -T_face.  Row-major n x n.  lap: compact face arrays.
+__global__ void k_dense_assemble(int nx, int ny, int nz, int lap, const double* __restrict__ Tx,
+                                 const double* __restrict__ Ty, const double* __restrict__ Tz, double* __restrict__ A) {
   const long long n = (long long)nx * ny * nz;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * n; e += (long long)gridDim.x * blockDim.x)
     A[e] = 0.0;
   __syncthreads();
   for (long long c = threadIdx.x; c < n; c += blockDim.x) {
     int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
-    long long row = j + (long long)ny * k;
     double d = 0.0, t;
-    t = Tx[c + row];
+    t = Tx[face_index(lap, 0, nx, ny, nz, i, j, k)];
     d += t;
     if (i > 0) A[c * n + c - 1] = -t;
-    t = Tx[c + row + 1];
+    t = Tx[face_index(lap, 0, nx, ny, nz, i + 1, j, k)];
     d += t;
     if (i < nx - 1) A[c * n + c + 1] = -t;
-    t = Ty[c + (long long)nx * k];
+    t = Ty[face_index(lap, 1, nx, ny, nz, i, j, k)];
     d += t;
     if (j > 0) A[c * n + c - nx] = -t;
-    t = Ty[c + (long long)nx * k + nx];
+    t = Ty[face_index(lap, 1, nx, ny, nz, i, j + 1, k)];
     d += t;
     if (j < ny - 1) A[c * n + c + nx] = -t;
     if (Tz) {
       long long pl = (long long)nx * ny;
-      t = Tz[c];
+      t = Tz[face_index(lap, 2, nx, ny, nz, i, j, k)];
       d += t;
       if (k > 0) A[c * n + c - pl] = -t;
-      t = Tz[c + pl];
+      t = Tz[face_index(lap, 2, nx, ny, nz, i, j, k + 1)];
       d += t;
       if (k < nz - 1) A[c * n + c + pl] = -t;
     }
@@ -381,35 +380,35 @@ __global__ void k_chol_inverse(int n, double* __restrict__ A, double* __restrict
 }
 
 // y = A x with FP64 transmissibilities: (A x)_c = sum_faces T (x_c - x_nb),
-// T x_c on a boundary face.
-__global__ void k_apply64(int nx, int ny, int nz, const double* __restrict__ Tx, const double* __restrict__ Ty,
+// T x_c on a boundary face.  lap: compact face arrays.
+__global__ void k_apply64(int nx, int ny, int nz, int lap, const double* __restrict__ Tx, const double* __restrict__ Ty,
                           const double* __restrict__ Tz, const double* __restrict__ x, double* __restrict__ y) {
   const long long n = (long long)nx * ny * nz;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
     int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
-    long long row = j + (long long)ny * k;
     double xc = x[c], s = 0.0, t;
-    t = Tx[c + row];
+    t = Tx[face_index(lap, 0, nx, ny, nz, i, j, k)];
     s += i > 0 ? t * (xc - x[c - 1]) : t * xc;
-    t = Tx[c + row + 1];
+    t = Tx[face_index(lap, 0, nx, ny, nz, i + 1, j, k)];
     s += i < nx - 1 ? t * (xc - x[c + 1]) : t * xc;
-    t = Ty[c + (long long)nx * k];
+    t = Ty[face_index(lap, 1, nx, ny, nz, i, j, k)];
     s += j > 0 ? t * (xc - x[c - nx]) : t * xc;
-    t = Ty[c + (long long)nx * k + nx];
+    t = Ty[face_index(lap, 1, nx, ny, nz, i, j + 1, k)];
     s += j < ny - 1 ? t * (xc - x[c + nx]) : t * xc;
     if (Tz) {
       long long pl = (long long)nx * ny;
-      t = Tz[c];
+      t = Tz[face_index(lap, 2, nx, ny, nz, i, j, k)];
       s += k > 0 ? t * (xc - x[c - pl]) : t * xc;
-      t = Tz[c + pl];
+      t = Tz[face_index(lap, 2, nx, ny, nz, i, j, k + 1)];
       s += k < nz - 1 ? t * (xc - x[c + pl]) : t * xc;
     }
     y[c] = s;
   }
 }
 
-// Lifted right-hand side, Sec. 3: b = f vol + g_D - A P_bf.
-__global__ void k_lift(int nx, int ny, int nz, const double* __restrict__ Tx, const double* __restrict__ Ty,
+// Lifted right-hand side, Sec. 3: b = f vol + g_D - A P_bf.  lap: compact
+// face arrays.
+__global__ void k_lift(int nx, int ny, int nz, int lap, const double* __restrict__ Tx, const double* __restrict__ Ty,
                        const double* __restrict__ Tz, const uint8_t* __restrict__ bc, const double* __restrict__ gD,
                        const double* __restrict__ f, double vol, const double* __restrict__ pbf, double* __restrict__ b) {
   const long long n = (long long)nx * ny * nz;
@@ -418,34 +417,44 @@ __global__ void k_lift(int nx, int ny, int nz, const double* __restrict__ Tx, co
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
     int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / nxy);
     long long row = j + (long long)ny * k;
+    const double tw = Tx[face_index(lap, 0, nx, ny, nz, i, j, k)], te = Tx[face_index(lap, 0, nx, ny, nz, i + 1, j, k)];
+    const double ts = Ty[face_index(lap, 1, nx, ny, nz, i, j, k)], tn = Ty[face_index(lap, 1, nx, ny, nz, i, j + 1, k)];
     double v = f ? f[c] * vol : 0.0;
-    if (i == 0 && bc[row]) v += Tx[c + row] * gD[row];
-    if (i == nx - 1 && bc[ox1 + row]) v += Tx[c + row + 1] * gD[ox1 + row];
+    if (i == 0 && bc[row]) v += tw * gD[row];
+    if (i == nx - 1 && bc[ox1 + row]) v += te * gD[ox1 + row];
     long long xz = i + (long long)nx * k;
-    if (j == 0 && bc[oy0 + xz]) v += Ty[c + (long long)nx * k] * gD[oy0 + xz];
-    if (j == ny - 1 && bc[oy1 + xz]) v += Ty[c + (long long)nx * k + nx] * gD[oy1 + xz];
+    if (j == 0 && bc[oy0 + xz]) v += ts * gD[oy0 + xz];
+    if (j == ny - 1 && bc[oy1 + xz]) v += tn * gD[oy1 + xz];
+    double tb = 0.0, tt = 0.0;
     if (Tz) {
+      tb = Tz[face_index(lap, 2, nx, ny, nz, i, j, k)];
+      tt = Tz[face_index(lap, 2, nx, ny, nz, i, j, k + 1)];
       long long xy = i + (long long)nx * j;
-      if (k == 0 && bc[oz0 + xy]) v += Tz[c] * gD[oz0 + xy];
-      if (k == nz - 1 && bc[oz1 + xy]) v += Tz[c + nxy] * gD[oz1 + xy];
+      if (k == 0 && bc[oz0 + xy]) v += tb * gD[oz0 + xy];
+      if (k == nz - 1 && bc[oz1 + xy]) v += tt * gD[oz1 + xy];
     }
     // A P_bf
-    double xc = pbf[c], s = 0.0, t;
-    t = Tx[c + row];
-    s += i > 0 ? t * (xc - pbf[c - 1]) : t * xc;
-    t = Tx[c + row + 1];
-    s += i < nx - 1 ? t * (xc - pbf[c + 1]) : t * xc;
-    t = Ty[c + (long long)nx * k];
-    s += j > 0 ? t * (xc - pbf[c - nx]) : t * xc;
-    t = Ty[c + (long long)nx * k + nx];
-    s += j < ny - 1 ? t * (xc - pbf[c + nx]) : t * xc;
+    double xc = pbf[c], s = 0.0;
+    s += i > 0 ? tw * (xc - pbf[c - 1]) : tw * xc;
+    s += i < nx - 1 ? te * (xc - pbf[c + 1]) : te * xc;
+    s += j > 0 ? ts * (xc - pbf[c - nx]) : ts * xc;
+    s += j < ny - 1 ? tn * (xc - pbf[c + nx]) : tn * xc;
     if (Tz) {
-      t = Tz[c];
-      s += k > 0 ? t * (xc - pbf[c - nxy]) : t * xc;
-      t = Tz[c + nxy];
-      s += k < nz - 1 ? t * (xc - pbf[c + nxy]) : t * xc;
+      s += k > 0 ? tb * (xc - pbf[c - nxy]) : tb * xc;
+      s += k < nz - 1 ? tt * (xc - pbf[c + nxy]) : tt * xc;
     }
     b[c] = v - s;
+  }
+}
+
+// Full face array of axis a of a constant-coefficient level from its compact
+// one (msrcg_get_trans).
+__global__ void k_expand_faces(int a, int nx, int ny, int nz, const double* __restrict__ Tc, double* __restrict__ T) {
+  const int fx = nx + (a == 0), fy = ny + (a == 1), fz = nz + (a == 2);
+  const long long nf = (long long)fx * fy * fz;
+  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf; f += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(f % fx), j = (int)((f / fx) % fy), k = (int)(f / ((long long)fx * fy));
+    T[f] = Tc[face_index(1, a, nx, ny, nz, i, j, k)];
   }
 }
 
@@ -547,6 +556,11 @@ struct Level0K {
   const uint8_t* bc = nullptr;
   const double* Kf[3] = {nullptr, nullptr, nullptr};
   const double* T0[3] = {nullptr, nullptr, nullptr};  // level-0 transmissibilities of another hierarchy
+  // constant coefficients: K per axis and the boundary type of each side
+  // (x-low, x-high, y-low, y-high, z-low, z-high; 1 = Dirichlet)
+  bool lap = false;
+  double lapK[3] = {0.0, 0.0, 0.0};
+  uint8_t lap_bc[6] = {0, 0, 0, 0, 0, 0};
 };
 int build_hier(const msrcg_grid* grid, const Level0K& src, const msrcg_opts* opts, cudaStream_t stream,
                cudaStream_t alloc_stream, msrcg_hier** out);
@@ -590,7 +604,13 @@ int msrcg_twin(msrcg_hier* h, cudaStream_t stream, msrcg_hier** out) {
     o.inner_floor = 0.0;
     o.escalate = 0;
     Level0K src;
-    for (int a = 0; a < h->dim; ++a) src.T0[a] = h->T64[0][a];
+    if (h->lap) {
+      src.lap = true;
+      for (int a = 0; a < 3; ++a) src.lapK[a] = h->lapK[a];
+      for (int e = 0; e < 6; ++e) src.lap_bc[e] = h->lap_bc[e];
+    } else {
+      for (int a = 0; a < h->dim; ++a) src.T0[a] = h->T64[0][a];
+    }
     // stream-ordered allocation (the server): build on the allocation stream,
     // so that every buffer exists before its first use; the build
     // synchronises that stream before it returns
@@ -599,6 +619,24 @@ int msrcg_twin(msrcg_hier* h, cudaStream_t stream, msrcg_hier** out) {
   }
   *out = h->twin;
   return MSRCG_OK;
+}
+
+extern "C" int msrcg_build_laplace(const msrcg_grid* grid, const double K[3], const uint8_t side_bc[6],
+                                   const msrcg_opts* opts, void* stream, msrcg_hier** out) {
+  if (!out) return MSRCG_EINVAL;
+  *out = nullptr;
+  if (!grid || !K || !side_bc || (grid->dim != 2 && grid->dim != 3)) return MSRCG_EINVAL;
+  Level0K src;
+  src.lap = true;
+  for (int a = 0; a < 3; ++a) {
+    src.lapK[a] = a < grid->dim ? K[a] : 0.0;
+    if (a < grid->dim && !(K[a] > 0.0 && isfinite(K[a]))) return MSRCG_EINVAL;
+  }
+  for (int e = 0; e < 6; ++e) {
+    if (side_bc[e] > 1) return MSRCG_EINVAL;
+    src.lap_bc[e] = e < 2 * grid->dim ? side_bc[e] : 0;
+  }
+  return build_hier(grid, src, opts, (cudaStream_t)stream, nullptr, out);
 }
 
 namespace {
@@ -661,16 +699,64 @@ int build_hier(const msrcg_grid* grid, const Level0K& src, const msrcg_opts* opt
   // ---- level 0 transmissibilities from cell K (A1) ----
   double hh[3] = {grid->h[0], grid->h[1], dim == 3 ? grid->h[2] : 1.0};
   double ratio[3] = {(hh[1] * hh[2]) / hh[0], (hh[0] * hh[2]) / hh[1], (hh[0] * hh[1]) / hh[2]};
+  h->lap = src.lap ? 1 : 0;
+  if (src.lap) {
+    for (int a = 0; a < 3; ++a) h->lapK[a] = src.lapK[a];
+    for (int e = 0; e < 6; ++e) h->lap_bc[e] = src.lap_bc[e];
+  }
+  // entries of level k's face array along axis a (compact when constant)
+  auto nfaces = [&](int k, int a) -> long long {
+    DevLevel t;
+    memset(&t, 0, sizeof(t));
+    t.nx = h->dims[k][0];
+    t.ny = h->dims[k][1];
+    t.nz = h->dims[k][2];
+    t.lap = h->lap;
+    return face_count(t, a);
+  };
   for (int k = 0; k < h->nlev; ++k) {
-    const int* d = h->dims[k];
     for (int a = 0; a < dim; ++a) {
-      long long nf = (long long)(d[0] + (a == 0)) * (d[1] + (a == 1)) * (d[2] + (a == 2));
       void* p;
-      if ((rc = msrcg_alloc(h, &p, sizeof(double) * nf))) return fail(rc);
+      if ((rc = msrcg_alloc(h, &p, sizeof(double) * nfaces(k, a)))) return fail(rc);
       h->T64[k][a] = (double*)p;
     }
   }
-  if (src.T0[0]) {
+  if (src.lap) {
+    // constant coefficients (Sec. 4.1, the Laplace specialisation): every
+    // level's interior faces carry (h_perp/h_par) K_face of that level's cells
+    // (the domain fixed, the cells of level k of size L_a / n_a(k); K_face the
+    // harmonic mean of two equal cells, formed as the cell-K build forms it),
+    // a Dirichlet boundary face 2 (h_perp/h_par) K, a Neumann face 0 -- the
+    // transmissibilities that the series-parallel coarsening of a constant
+    // field reproduces
+    std::vector<double> buf;
+    for (int k = 0; k < h->nlev; ++k) {
+      double hk[3];
+      for (int a = 0; a < 3; ++a) hk[a] = a < dim ? hh[a] * n3[a] / (double)h->dims[k][a] : 1.0;
+      const double rk[3] = {(hk[1] * hk[2]) / hk[0], (hk[0] * hk[2]) / hk[1], (hk[0] * hk[1]) / hk[2]};
+      for (int a = 0; a < dim; ++a) {
+        const double K = src.lapK[a];
+        const double c = K + K > 0.0 ? rk[a] * (2.0 * K * K / (K + K)) : 0.0;
+        const double lo = src.lap_bc[2 * a] ? rk[a] * (2.0 * K) : 0.0;
+        const double hi = src.lap_bc[2 * a + 1] ? rk[a] * (2.0 * K) : 0.0;
+        const int nx = h->dims[k][0], ny = h->dims[k][1], nz = h->dims[k][2];
+        buf.assign((size_t)nfaces(k, a), c);
+        if (a == 0) {
+          buf[0] = lo;
+          buf[nx] = hi;
+        } else {
+          const long long row = a == 1 ? nx : (long long)nx * ny;  // one compact row / plane
+          const int n = a == 1 ? ny : nz;
+          for (long long e = 0; e < row; ++e) {
+            buf[e] = lo;
+            buf[(size_t)row * (n == 1 ? 1 : 3) + e] = hi;
+          }
+        }
+        if (cudaMemcpy(h->T64[k][a], buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+          return fail(MSRCG_ECUDA);
+      }
+    }
+  } else if (src.T0[0]) {
     for (int a = 0; a < dim; ++a) {
       long long nf = (long long)(n3[0] + (a == 0)) * (n3[1] + (a == 1)) * (n3[2] + (a == 2));
       if (cudaMemcpyAsync(h->T64[0][a], src.T0[a], sizeof(double) * nf, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
@@ -693,7 +779,7 @@ int build_hier(const msrcg_grid* grid, const Level0K& src, const msrcg_opts* opt
     }
   }
   // ---- coarse transmissibilities (A2) ----
-  for (int k = 0; k + 1 < h->nlev; ++k) {
+  for (int k = 0; k + 1 < h->nlev && !h->lap; ++k) {
     int3 nf = make_int3(h->dims[k][0], h->dims[k][1], h->dims[k][2]);
     int3 nc = make_int3(h->dims[k + 1][0], h->dims[k + 1][1], h->dims[k + 1][2]);
     for (int a = 0; a < dim; ++a) {
@@ -705,8 +791,7 @@ int build_hier(const msrcg_grid* grid, const Level0K& src, const msrcg_opts* opt
   // ---- smoother-precision copies ----
   for (int k = 0; k < h->nlev; ++k)
     for (int a = 0; a < dim; ++a) {
-      const int* d = h->dims[k];
-      long long nf = (long long)(d[0] + (a == 0)) * (d[1] + (a == 1)) * (d[2] + (a == 2));
+      const long long nf = nfaces(k, a);
       if (f32) {
         void* p;
         if ((rc = msrcg_alloc(h, &p, sizeof(float) * nf))) return fail(rc);
@@ -735,6 +820,7 @@ int build_hier(const msrcg_grid* grid, const Level0K& src, const msrcg_opts* opt
       L.T[a] = h->TR[k][a];
       L.T64[a] = h->T64[k][a];
     }
+    L.lap = h->lap;
     L.fk = fk;
     fk *= o.f;
     L.maxit = k == 0 ? o.maxit_outer : o.maxit_inner;
@@ -821,8 +907,8 @@ int build_hier(const msrcg_grid* grid, const Level0K& src, const msrcg_opts* opt
     if ((rc = msrcg_alloc(h, &Ai, sizeof(double) * h->nc * h->nc))) return fail(rc);
     if ((rc = msrcg_alloc(h, &fl, sizeof(int)))) return fail(rc);
     MSRCG_CUDA_TRY(cudaMemsetAsync(fl, 0, sizeof(int), st));
-    k_dense_assemble<<<1, 512, 0, st>>>(h->dims[kc][0], h->dims[kc][1], h->dims[kc][2], h->T64[kc][0], h->T64[kc][1],
-                                        dim == 3 ? h->T64[kc][2] : nullptr, (double*)A);
+    k_dense_assemble<<<1, 512, 0, st>>>(h->dims[kc][0], h->dims[kc][1], h->dims[kc][2], h->lap, h->T64[kc][0],
+                                        h->T64[kc][1], dim == 3 ? h->T64[kc][2] : nullptr, (double*)A);
     k_chol_inverse<<<1, 512, 0, st>>>(h->nc, (double*)A, (double*)Ai, (int*)fl);
     int hf = 0;
     if (cudaMemcpyAsync(&hf, fl, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -925,7 +1011,8 @@ extern "C" int msrcg_lift_rhs(msrcg_hier* h, const uint8_t* bc, const double* gD
   const int* d = h->dims[0];
   const double vol = h->hsz[0] * h->hsz[1] * (h->dim == 3 ? h->hsz[2] : 1.0);
   k_lift<<<grid_for(h->N[0], 256, h->sms * 8), 256, 0, (cudaStream_t)stream>>>(
-      d[0], d[1], d[2], h->T64[0][0], h->T64[0][1], h->dim == 3 ? h->T64[0][2] : nullptr, bc, gD, f, vol, pbf, b);
+      d[0], d[1], d[2], h->lap, h->T64[0][0], h->T64[0][1], h->dim == 3 ? h->T64[0][2] : nullptr, bc, gD, f, vol, pbf,
+      b);
   MSRCG_CUDA_TRY(cudaGetLastError());
   return MSRCG_OK;
 }
@@ -945,8 +1032,14 @@ extern "C" int msrcg_get_trans(const msrcg_hier* h, int level, double* Tx, doubl
   double* outs[3] = {Tx, Ty, Tz};
   for (int a = 0; a < h->dim; ++a) {
     long long nf = (long long)(d[0] + (a == 0)) * (d[1] + (a == 1)) * (d[2] + (a == 2));
-    MSRCG_CUDA_TRY(cudaMemcpyAsync(outs[a], h->T64[level][a], sizeof(double) * nf, cudaMemcpyDeviceToDevice,
-                                   (cudaStream_t)stream));
+    if (h->lap) {
+      k_expand_faces<<<grid_for(nf, 256, h->sms * 8), 256, 0, (cudaStream_t)stream>>>(a, d[0], d[1], d[2],
+                                                                                       h->T64[level][a], outs[a]);
+      MSRCG_CUDA_TRY(cudaGetLastError());
+    } else {
+      MSRCG_CUDA_TRY(cudaMemcpyAsync(outs[a], h->T64[level][a], sizeof(double) * nf, cudaMemcpyDeviceToDevice,
+                                     (cudaStream_t)stream));
+    }
   }
   return MSRCG_OK;
 }
@@ -955,7 +1048,7 @@ extern "C" int msrcg_apply(const msrcg_hier* h, int level, const double* x, doub
   if (!h || level < 0 || level >= h->nlev || !x || !y) return MSRCG_EINVAL;
   const int* d = h->dims[level];
   k_apply64<<<grid_for(h->N[level], 256, h->sms * 8), 256, 0, (cudaStream_t)stream>>>(
-      d[0], d[1], d[2], h->T64[level][0], h->T64[level][1], h->dim == 3 ? h->T64[level][2] : nullptr, x, y);
+      d[0], d[1], d[2], h->lap, h->T64[level][0], h->T64[level][1], h->dim == 3 ? h->T64[level][2] : nullptr, x, y);
   MSRCG_CUDA_TRY(cudaGetLastError());
   return MSRCG_OK;
 }
@@ -1218,8 +1311,8 @@ int msrcg_build_into(msrcg_hier* h, const msrcg_grid* grid, const double* K, int
       return fail(MSRCG_ECUDA);
   }
   if (cudaMemsetAsync(fl, 0, sizeof(int), st) != cudaSuccess) return fail(MSRCG_ECUDA);
-  k_dense_assemble<<<1, 512, 0, st>>>(h->dims[kc][0], h->dims[kc][1], h->dims[kc][2], h->T64[kc][0], h->T64[kc][1],
-                                      dim == 3 ? h->T64[kc][2] : nullptr, A);
+  k_dense_assemble<<<1, 512, 0, st>>>(h->dims[kc][0], h->dims[kc][1], h->dims[kc][2], 0, h->T64[kc][0],
+                                      h->T64[kc][1], dim == 3 ? h->T64[kc][2] : nullptr, A);
   k_chol_inverse<<<1, 512, 0, st>>>(h->nc, A, Ai, fl);
   int hf = 0;
   if (cudaMemcpyAsync(&hf, fl, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||

@@ -75,8 +75,41 @@ struct DevLevel {
   void* rp;              // r in smoother precision (aliases r when the types agree)
   double fk;             // f^k of the level test
   int maxit;
-  int pad;
+  int lap;               // constant coefficients (msrcg_build_laplace): compact face arrays, see face_row
 };
+
+// Constant-coefficient levels keep compact face arrays: Tx one row of nx+1
+// faces (every row of x-faces is the same), Ty the face rows south boundary,
+// interior, interior, north boundary (nx each; two rows when ny = 1), Tz
+// the same four planes (nx*ny each).  Face row f of an axis with n cells
+// (f = 0..n) is stored in compact row face_row(f, n); the cell rows of
+// make_row address cell j's south face in row cell_row(j, n) and its north
+// face in the next row.
+__host__ __device__ __forceinline__ int face_row(int f, int n) {
+  return n == 1 ? (f == 0 ? 0 : 1) : (f == 0 ? 0 : (f == n ? 3 : 1));
+}
+__host__ __device__ __forceinline__ int cell_row(int j, int n) {
+  return n == 1 ? 0 : (j == 0 ? 0 : (j == n - 1 ? 2 : 1));
+}
+// entries of level L's face array along axis a (compact or full)
+__host__ __device__ __forceinline__ long long face_count(const DevLevel& L, int a) {
+  if (!L.lap)
+    return (long long)(L.nx + (a == 0)) * (L.ny + (a == 1)) * (L.nz + (a == 2));
+  if (a == 0) return L.nx + 1;
+  if (a == 1) return (long long)L.nx * (L.ny == 1 ? 2 : 4);
+  return (long long)L.nx * L.ny * (L.nz == 1 ? 2 : 4);
+}
+// index of face (i, j, k) along axis a (i = 0..nx for a = 0, and so on)
+__host__ __device__ __forceinline__ long long face_index(int lap, int a, int nx, int ny, int nz, int i, int j, int k) {
+  if (!lap) {
+    if (a == 0) return i + (long long)(nx + 1) * (j + (long long)ny * k);
+    if (a == 1) return i + (long long)nx * (j + (long long)(ny + 1) * k);
+    return i + (long long)nx * (j + (long long)ny * k);
+  }
+  if (a == 0) return i;
+  if (a == 1) return i + (long long)nx * face_row(j, ny);
+  return i + (long long)nx * (j + (long long)ny * face_row(k, nz));
+}
 
 struct LevelState {
   double rho, rho_old, pq, rr, bb, thr;
@@ -162,6 +195,11 @@ struct msrcg_hier {
   int64_t last_calls[MSRCG_MAXLEV] = {};
   int sms = 0;
   msrcg_hier* twin = nullptr;           // FP64-preconditioner twin of an FP32-mode hierarchy (escalation)
+  // constant coefficients (msrcg_build_laplace): K per axis and the
+  // boundary type of each side, kept for the twin
+  int lap = 0;
+  double lapK[3] = {};
+  uint8_t lap_bc[6] = {};
   // tiled restriction of a wide 2D level k into k+1: the largest fine extent
   // (columns, rows) of a tile of msrcg::kRestrictTI x rtj coarse cells, 0 = no
   // tiled kernel (3D, or the tile does not fit the shared memory)

@@ -131,10 +131,12 @@ struct Row {
 struct Geo {
   int nx, ny, nz, px, py;
   int plane, off, npad, n;
+  int lap;
 };
 struct Xf {
   int nx, ny, nz, px, py;
   int plane, off, npad, n;
+  int lap;
   const int* c0[3];
   const int* c1[3];
   const void* w[3];
@@ -154,6 +156,7 @@ __device__ __forceinline__ Geo geo_of(const DevLevel& L) {
   g.off = (int)L.off;
   g.npad = (int)L.npad;
   g.n = (int)L.n;
+  g.lap = L.lap;
   return g;
 }
 __device__ __forceinline__ Xf xf_of(const DevLevel& L) {
@@ -167,6 +170,7 @@ __device__ __forceinline__ Xf xf_of(const DevLevel& L) {
   x.off = (int)L.off;
   x.npad = (int)L.npad;
   x.n = (int)L.n;
+  x.lap = L.lap;
   for (int a = 0; a < 3; ++a) {
     x.c0[a] = L.c0[a];
     x.c1[a] = L.c1[a];
@@ -189,9 +193,16 @@ __device__ __forceinline__ Row make_row(const LV& L, int row) {
     r.j = row - r.k * L.ny;
   }
   r.pc = (int)L.off + L.px * r.j + (int)L.plane * r.k;
-  r.fx = (L.nx + 1) * row;
-  r.fy = L.nx * (row + r.k);
-  r.fz = L.nx * row;
+  if (L.lap) {
+    // compact face arrays of a constant-coefficient level (face_row)
+    r.fx = 0;
+    r.fy = L.nx * cell_row(r.j, L.ny);
+    r.fz = L.nx * (r.j + L.ny * cell_row(r.k, L.nz));
+  } else {
+    r.fx = (L.nx + 1) * row;
+    r.fy = L.nx * (row + r.k);
+    r.fz = L.nx * row;
+  }
   return r;
 }
 
@@ -855,26 +866,27 @@ __device__ V fused_smooth(const DevLevel& L, int m, bool pre, unsigned win_off, 
     const bool own = live && i >= a0 && i < a1;           // a cell this strip writes
     // loads (share 0: T rows; share 1: rp and z rows; the last share: r rows)
     // walk down the level with running pointers
-    const float* pTx = gTx + (i < 0 ? 0 : i);
-    const float* pTy = gTy + (i < 0 ? 0 : i);
+    // face rows: x-faces of cell row j at tx(j), y-faces of face row f at
+    // ty(f) (compact rows on a constant-coefficient level)
+    const int ii = i < 0 ? 0 : i;
+    const bool lap = L.lap != 0;
+    auto tx_row = [&](int j) __attribute__((always_inline)) { return gTx + (lap ? 0 : (nx + 1) * j) + ii; };
+    auto ty_row = [&](int f) __attribute__((always_inline)) { return gTy + nx * (lap ? face_row(f, ny) : f) + ii; };
     const float* prp = grp + off + i;
     const float* pz = gz + off + i;
-    if (mine && hs == 0) cp_async4(sTy + col, pTy);  // face row 0
-    pTy += nx;
+    if (mine && hs == 0) cp_async4(sTy + col, ty_row(0));  // face row 0
     int jl = 0, lo = 0;  // next row to load and its ring offset
     auto load_next = [&]() __attribute__((always_inline)) {
       if (jl < ny) {
         if (hs == 0) {
           const int fo = lo + Ws == DW ? 0 : lo + Ws;
-          if (face) cp_async4(sTx + lo + col, pTx);
-          if (mine) cp_async4(sTy + fo + col, pTy);
+          if (face) cp_async4(sTx + lo + col, tx_row(jl));
+          if (mine) cp_async4(sTy + fo + col, ty_row(jl + 1));
         }
         if (hs == kFuseRoleZ && mine) {
           cp_async4(srp + lo + col, prp);
           if (!pre) cp_async4(sz + lo + col, pz);
         }
-        pTx += nx + 1;
-        pTy += nx;
         prp += px;
         pz += px;
       } else if (jl == ny && !pre && hs == kFuseRoleZ && mine) {
@@ -1396,8 +1408,8 @@ __host__ __device__ __forceinline__ size_t level_smem_bytes(const DevLevel& L, s
   const long long n = L.npad;
   size_t b = 4 * align16(n * vsz) + align16(n * rsz);
   if (vsz != rsz) b += 2 * align16(n * rsz);
-  b += align16((size_t)(L.nx + 1) * L.ny * L.nz * rsz) + align16((size_t)L.nx * (L.ny + 1) * L.nz * rsz);
-  if (dim == 3) b += align16((size_t)L.nx * L.ny * (L.nz + 1) * rsz);
+  b += align16((size_t)face_count(L, 0) * rsz) + align16((size_t)face_count(L, 1) * rsz);
+  if (dim == 3) b += align16((size_t)face_count(L, 2) * rsz);
   return b;
 }
 
@@ -1445,7 +1457,7 @@ __device__ int place_levels(DevLevel* sL, const DevLevel* gL, int lo, int kmax, 
     for (int k = ksm; k <= kmax; ++k) {
       DevLevel& L = sL[k];
       for (int ax = 0; ax < DIM; ++ax) {
-        const size_t nf = (size_t)(L.nx + (ax == 0)) * (L.ny + (ax == 1)) * (L.nz + (ax == 2));
+        const size_t nf = (size_t)face_count(L, ax);
         L.T[ax] = dsm + off;
         if (sizeof(RP) == sizeof(double)) L.T64[ax] = (const double*)(dsm + off);
         off += align16(nf * sizeof(RP));
@@ -1461,7 +1473,7 @@ __device__ int place_levels(DevLevel* sL, const DevLevel* gL, int lo, int kmax, 
   for (int k = ksm; k <= kmax; ++k) {
     for (int ax = 0; ax < DIM; ++ax) {
       const DevLevel& L = sL[k];
-      const size_t nf = (size_t)(L.nx + (ax == 0)) * (L.ny + (ax == 1)) * (L.nz + (ax == 2));
+      const size_t nf = (size_t)face_count(L, ax);
       const RP* src = (const RP*)gL[k].T[ax];
       RP* dst = (RP*)L.T[ax];
       for (size_t e = threadIdx.x; e < nf; e += blockDim.x) dst[e] = __ldg(src + e);

@@ -71,6 +71,8 @@ def lib():
         L.msrcg_default_opts.argtypes = [C.POINTER(Opts)]
         L.msrcg_build.argtypes = [C.POINTER(Grid), vp, C.c_int, vp, C.POINTER(Opts), vp, C.POINTER(vp)]
         L.msrcg_build_faces.argtypes = [C.POINTER(Grid), vp, vp, vp, C.POINTER(Opts), vp, C.POINTER(vp)]
+        L.msrcg_build_laplace.argtypes = [C.POINTER(Grid), C.POINTER(C.c_double * 3), C.POINTER(C.c_uint8 * 6),
+                                          C.POINTER(Opts), vp, C.POINTER(vp)]
         L.msrcg_lift_rhs.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.msrcg_solve.argtypes = [vp, vp, C.c_double, vp, C.POINTER(Stats), vp]
         L.msrcg_batch_solve.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(vp), C.c_double, C.POINTER(vp),
@@ -226,6 +228,37 @@ class Hierarchy:
     @classmethod
     def from_problem(cls, prob, opts: Opts | None = None, device="cuda", stream=None):
         return cls(prob.dim, prob.n, prob.h, prob.K, prob.bc, opts, device, stream)
+
+    @classmethod
+    def laplace(cls, dim, n, h, K, side_bc, opts: Opts | None = None, device="cuda", stream=None):
+        """Constant-coefficient hierarchy (msrcg_build_laplace): K a scalar or
+        one value per axis, side_bc six 0/1 flags (x-low, x-high, y-low,
+        y-high, z-low, z-high; 1 = Dirichlet)."""
+        self = cls.__new__(cls)
+        self.device = _device(device)
+        self.dim = dim
+        self.n = tuple(int(v) for v in n)
+        self.N = int(np.prod(self.n))
+        g = Grid()
+        g.dim = dim
+        for a in range(3):
+            g.n[a] = self.n[a] if a < min(dim, len(self.n)) else 1
+            g.h[a] = float(h[a]) if a < min(dim, len(h)) else 1.0
+        Kv = np.broadcast_to(np.asarray(K, np.float64).reshape(-1), (3,)) if np.size(K) == 1 else \
+            np.asarray(list(np.asarray(K, np.float64).reshape(-1)) + [1.0] * 3)[:3]
+        Ka = (C.c_double * 3)(*[float(v) for v in Kv])
+        sb = list(side_bc) + [0] * 6
+        Sa = (C.c_uint8 * 6)(*[int(v) for v in sb[:6]])
+        self.opts = opts or default_opts()
+        hp = C.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = lib().msrcg_build_laplace(C.byref(g), C.byref(Ka), C.byref(Sa), C.byref(self.opts), _stream(stream),
+                                           C.byref(hp))
+        if rc != OK:
+            raise MsrcgError(rc, "msrcg_build_laplace")
+        self._h = hp
+        self.nlev = lib().msrcg_num_levels(self._h)
+        return self
 
     @classmethod
     def from_faces(cls, dim, n, h, Kfaces, opts: Opts | None = None, device="cuda", stream=None):

@@ -741,3 +741,82 @@ def test_profile_level_entry(M):
     R = O.Hierarchy(prob)
     xr, sr = R.solve(R.lift_rhs(), 1e-8)
     assert st["status"] == 0 and np.linalg.norm(x.cpu().numpy() - xr) / np.linalg.norm(xr) <= SOL_RTOL
+
+
+# ---------------------------------------------------------------------------
+# constant coefficients (msrcg_build_laplace, the Laplace specialisation of
+# Sec. 4.1): compact face arrays, same operator as the cell-K build of a
+# constant field
+# ---------------------------------------------------------------------------
+def _const_problem(n, K, seed=91):
+    rng = np.random.default_rng(seed)
+    dim = len(n)
+    N = int(np.prod(n))
+    Kc = np.repeat(np.asarray(K, np.float64).reshape(-1, 1), N, axis=1)
+    bc, gD = P.standard_bc(dim, n)
+    return P.Problem(dim=dim, n=tuple(n), h=tuple(1.0 / m for m in n), K=Kc, bc=bc, gD=gD,
+                     f=rng.standard_normal(N), pbf=P.linear_lifting(dim, n))
+
+
+LAP_CASES = [((64, 48), (1.0, 1.0)), ((37, 23), (3.0, 0.25)), ((1024, 1024), (1.0, 1.0)), ((12, 10, 9), (1.0, 2.0, 0.5)),
+             ((64, 64, 64), (1.0, 1.0, 1.0))]
+
+
+@pytest.mark.parametrize("n,K", LAP_CASES, ids=["x".join(map(str, c[0])) for c in LAP_CASES])
+def test_laplace_transmissibilities_match_oracle(M, n, K):
+    """The compact constant-coefficient levels expand to the oracle's
+    transmissibilities of the same constant field: level 0 to the bit, the
+    coarse levels (the oracle's series-parallel sums of equal conductors) to
+    rounding."""
+    prob = _const_problem(n, K)
+    H = M.Hierarchy.laplace(prob.dim, prob.n, prob.h, K, [1, 1, 0, 0, 0, 0])
+    R = O.Hierarchy(prob)
+    assert H.nlev == R.nlev
+    for k in range(R.nlev):
+        for tg, tr in zip(H.trans(k), R.T(k)):
+            if tr is None:
+                continue
+            tg = tg.cpu().numpy()
+            if k == 0:
+                assert np.array_equal(tg, tr)
+            else:
+                assert np.max(np.abs(tg - tr)) <= 1e-13 * np.max(np.abs(tr)), k
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("n,K", LAP_CASES, ids=["x".join(map(str, c[0])) for c in LAP_CASES])
+def test_laplace_solve_matches_oracle(M, n, K, prec):
+    """Single and batched solves of the constant-coefficient hierarchy (lifted
+    right-hand side with a source) against the oracle's solve of the same
+    constant field, norm-wise and element-wise."""
+    prob = _const_problem(n, K)
+    opts = M.default_opts(precision=prec, inner_floor=1e-6 if prec else 0.0)
+    H = M.Hierarchy.laplace(prob.dim, prob.n, prob.h, K, [1, 1, 0, 0, 0, 0], opts)
+    b = H.rhs_for(prob)
+    R = O.Hierarchy(prob)
+    br = R.lift_rhs()
+    assert np.max(np.abs(b.cpu().numpy() - br)) <= 1e-12 * np.max(np.abs(br))
+    xr, sr = R.solve(br, 1e-8)
+    assert sr["status"] == 0
+    x, st = H.solve(b, 1e-8)
+    xs, sts = M.batch_solve([H], [b], 1e-8)
+    for xx, ss in ((x, st), (xs[0], sts[0])):
+        assert ss["status"] == 0 and ss["relres_true"] < 1e-8, ss
+        xg = xx.cpu().numpy()
+        assert np.linalg.norm(xg - xr) / np.linalg.norm(xr) <= SOL_RTOL
+        assert np.max(np.abs(xg - xr)) / np.max(np.abs(xr)) <= SOL_RTOL
+        if prec == 0:
+            _counts_close(ss["iters"], sr["iters"], sr["calls"])
+
+
+def test_laplace_uses_less_memory(M):
+    """No full face array is kept: the constant-coefficient hierarchy of a
+    1024^2 problem is smaller than the cell-K one by about the face arrays
+    (two FP64 words per cell, and two FP32 ones with the FP32 preconditioner)."""
+    prob = _const_problem((1024, 1024), (1.0, 1.0))
+    for prec in (0, 1):
+        opts = M.default_opts(precision=prec)
+        A = M.Hierarchy.from_problem(prob, opts)
+        B = M.Hierarchy.laplace(2, prob.n, prob.h, 1.0, [1, 1, 0, 0, 0, 0], opts)
+        saved = A.device_bytes() - B.device_bytes()
+        assert saved >= (16 + (8 if prec else 0)) * prob.N, (A.device_bytes(), B.device_bytes())
