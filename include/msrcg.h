@@ -87,7 +87,8 @@ typedef struct {
                           never refined, and the level where no axis changes is the coarsest */
   int interp;          /* extension E (R = E^T): 0 = tensor linear interpolation with zero slope at
                           the boundary, 1 = piecewise constant (Sec. 3) */
-  int stall_iters;     /* precision 1: stall test of the level-0 PCG: when its residual norm has not
+  int stall_iters;     /* precision 1, precond 0: stall test of the level-0 PCG: when its residual
+                          norm has not
                           halved for
                           this many iterations it switches to the flexible (Polak-Ribiere) direction
                           factor beta = r_new.(z_new - z_old) / r_old.z_old, which keeps the CG

@@ -2493,7 +2493,11 @@ ProblemDesc make_desc(msrcg_hier* h, const double* b, double* x, double tol) {
   pd.fuse_min_cells = h->o.fuse_min_cells > 0 ? h->o.fuse_min_cells : kFuseMinCells;
   pd.splitting = h->o.splitting;
   pd.allow_flex = h->o.precision == 1;
-  pd.stall_w = pd.allow_flex && h->o.stall_iters >= 0 ? (h->o.stall_iters > 0 ? h->o.stall_iters : 30) : 0;
+  // the stall test watches the recursive multi-scale PCG (eq. 2.10); the
+  // multigrid and polynomial preconditioners converge slowly by design
+  pd.stall_w = pd.allow_flex && h->o.precond == 0 && h->o.stall_iters >= 0
+                   ? (h->o.stall_iters > 0 ? h->o.stall_iters : 30)
+                   : 0;
   pd.flex0 = h->o.flexible;
   pd.precond = h->o.precond;
   return pd;
