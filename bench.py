@@ -357,7 +357,7 @@ def run_uneven(args, M, P, dev, stream):
     for prec, key in ((1, "fp32_precond"), (0, "fp64_plain")):
         if prec == 0 and args.no_fp64:
             continue
-        opts = M.default_opts(precision=prec, inner_floor=1e-6 if prec else 0.0, **(tuned if prec else {}))
+        opts = M.default_opts(precision=prec, **({"inner_floor": 1e-6, **tuned} if prec else {"inner_floor": 0.0}))
         hs = [M.Hierarchy.from_problem(p, opts, device=dev) for p in probs]
         bs = [h.rhs_for(p) for h, p in zip(hs, probs)]
         per, sts = _timed_batch(M, hs, bs, 3 if prec else 2, stream, dev)
@@ -617,7 +617,7 @@ def main():
     tuned = tuned_rec or {}
 
     def make_batch(prec):
-        opts = M.default_opts(precision=prec, inner_floor=1e-6 if prec else 0.0, **(tuned if prec else {}))
+        opts = M.default_opts(precision=prec, **({"inner_floor": 1e-6, **tuned} if prec else {"inner_floor": 0.0}))
         hs, bs = [], []
         for j in range(nb):
             # problem j of this rank: the shared permeability field with its own

@@ -1,4 +1,4 @@
-"""Autotuner for the tile shapes of the batched solver.
+"""Autotuner of the batched solver: tile shapes, then the FP32 inner floor.
 
 The batched solver (`msrcg_batch_solve`, one CTA per problem) smooths the
 levels it keeps in global memory in one pass over column strips (see
@@ -7,6 +7,13 @@ levels it keeps in global memory in one pass over column strips (see
 the plain per-half-sweep passes are the alternative.  Which is fastest depends
 on the problem sizes, the batch and the GPU, so `tune` times the candidates on
 the actual workload and `best` returns the winner recorded for this GPU.
+
+A second stage tunes the floor of the FP32 inner levels (`inner_floor`: an
+inner PCG also stops once ||r_k|| < floor ||b_k||) on the winning tile shape:
+a candidate qualifies only if every solve converges without the FP64 rerun,
+meets the tolerance in its true residual and needs no more outer (level-0)
+iterations than the library's 1e-6; the fastest qualifying one wins.  The
+FP64 outer PCG keeps the result at the requested tolerance either way.
 
 Records live in `tuned.json` beside this module, keyed by GPU name and a
 workload key chosen by the caller; `python -m paper_math_9809043_gb300.tune
@@ -31,6 +38,10 @@ CANDIDATES: List[Dict[str, int]] = [
 ]
 
 
+# candidate floors of the FP32 inner levels (the first is the library's)
+FLOORS: List[float] = [1e-6, 1e-5, 1e-4, 1e-3]
+
+
 def key_of(cand: Dict[str, int]) -> str:
     return ",".join(f"{k}={v}" for k, v in sorted(cand.items())) or "default"
 
@@ -43,7 +54,7 @@ def load_table(path: str = TABLE) -> dict:
         return {}
 
 
-def record(table: dict, gpu: str, workload: str, best: Dict[str, int], times: Dict[str, float]) -> dict:
+def record(table: dict, gpu: str, workload: str, best: Dict[str, float], times: Dict[str, Optional[float]]) -> dict:
     table.setdefault(gpu, {})[workload] = {"best": best, "ms": times}
     return table
 
@@ -54,37 +65,62 @@ def best(gpu: str, workload: str, path: str = TABLE) -> Optional[Dict[str, int]]
     return dict(ent["best"]) if ent else None
 
 
-def tune(problems, precision: int = 1, tol: float = 1e-8, steps: int = 2,
-         candidates: List[Dict[str, int]] = CANDIDATES, device=None):
-    """Time one batched solve of `problems` per candidate (after one warm-up)
-    and return (fastest candidate, {candidate key: mean ms})."""
+def _time(problems, opts_kw, precision, tol, steps, dev):
+    """Mean ms of one batched solve (after a warm-up) and the last stats."""
     import torch
 
     from . import msrcg as M
 
+    opts = M.default_opts(precision=precision, **opts_kw)
+    hs = [M.Hierarchy.from_problem(p, opts, device=dev) for p in problems]
+    bs = [h.rhs_for(p) for h, p in zip(hs, problems)]
+    M.batch_solve(hs, bs, tol, check=False)
+    torch.cuda.synchronize(dev)
+    per, sts = [], None
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, sts = M.batch_solve(hs, bs, tol, check=False)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        per.append(e0.elapsed_time(e1))
+    del hs, bs
+    torch.cuda.empty_cache()
+    return statistics.mean(per), sts
+
+
+def tune(problems, precision: int = 1, tol: float = 1e-8, steps: int = 2,
+         candidates: List[Dict[str, int]] = CANDIDATES, floors: List[float] = FLOORS, device=None):
+    """Time one batched solve of `problems` per tile-shape candidate, then per
+    inner floor on the fastest shape (precision 1); return (fastest settings,
+    {candidate key: mean ms})."""
+    import torch
+
     dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    base_floor = {"inner_floor": floors[0]} if precision else {}
     times: Dict[str, float] = {}
     for cand in candidates:
-        opts = M.default_opts(precision=precision, inner_floor=1e-6 if precision else 0.0, **cand)
-        hs = [M.Hierarchy.from_problem(p, opts, device=dev) for p in problems]
-        bs = [h.rhs_for(p) for h, p in zip(hs, problems)]
-        M.batch_solve(hs, bs, tol)
-        torch.cuda.synchronize(dev)
-        per = []
-        for _ in range(steps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            _, sts = M.batch_solve(hs, bs, tol)
-            e1.record()
-            torch.cuda.synchronize(dev)
-            if any(s["status"] != 0 for s in sts):
-                raise RuntimeError(f"candidate {key_of(cand)} did not converge")
-            per.append(e0.elapsed_time(e1))
-        times[key_of(cand)] = statistics.mean(per)
-        del hs, bs
-        torch.cuda.empty_cache()
-    fastest = min(candidates, key=lambda c: times[key_of(c)])
-    return dict(fastest), times
+        ms, sts = _time(problems, {**base_floor, **cand}, precision, tol, steps, dev)
+        if any(s["status"] != 0 for s in sts):
+            raise RuntimeError(f"candidate {key_of(cand)} did not converge")
+        times[key_of(cand)] = ms
+    fastest = dict(min(candidates, key=lambda c: times[key_of(c)]))
+    if not precision:
+        return fastest, times
+    ref_ms, ref = times[key_of(fastest)], None
+    _, ref = _time(problems, {**base_floor, **fastest}, precision, tol, 1, dev)
+    outer = max(s["iters"][0] for s in ref)
+    best_ms, best_floor = ref_ms, floors[0]
+    for fl in floors[1:]:
+        ms, sts = _time(problems, {**fastest, "inner_floor": fl}, precision, tol, steps, dev)
+        ok = all(s["status"] == 0 and s["escalated"] == 0 and s["relres_true"] < tol and s["iters"][0] <= outer
+                 for s in sts)
+        times[key_of({**fastest, "inner_floor": fl})] = ms if ok else None  # None: did not qualify
+        if ok and ms < best_ms:
+            best_ms, best_floor = ms, fl
+    if best_floor != floors[0]:
+        fastest["inner_floor"] = best_floor
+    return fastest, times
 
 
 def _grf_batch(n_problems: int, side: int):
@@ -117,7 +153,8 @@ def main(argv=None) -> int:
     for workload, probs in ((f"grf1024x{sms}", _grf_batch(sms, 1024)), ("uneven256", P.batch_problems(256))):
         fastest, times = tune(probs)
         record(table, gpu, workload, fastest, times)
-        print(workload, key_of(fastest), {k: round(v, 2) for k, v in times.items()}, flush=True)
+        print(workload, key_of(fastest), {k: (round(v, 2) if v is not None else None) for k, v in times.items()},
+              flush=True)
     with open(args.out, "w") as f:
         json.dump(table, f, indent=1, sort_keys=True)
     return 0

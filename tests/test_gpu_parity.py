@@ -373,7 +373,7 @@ def test_bench_batch_full_launch(M, prec):
                        f=np.random.default_rng(1001 * 1000 + j).standard_normal(base.N), pbf=base.pbf)
              for j in range(nb)]
     tuned = (TU.best(torch.cuda.get_device_name(), f"grf1024x{nb}") or {}) if prec else {}
-    opts = M.default_opts(precision=prec, inner_floor=1e-6 if prec else 0.0, **tuned)
+    opts = M.default_opts(precision=prec, **({"inner_floor": 1e-6, **tuned} if prec else {"inner_floor": 0.0}))
     hs = [M.Hierarchy.from_problem(p, opts) for p in probs]
     bs = [h.rhs_for(p) for h, p in zip(hs, probs)]
     xs, sts = M.batch_solve(hs, bs, 1e-8)

@@ -25,3 +25,4 @@ def test_candidates_are_option_fields():
     names = {f[0] for f in M.Opts._fields_}
     for cand in TU.CANDIDATES:
         assert set(cand) <= names, cand
+    assert "inner_floor" in names and TU.FLOORS[0] == 1e-6  # the second stage's field; the first is the default
