@@ -183,6 +183,14 @@ __device__ __forceinline__ Xf xf_of(const DevLevel& L) {
   return x;
 }
 
+// Face offsets of row (j, k) on a constant-coefficient level (compact face
+// arrays, face_row).  Kept out of line: make_row is inlined into every
+// stencil loop of the solver, and this rarely taken path would otherwise be
+// copied into each of them.
+__device__ __noinline__ int3 lap_row_faces(int nx, int ny, int nz, int j, int k) {
+  return make_int3(0, nx * cell_row(j, ny), nx * (j + ny * cell_row(k, nz)));
+}
+
 template <int DIM, class LV>
 __device__ __forceinline__ Row make_row(const LV& L, int row) {
   Row r;
@@ -194,10 +202,10 @@ __device__ __forceinline__ Row make_row(const LV& L, int row) {
   }
   r.pc = (int)L.off + L.px * r.j + (int)L.plane * r.k;
   if (__builtin_expect(L.lap != 0, 0)) {
-    // compact face arrays of a constant-coefficient level (face_row)
-    r.fx = 0;
-    r.fy = L.nx * cell_row(r.j, L.ny);
-    r.fz = L.nx * (r.j + L.ny * cell_row(r.k, L.nz));
+    const int3 f = lap_row_faces(L.nx, L.ny, L.nz, r.j, r.k);
+    r.fx = f.x;
+    r.fy = f.y;
+    r.fz = f.z;
   } else {
     r.fx = (L.nx + 1) * row;
     r.fy = L.nx * (row + r.k);
@@ -1001,13 +1009,9 @@ struct LvlCtl {
   double rho_d, rho_old_d, thrN_d;
   float rho_f, rho_old_f, thrN_f;
   int it, phase;
-};
-
-// Level 0's extra state (one per recursion, not per level): ||r||^2 of the
-// last update, the stall test's best residual and its iteration, and
-// r_new . z_old of the last update for the flexible beta.
-struct Lvl0 {
-  double rr, rr_best, gamma;
+  // level 0: ||r||^2 of the last update, the stall test's best residual and
+  // its iteration, r_new . z_old of the last update (flexible beta)
+  double rr_d, rr_best, gamma_d;
   int it_best;
   bool gamma_ok;
 };
@@ -1199,11 +1203,11 @@ struct Ops {
   // Returns ||r||^2 (false on breakdown).  With `flex`, beta is the flexible
   // (Polak-Ribiere) factor (rho - r.z_old) / rho_old once the previous update
   // has formed r.z_old, and this update forms r_new . z for the next one.
-  static __device__ bool cg_step(BlockTeam& tm, const DevLevel& L, LvlCtl& ct, V& rr_out, bool flex, Lvl0& z0) {
+  static __device__ bool cg_step(BlockTeam& tm, const DevLevel& L, LvlCtl& ct, V& rr_out, bool flex) {
     const V rho = Scal<V>::rho(ct);
     const bool first = ct.it == 0;
     const V beta = first ? (V)0
-                         : (flex && z0.gamma_ok ? (rho - (V)z0.gamma) / Scal<V>::rho_old(ct)
+                         : (flex && ct.gamma_ok ? (rho - (V)ct.gamma_d) / Scal<V>::rho_old(ct)
                                                 : rho / Scal<V>::rho_old(ct));
     V* p = (V*)L.p;
     V* q = (V*)L.q;
@@ -1246,8 +1250,8 @@ struct Ops {
                 r[c] = rv;
               });
       rr_out = tm.sum<V>(acc2);
-      z0.gamma = (double)tm.sum<V>(acc3);
-      z0.gamma_ok = true;
+      ct.gamma_d = (double)tm.sum<V>(acc3);
+      ct.gamma_ok = true;
       return true;
     }
     for_lin(npad, [&](int c) { return Four<V>{x[c], p[c], r[c], q[c]}; }, [&](int c, Four<V> v) {
@@ -1258,16 +1262,15 @@ struct Ops {
       r[c] = rv;
     });
     rr_out = tm.sum<V>(acc2);
-    if (flex) z0.gamma_ok = false;
+    ct.gamma_ok = false;
     return true;
   }
   // one CG step and the level test; returns 0 = continue, 1 = converged,
   // 2 = breakdown
-  static __device__ int iterate(BlockTeam& tm, const DevLevel& L, LvlCtl& c, SolveState* S, const RecArgs& a, int k,
-                                Lvl0& z0) {
+  static __device__ int iterate(BlockTeam& tm, const DevLevel& L, LvlCtl& c, SolveState* S, const RecArgs& a, int k) {
     V rr;
-    if (!cg_step(tm, L, c, rr, k == 0 && *a.flex, z0)) return 2;
-    if (k == 0) z0.rr = (double)rr;
+    if (!cg_step(tm, L, c, rr, k == 0 && *a.flex)) return 2;
+    c.rr_d = (double)rr;
     if (threadIdx.x == 0) {
       a.iters[k]++;
       if (k == 0) S->lv[0].rr = (double)rr;
@@ -1282,8 +1285,6 @@ struct Ops {
 template <int DIM, typename RP>
 __device__ void recursion(BlockTeam& tm, const DevLevel* sL, int ks, const RecArgs& a) {
   LvlCtl ct[kMaxLev];
-  Lvl0 z0;
-  z0.gamma_ok = false;
   int k = ks;
   ct[k].phase = kStart;
   SolveState* S = a.S;
@@ -1307,13 +1308,14 @@ __device__ void recursion(BlockTeam& tm, const DevLevel* sL, int ks, const RecAr
       if (dbl || sizeof(RP) == sizeof(double)) {
         const double bb = dbl ? (double)Ops<DIM, double, RP>::enter(tm, L) : (double)Ops<DIM, RP, RP>::enter(tm, L);
         live = bb > 0.0;
-        if (k == 0) z0.rr_best = bb;
+        c.rr_best = bb;
         c.thrN_d = a.thrN_d[k];
         if (k > 0 && a.floor2 > 0.0) c.thrN_d = fmax(c.thrN_d, a.floor2 * bb);
         c.thrN_f = (float)c.thrN_d;
       } else {
         const float bb = (float)Ops<DIM, RP, RP>::enter(tm, L);
         live = bb > 0.f;
+        c.rr_best = (double)bb;
         c.thrN_f = fmaxf(a.thrN_f[k], a.floor2_f * bb);
         if (!(c.thrN_f > 1e-30f)) c.thrN_d = fmax(a.thrN_d[k], a.floor2 * (double)bb);
       }
@@ -1324,10 +1326,8 @@ __device__ void recursion(BlockTeam& tm, const DevLevel* sL, int ks, const RecAr
       c.it = 0;
       c.rho_old_d = 0.0;
       c.rho_old_f = 0.f;
-      if (k == 0) {
-        z0.gamma_ok = false;
-        z0.it_best = 0;
-      }
+      c.gamma_ok = false;
+      c.it_best = 0;
       c.phase = kIterate;
     } else if (c.phase == kIterate) {
       if (a.precond == 2 && k == 0 && a.kmax > 0) {
@@ -1361,20 +1361,19 @@ __device__ void recursion(BlockTeam& tm, const DevLevel* sL, int ks, const RecAr
         c.phase = kReturn;
         continue;
       }
-      const int st = dbl ? Ops<DIM, double, RP>::iterate(tm, L, c, S, a, k, z0)
-                         : Ops<DIM, RP, RP>::iterate(tm, L, c, S, a, k, z0);
+      const int st = dbl ? Ops<DIM, double, RP>::iterate(tm, L, c, S, a, k) : Ops<DIM, RP, RP>::iterate(tm, L, c, S, a, k);
       c.it++;
       // stall test of the level-0 PCG (every thread takes the same decision:
       // the residual norm is the same block-wide total in all of them)
       bool stalled = false;
       if (st == 0 && k == 0 && a.stall_w > 0) {
-        if (z0.rr < 0.25 * z0.rr_best) {
-          z0.rr_best = z0.rr;
-          z0.it_best = c.it;
-        } else if (c.it - z0.it_best >= a.stall_w) {
+        if (c.rr_d < 0.25 * c.rr_best) {
+          c.rr_best = c.rr_d;
+          c.it_best = c.it;
+        } else if (c.it - c.it_best >= a.stall_w) {
           if (!*a.flex && a.allow_flex) {
             *a.flex = true;
-            z0.it_best = c.it;
+            c.it_best = c.it;
           } else {
             stalled = true;
           }
