@@ -157,6 +157,13 @@ def hbm_bytes_of_solve(stats, prec):
     return sum(stats["iters"][k] * level_bytes_per_iter(k, dims[k], prec) for k in range(len(dims)) if k not in res)
 
 
+def all_level_bytes_of_solve(stats, prec):
+    """The same formula over every level, shared-memory ones included (the
+    scope table's per-solve figure)."""
+    dims = [tuple(d) for d in stats["dims"]]
+    return sum(stats["iters"][k] * level_bytes_per_iter(k, dims[k], prec) for k in range(len(dims)))
+
+
 def traffic_from_profile(kernel_src):
     """DRAM traffic per launch from the committed ncu summary, valid only
     while the kernel source is unchanged."""
@@ -687,10 +694,13 @@ def main():
     traffic = None
     if tr and tr.get("batch") and tr.get("size") == args.size:
         traffic = tr["dram_bytes_per_problem"] * nb
+    all_bytes = sum(all_level_bytes_of_solve(s, prec) for s in sts)
     roofline = {"kernel": "k_small (persistent batched solve, one CTA per problem)", "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": peak_src, "traffic": traffic,
                 "algorithmic_bytes_per_launch": alg_bytes,
+                "numerator": "levels that stay in HBM (0-1 at 1024^2); frac_all_levels counts every level's bytes",
+                "frac_all_levels": all_bytes / launch_s / 1e9 / peak,
                 "launch_ms": launch_s * 1e3}
     if traffic is not None and tr.get("counters"):
         # per-SM issue counters of the same ncu capture (batch of 8): the kernel's
