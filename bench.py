@@ -620,7 +620,9 @@ def main():
     # tile shapes of the batched solver for this GPU and workload (autotuner record)
     from paper_math_9809043_gb300 import tune as TU
     gpu_name = torch.cuda.get_device_name(dev)
-    tuned_rec = TU.best(gpu_name, f"grf{args.size}x{nb}")
+    # the record for this batch, else the one for a batch of one problem per SM
+    # (same workload and tile-shape candidates)
+    tuned_rec = TU.best(gpu_name, f"grf{args.size}x{nb}") or TU.best(gpu_name, f"grf{args.size}x{sms}")
     tuned = tuned_rec or {}
 
     def make_batch(prec):

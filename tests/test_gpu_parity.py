@@ -525,13 +525,21 @@ def test_single_pass_smoothing_on_thin_levels(M, n):
 
 def test_tuner_picks_a_candidate(M):
     """The autotuner times every candidate tile shape on a small batch, all of
-    them solve, and it returns the fastest."""
+    them solve, and it keeps the fastest; its second stage times every other
+    inner floor on that shape and keeps one only where it is faster (a floor
+    that does not qualify is recorded as None)."""
     from paper_math_9809043_gb300 import tune as TU
     probs = [P.config_problem(1, scale=256) for _ in range(2)]
     cands = [{}, {"plain_sweeps": 1}, {"fuse_width": 64}]
     fastest, times = TU.tune(probs, steps=1, candidates=cands)
-    assert fastest in cands and set(times) == {TU.key_of(c) for c in cands}
-    assert times[TU.key_of(fastest)] == min(times.values())
+    shape = {k: v for k, v in fastest.items() if k != "inner_floor"}
+    shape_keys = {TU.key_of(c) for c in cands}
+    assert shape in cands and shape_keys <= set(times)
+    assert times[TU.key_of(shape)] == min(times[k] for k in shape_keys)
+    assert set(times) - shape_keys == {TU.key_of({**shape, "inner_floor": f}) for f in TU.FLOORS[1:]}
+    if "inner_floor" in fastest:
+        assert fastest["inner_floor"] in TU.FLOORS[1:]
+        assert times[TU.key_of(fastest)] is not None and times[TU.key_of(fastest)] < times[TU.key_of(shape)]
 
 
 @pytest.mark.parametrize("prec", [1, 0])
