@@ -909,17 +909,7 @@ __device__ V fused_smooth(const DevLevel& L, int m, bool pre, unsigned win_off, 
     }
     // stage q updates row s - 2q, whose colour at this column is (i+s)&1: the
     // column takes the stages of that parity, dealt round its threads; the
-    // parity flips every step.  Per parity and entry e: the stage q, its ring
-    // offset 2q Ws (0 for a q beyond the last stage, which stays in the ring)
-    // and the steps in which it has a row.
-    int qv[2][kFuseE], qoff[2][kFuseE];
-#pragma unroll
-    for (int pp = 0; pp < 2; ++pp)
-#pragma unroll
-      for (int e = 0; e < kFuseE; ++e) {
-        qv[pp][e] = pp + 2 * hs + 2 * kFuseShare * e;
-        qoff[pp][e] = qv[pp][e] < S ? 2 * qv[pp][e] * Ws : 0;
-      }
+    // parity flips every step
     int par = i & 1;
     int sbo = 0;  // ring offset of row s
     const int lago = lag * Ws, lasto = 2 * (S - 1) * Ws;
@@ -948,27 +938,32 @@ __device__ V fused_smooth(const DevLevel& L, int m, bool pre, unsigned win_off, 
         float v[kFuseE];
         int ro[kFuseE];
         bool act[kFuseE];
-        // Both entries are computed without a branch, so that their
-        // dependency chains overlap; an inactive entry reads slots inside the
-        // rings (its values are discarded) and only active entries store.
 #pragma unroll
         for (int e = 0; e < kFuseE; ++e) {
-          const int q = par ? qv[1][e] : qv[0][e];
+          const int q = par + 2 * hs + 2 * kFuseShare * e;
           act[e] = q < S && s >= 2 * q && s < 2 * q + ny;
-          int r0 = sbo - (par ? qoff[1][e] : qoff[0][e]);
-          if (r0 < 0) r0 += DW;
-          const int ru = r0 + Ws == DW ? 0 : r0 + Ws, rd = r0 == 0 ? DW - Ws : r0 - Ws;
-          const int c = r0 + col;
-          const float tw = sTx[c], te = sTx[c + 1], ts = sTy[c], tn = sTy[ru + col];
-          const float rhs = srp[c];
-          float d, sm = rhs;
-          gs_terms2<float>(d, sm, tw, te, ts, tn, sz[c - 1], sz[c + 1], sz[rd + col], sz[ru + col]);
-          // stage 0 of pre-smoothing (from zero): rp / D on red cells (d is
-          // the same sum of the four faces)
-          if (pre && q == 0) sm = rhs;
-          v[e] = quot<float>(sm, d);
-          ro[e] = c;
-          if (!pre && q == S - 1 && own && act[e]) acc += sr[rs] * (V)v[e];
+          ro[e] = 0;
+          v[e] = 0.f;
+          if (act[e]) {
+            int r0 = sbo - 2 * q * Ws;
+            if (r0 < 0) r0 += DW;
+            const int ru = r0 + Ws == DW ? 0 : r0 + Ws, rd = r0 == 0 ? DW - Ws : r0 - Ws;
+            const int c = r0 + col;
+            const float tw = sTx[c], te = sTx[c + 1], ts = sTy[c], tn = sTy[ru + col];
+            float d, sm = srp[c];
+            if (pre && q == 0) {
+              // stage 0 of pre-smoothing (from zero): rp / D on red cells
+              d = tw;
+              d += te;
+              d += ts;
+              d += tn;
+            } else {
+              gs_terms2<float>(d, sm, tw, te, ts, tn, sz[c - 1], sz[c + 1], sz[rd + col], sz[ru + col]);
+            }
+            v[e] = quot<float>(sm, d);
+            ro[e] = c;
+            if (!pre && q == S - 1 && own) acc += sr[rs] * (V)v[e];
+          }
         }
         if (hs == 0 && pre && par == 1 && s < ny) sz[sbo + col] = 0.f;  // black cell of stage 0's row
         if (hs == kFuseRoleR) {
