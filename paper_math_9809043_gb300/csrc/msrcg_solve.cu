@@ -759,6 +759,14 @@ __device__ void t_restrict(const Xf& F, const Geo& Gc, const R* t, R* rc) {
   }
 }
 
+__host__ __device__ __forceinline__ size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+// Zero `bytes` (a multiple of 16) of shared memory at p, 16 bytes a store.
+__device__ __forceinline__ void zero_block(unsigned char* p, size_t bytes) {
+  float4* q = (float4*)p;
+  for (size_t e = threadIdx.x; e < bytes / 16; e += blockDim.x) q[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 // ---------------------------------------------------------------------------
 // Single-pass red-black smoothing of a 2D level in global memory (one CTA)
 // ---------------------------------------------------------------------------
@@ -772,9 +780,11 @@ __device__ void t_restrict(const Xf& F, const Geo& Gc, const R* t, R* rc) {
 // stale without the neighbouring strip; the neighbour recomputes them with the
 // same arithmetic) into rings of rows in shared memory, prefetched kFuseAhead
 // rows ahead with cp.async.  Each row of T, rp (and z) then crosses HBM once
-// per smoothing instead of once per half-sweep.  Three threads own each
+// per smoothing instead of once per half-sweep.  kFuseShare threads own each
 // column of the strip and, at step s, share the stages whose row has its
-// colour there; every load of a step precedes its stores.
+// colour there; every load of a step precedes its stores.  The rings take the
+// shared memory of the coarse levels resident there, whose vectors hold
+// nothing live while a finer level smooths (they are zeroed again after).
 //   pre  (from zero): stage 0 sets z = rp/D on red cells and 0 on black; after
 //        the last stage a result step forms t = rp - A z and writes z and t.
 //   post (z holds the prolonged pre-smoothing result): the strip reads z and
@@ -784,9 +794,9 @@ __device__ void t_restrict(const Xf& F, const Geo& Gc, const R* t, R* rc) {
 constexpr int kFuseAhead = 8;    // rows prefetched ahead of stage 0
 constexpr int kFuseMinWidth = 16;
 constexpr int kFuseMinCells = 4096;  // default smallest level that takes the single pass
-constexpr int kFuseMaxM = 4;     // stages per thread <= 2 (three threads per column)
+constexpr int kFuseMaxM = 4;     // stages per thread <= 3 (two threads per column)
 #ifndef MSRCG_FUSE_SHARE
-#define MSRCG_FUSE_SHARE 3
+#define MSRCG_FUSE_SHARE 2
 #endif
 constexpr int kFuseShare = MSRCG_FUSE_SHARE;  // threads per ring column
 // stage entries per thread and step: the column's stages of one parity
@@ -822,13 +832,14 @@ __host__ __device__ __forceinline__ int fuse_depth(int S) { return 2 * S + kFuse
 __host__ __device__ __forceinline__ int fuse_rdepth() { return kFuseAhead + 2; }
 
 // Output columns per strip that fit `bytes` of shared memory and a CTA of
-// `threads` (kFuseShare threads per ring column); 0: fusion off.
+// `threads` (kFuseShare threads per loaded column; a ring row also holds the
+// two zero columns at its ends); 0: fusion off.
 __host__ __device__ __forceinline__ int fuse_width(int m, size_t bytes, int vsz, int threads) {
   if (m < 1 || m > kFuseMaxM || bytes < 64) return 0;
   const int S = 2 * m + 1, D = fuse_depth(S);
   const size_t per_col = 16 * (size_t)D + (size_t)fuse_rdepth() * vsz;
   int ws = (int)((bytes - 16) / per_col);
-  if (ws > threads / kFuseShare) ws = threads / kFuseShare;
+  if (ws > threads / kFuseShare + 2) ws = threads / kFuseShare + 2;
   const int wo = ws - 2 * S - 2;
   return wo >= kFuseMinWidth ? wo : 0;
 }
@@ -850,9 +861,9 @@ __device__ V fused_smooth(const DevLevel& L, int m, bool pre, unsigned win_off, 
   float* gt = (float*)L.t;
   const V* gr = (const V*)L.r;
   const int bd = blockDim.x, share = bd / kFuseShare;
-  // ring column, and which share of the column's stages (hs == kFuseShare:
-  // the few threads left over, idle)
-  const int col = threadIdx.x % share, hs = threadIdx.x / share;
+  // ring column (1 + the loaded column), and which share of the column's
+  // stages (hs == kFuseShare: the few threads left over, idle)
+  const int col = 1 + threadIdx.x % share, hs = threadIdx.x / share;
   const int s_end = ny - 1 + lag;
   V acc = 0;
   for (int a0 = 0; a0 < nx; a0 += Wo) {
@@ -869,17 +880,16 @@ __device__ V fused_smooth(const DevLevel& L, int m, bool pre, unsigned win_off, 
     // this thread's ring column `col` is column i of the level
     const int i = c0 - 1 + col;
     const bool live = hs < kFuseShare;
-    const bool mine = live && col >= 1 && col <= Ws - 2;  // a loaded cell
-    const bool face = live && col >= 1 && col <= Ws - 1;  // a loaded x-face (west of cell i)
-    const bool own = live && i >= a0 && i < a1;           // a cell this strip writes
+    const bool mine = live && col <= Ws - 2;  // a loaded cell (and its west x-face)
+    const bool east = mine && col == Ws - 2;  // ... and the strip's last x-face
+    const bool own = live && i >= a0 && i < a1;  // a cell this strip writes
     // loads (share 0: T rows; share 1: rp and z rows; the last share: r rows)
     // walk down the level with running pointers
     // face rows: x-faces of cell row j at tx(j), y-faces of face row f at
     // ty(f) (compact rows on a constant-coefficient level)
-    const int ii = i < 0 ? 0 : i;
     const bool lap = L.lap != 0;
-    auto tx_row = [&](int j) __attribute__((always_inline)) { return gTx + (lap ? 0 : (nx + 1) * j) + ii; };
-    auto ty_row = [&](int f) __attribute__((always_inline)) { return gTy + nx * (lap ? face_row(f, ny) : f) + ii; };
+    auto tx_row = [&](int j) __attribute__((always_inline)) { return gTx + (lap ? 0 : (nx + 1) * j) + i; };
+    auto ty_row = [&](int f) __attribute__((always_inline)) { return gTy + nx * (lap ? face_row(f, ny) : f) + i; };
     const float* prp = grp + off + i;
     const float* pz = gz + off + i;
     if (mine && hs == 0) cp_async4(sTy + col, ty_row(0));  // face row 0
@@ -888,8 +898,12 @@ __device__ V fused_smooth(const DevLevel& L, int m, bool pre, unsigned win_off, 
       if (jl < ny) {
         if (hs == 0) {
           const int fo = lo + Ws == DW ? 0 : lo + Ws;
-          if (face) cp_async4(sTx + lo + col, tx_row(jl));
-          if (mine) cp_async4(sTy + fo + col, ty_row(jl + 1));
+          if (mine) {
+            const float* tx = tx_row(jl);
+            cp_async4(sTx + lo + col, tx);
+            if (east) cp_async4(sTx + lo + col + 1, tx + 1);
+            cp_async4(sTy + fo + col, ty_row(jl + 1));
+          }
         }
         if (hs == kFuseRoleZ && mine) {
           cp_async4(srp + lo + col, prp);
@@ -1051,9 +1065,11 @@ struct RecArgs {
   const float* thrN_f;
   long long* iters;
   long long* calls;
-  // shared memory left after the resident levels: rings of the single-pass
-  // smoother, when allowed
-  unsigned win_off;  // byte offset in the dynamic shared memory
+  // rings of the single-pass smoother, when allowed: the shared memory from
+  // the resident levels' vectors (free while a wider level smooths; zeroed
+  // again after each pass) to the end
+  unsigned win_off;    // byte offset in the dynamic shared memory
+  unsigned vec_bytes;  // the resident vectors at its start
   size_t win_bytes;
   bool fuse;
   int fuse_width, fuse_min_cells;
@@ -1071,8 +1087,22 @@ struct RecArgs {
 template <typename V>
 __device__ __forceinline__ int fuse_wo(const DevLevel& L, int m, const RecArgs& a) {
   if (!a.fuse || a.splitting != 0 || __isShared(L.z) || (long long)L.nx * L.ny < a.fuse_min_cells) return 0;
-  const int w = fuse_width(m, a.win_bytes, (int)sizeof(V), blockDim.x);
-  return a.fuse_width > 0 && a.fuse_width < w ? max(a.fuse_width, kFuseMinWidth) : w;
+  int w = fuse_width(m, a.win_bytes, (int)sizeof(V), blockDim.x);
+  if (w <= 0) return 0;
+  // one strip over the whole level needs no halo columns
+  if (L.nx <= w + 2 * (2 * m + 1)) w = L.nx;
+  if (a.fuse_width > 0 && a.fuse_width < w) w = max(a.fuse_width, kFuseMinWidth);
+  // strips of equal width: as many as width w needs
+  const int ns = (L.nx + w - 1) / w;
+  return (L.nx + ns - 1) / ns;
+}
+
+// After a single pass: the resident levels' vectors, which the rings
+// overwrote, back to zero (their state at placement), then a barrier.
+__device__ __forceinline__ void release_window(const RecArgs& a) {
+  extern __shared__ __align__(16) unsigned char fuse_smem[];
+  zero_block(fuse_smem + a.win_off, a.vec_bytes);
+  __syncthreads();
 }
 
 // Per-level thresholds of the level test and zeroed counters (thread 0),
@@ -1131,6 +1161,7 @@ struct Ops {
           tm.sync();
         }
         fused_smooth<V>(L, m, true, a.win_off, wo, nullptr);
+        release_window(a);
         t_restrict<DIM, RP>(xf_of(L), geo_of(C), (const RP*)L.t, (RP*)C.r);
         tm.sync();
         return;
@@ -1177,6 +1208,7 @@ struct Ops {
       const int wo = fuse_wo<V>(L, m, a);
       if (wo > 0) {
         const V acc = fused_smooth<V>(L, m, false, a.win_off, wo, (float*)L.t);
+        release_window(a);
         // the smoothed z went to the t buffer (free after the restriction):
         // swap the two in this CTA's copy of the level descriptor
         if (threadIdx.x == 0) {
@@ -1406,7 +1438,6 @@ __device__ void recursion(BlockTeam& tm, const DevLevel* sL, int ks, const RecAr
   tm.sync();
 }
 
-__host__ __device__ __forceinline__ size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
 // Shared-memory bytes of level L's arrays when it runs from shared memory:
 // x, r, p, q in the level's vector type, z in RP, the residual t and the
@@ -1421,26 +1452,54 @@ __host__ __device__ __forceinline__ size_t level_smem_bytes(const DevLevel& L, s
   return b;
 }
 
+// Where place_levels put things in the dynamic shared memory.
+struct Placement {
+  int ksm;              // first level placed (kmax + 1: none)
+  size_t ainv_off;      // the coarsest inverse (transposed), or SIZE_MAX
+  size_t vec_off;       // the placed levels' vectors, one block ...
+  size_t vec_bytes;     // ... of this many bytes, zero between solves
+  size_t used;          // end of the block
+};
+
 // Place levels lo..kmax that fit (from the coarsest up) in the dynamic shared
 // memory: rewrite their pointers in sL, zero their vectors (ghosts included)
-// and copy their transmissibilities.  Returns the first level placed.
+// and copy their transmissibilities; then the coarsest inverse, transposed,
+// when it fits as well.  Layout: transmissibilities, the inverse, the
+// vectors.  The vectors come last, so that the single-pass smoother may take
+// them with the free rest as its ring window while no placed level is live.
 template <int DIM, typename RP>
-__device__ int place_levels(DevLevel* sL, const DevLevel* gL, int lo, int kmax, bool top_double, unsigned char* dsm,
-                            size_t budget, size_t* used) {
-  __shared__ int s_ksm;
-  __shared__ size_t s_vec_bytes, s_used;
+__device__ Placement place_levels(DevLevel* sL, const DevLevel* gL, int lo, int kmax, bool top_double,
+                                  unsigned char* dsm, size_t budget, const double* Ainv, int nc) {
+  __shared__ Placement s_pl;
   if (threadIdx.x == 0) {
-    size_t off = 0;
+    size_t tot = 0;
     int ksm = kmax + 1;
     for (int k = kmax; k >= lo; --k) {
       const size_t vsz = (top_double && k == 0) ? sizeof(double) : sizeof(RP);
       const size_t need = level_smem_bytes(sL[k], vsz, sizeof(RP), DIM);
-      if (off + need > budget) break;
-      off += need;
+      if (tot + need > budget) break;
+      tot += need;
       ksm = k;
     }
-    off = 0;
-    // vectors of all placed levels first (one contiguous block to zero)
+    size_t off = 0;
+    for (int k = ksm; k <= kmax; ++k) {
+      DevLevel& L = sL[k];
+      for (int ax = 0; ax < DIM; ++ax) {
+        const size_t nf = (size_t)face_count(L, ax);
+        L.T[ax] = dsm + off;
+        if (sizeof(RP) == sizeof(double)) L.T64[ax] = (const double*)(dsm + off);
+        off += align16(nf * sizeof(RP));
+      }
+    }
+    const size_t ainv = sizeof(double) * (size_t)nc * nc;
+    Placement pl;
+    pl.ksm = ksm;
+    pl.ainv_off = SIZE_MAX;
+    if (tot + align16(ainv) <= budget) {
+      pl.ainv_off = off;
+      off = align16(off + ainv);
+    }
+    pl.vec_off = off;
     for (int k = ksm; k <= kmax; ++k) {
       DevLevel& L = sL[k];
       const size_t vsz = (top_double && k == 0) ? sizeof(double) : sizeof(RP);
@@ -1461,24 +1520,14 @@ __device__ int place_levels(DevLevel* sL, const DevLevel* gL, int lo, int kmax, 
         L.rp = L.r;
       }
     }
-    s_vec_bytes = off;
-    for (int k = ksm; k <= kmax; ++k) {
-      DevLevel& L = sL[k];
-      for (int ax = 0; ax < DIM; ++ax) {
-        const size_t nf = (size_t)face_count(L, ax);
-        L.T[ax] = dsm + off;
-        if (sizeof(RP) == sizeof(double)) L.T64[ax] = (const double*)(dsm + off);
-        off += align16(nf * sizeof(RP));
-      }
-    }
-    s_ksm = ksm;
-    s_used = off;
+    pl.vec_bytes = off - pl.vec_off;
+    pl.used = off;
+    s_pl = pl;
   }
   __syncthreads();
-  const int ksm = s_ksm;
-  *used = s_used;
-  for (size_t e = threadIdx.x; e < s_vec_bytes / 16; e += blockDim.x) ((float4*)dsm)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int k = ksm; k <= kmax; ++k) {
+  const Placement pl = s_pl;
+  zero_block(dsm + pl.vec_off, pl.vec_bytes);
+  for (int k = pl.ksm; k <= kmax; ++k) {
     for (int ax = 0; ax < DIM; ++ax) {
       const DevLevel& L = sL[k];
       const size_t nf = (size_t)face_count(L, ax);
@@ -1487,8 +1536,15 @@ __device__ int place_levels(DevLevel* sL, const DevLevel* gL, int lo, int kmax, 
       for (size_t e = threadIdx.x; e < nf; e += blockDim.x) dst[e] = __ldg(src + e);
     }
   }
+  if (pl.ainv_off != SIZE_MAX) {
+    double* dst = (double*)(dsm + pl.ainv_off);
+    for (int e = threadIdx.x; e < nc * nc; e += blockDim.x) {
+      const int c = e / nc, j = e - c * nc;
+      dst[j * nc + c] = Ainv[e];
+    }
+  }
   __syncthreads();
-  return ksm;
+  return pl;
 }
 
 // Single-CTA kernel.
@@ -1529,37 +1585,20 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallPerSM) k_small(const Prob
     const int kmax = pd.nlev - 1;
     const bool full = mode != 0;
     const int lo = full ? 0 : ks;
-    size_t used = 0;
-    place_levels<DIM, RP>(sL, pd.L, lo, kmax, full, dsm, smem_budget, &used);
+    const Placement pl = place_levels<DIM, RP>(sL, pd.L, lo, kmax, full, dsm, smem_budget, pd.Ainv, pd.nc);
     RecArgs a;
     a.kmax = kmax;
     a.m = pd.m;
     a.nc = pd.nc;
-    a.Ainv = pd.Ainv;
-    a.ainv_t = false;
-    {
-      // the coarsest inverse, transposed, into shared memory when it fits
-      const size_t need = sizeof(double) * (size_t)pd.nc * pd.nc;
-      if (used + need <= smem_budget) {
-        double* dst = (double*)(dsm + used);
-        for (int e = threadIdx.x; e < pd.nc * pd.nc; e += blockDim.x) {
-          const int c = e / pd.nc, j = e - c * pd.nc;
-          dst[j * pd.nc + c] = pd.Ainv[e];
-        }
-        a.Ainv = dst;
-        a.ainv_t = true;
-        __syncthreads();
-      }
-    }
-    {
-      const size_t base = align16(used + (a.ainv_t ? sizeof(double) * (size_t)pd.nc * pd.nc : 0));
-      a.win_off = (unsigned)base;
-      a.win_bytes = smem_budget > base ? smem_budget - base : 0;
-      a.fuse = pd.fuse != 0;
-      a.fuse_width = pd.fuse_width;
-      a.fuse_min_cells = pd.fuse_min_cells;
-      a.splitting = pd.splitting;
-    }
+    a.Ainv = pl.ainv_off != SIZE_MAX ? (const double*)(dsm + pl.ainv_off) : pd.Ainv;
+    a.ainv_t = pl.ainv_off != SIZE_MAX;
+    a.win_off = (unsigned)pl.vec_off;
+    a.win_bytes = smem_budget > pl.vec_off ? smem_budget - pl.vec_off : 0;
+    a.vec_bytes = (unsigned)pl.vec_bytes;
+    a.fuse = pd.fuse != 0;
+    a.fuse_width = pd.fuse_width;
+    a.fuse_min_cells = pd.fuse_min_cells;
+    a.splitting = pd.splitting;
     a.floor2 = S->inner_floor2;
     a.floor2_f = (float)a.floor2;
     bool flex = pd.flex0 != 0;
@@ -2472,7 +2511,7 @@ size_t levels_smem(const msrcg_hier* h, int lo, bool top_double) {
     tot += b;
     kfit = k;
   }
-  const size_t ainv = sizeof(double) * (size_t)h->nc * h->nc;
+  const size_t ainv = align16(sizeof(double) * (size_t)h->nc * h->nc);
   if (tot + ainv <= lim) tot += ainv;
   const long long fmin = h->o.fuse_min_cells > 0 ? h->o.fuse_min_cells : kFuseMinCells;
   if (h->dim == 2 && f32 && fuse_on(h))
