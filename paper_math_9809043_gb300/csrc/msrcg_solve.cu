@@ -770,40 +770,46 @@ __device__ __forceinline__ void zero_block(unsigned char* p, size_t bytes) {
 // ---------------------------------------------------------------------------
 // Single-pass red-black smoothing of a 2D level in global memory (one CTA)
 // ---------------------------------------------------------------------------
-// The 2m+1 half-sweeps of one smoothing run as the stages of a row pipeline:
-// at step s, stage q updates its colour's cells in row s - 2q.  Stage q reads
-// the other colour in rows s-2q-1 .. s-2q+1, which stage q-1 finished at steps
-// s-3 .. s-1, and no two stages of a step touch the same cells, so one barrier
-// per step orders everything and every cell sees exactly the values of the
-// plain half-sweep order.  The level is cut into column strips; a strip loads
-// its columns and 2m+1 more on each side (the cells whose later stages go
-// stale without the neighbouring strip; the neighbour recomputes them with the
-// same arithmetic) into rings of rows in shared memory, prefetched kFuseAhead
-// rows ahead with cp.async.  Each row of T, rp (and z) then crosses HBM once
-// per smoothing instead of once per half-sweep.  kFuseShare threads own each
-// column of the strip and, at step s, share the stages whose row has its
-// colour there; every load of a step precedes its stores.  The rings take the
-// shared memory of the coarse levels resident there, whose vectors hold
-// nothing live while a finer level smooths (they are zeroed again after).
-//   pre  (from zero): stage 0 sets z = rp/D on red cells and 0 on black; after
-//        the last stage a result step forms t = rp - A z and writes z and t.
+// The 2m+1 half-sweeps of one smoothing run as the stages of a row pipeline
+// that advances two rows a step: at step s, stage q updates its colour's cells
+// in rows 2s - 3q and 2s - 3q + 1.  Those two rows hold one cell of each colour
+// per column, so every column takes part in every stage at every step (column
+// i: row 2s - 3q + (i & 1), the colour of half-sweep q there).  Stage q reads
+// the other colour in rows 2s-3q-1 .. 2s-3q+2, which stage q-1 finished at
+// earlier steps (it works on rows 2s-3q+3 and +4 now) and which stage q+1
+// (rows 2s-3q-3 and -2 now) has not yet overwritten; no two stages of a step
+// touch the same cells, so one barrier per step orders everything and every
+// cell gets exactly the values of the plain half-sweep order.  The level is
+// cut into column strips; a strip loads its columns and 2m+1 more on each side
+// (the cells whose later stages go stale without the neighbouring strip; the
+// neighbour recomputes them with the same arithmetic) into rings of rows in
+// shared memory, prefetched kFuseAhead steps ahead with cp.async.  Each row of
+// T, rp (and z) then crosses HBM once per smoothing instead of once per
+// half-sweep.  kFuseShare threads own each column of the strip and share its
+// stages; every load of a step precedes its stores.  The rings take the shared
+// memory of the coarse levels resident there, whose vectors hold nothing live
+// while a finer level smooths (they are zeroed again after).
+//   pre  (from zero): stage 0 sets z = rp/D on red cells and 0 on black; rows
+//        2s - 3S and 2s - 3S + 1, final by then, get t = rp - A z, and z and t
+//        are written.
 //   post (z holds the prolonged pre-smoothing result): the strip reads z and
 //        writes the smoothed z to `zout` (strips read their halo from the
-//        unsmoothed z, so the result cannot go back in place); the last stage
-//        adds r . z over the strip's own cells (returned per thread).
-constexpr int kFuseAhead = 8;    // rows prefetched ahead of stage 0
+//        unsmoothed z, so the result cannot go back in place) two rows behind
+//        the last stage; the last stage's two rows add r . z over the strip's
+//        own cells (returned per thread).
+constexpr int kFuseAhead = 3;    // steps (two rows each) prefetched ahead of stage 0
 constexpr int kFuseMinWidth = 16;
 constexpr int kFuseMinCells = 4096;  // default smallest level that takes the single pass
-constexpr int kFuseMaxM = 4;     // stages per thread <= 3 (two threads per column)
+constexpr int kFuseMaxM = 4;     // stages per thread <= 5 (two threads per column)
 #ifndef MSRCG_FUSE_SHARE
 #define MSRCG_FUSE_SHARE 2
 #endif
 constexpr int kFuseShare = MSRCG_FUSE_SHARE;  // threads per ring column
-// stage entries per thread and step: the column's stages of one parity
-// (at most kFuseMaxM + 1) dealt round kFuseShare threads
-constexpr int kFuseE = (kFuseMaxM + 1 + kFuseShare - 1) / kFuseShare;
-constexpr int kFuseRoleZ = kFuseShare > 1 ? 1 : 0;  // share loading rp / z, adding the black r.z
-// share with the fewest stages: the result (pre) / write-back (post) step and
+// stage entries per thread and step: the column's 2m+1 stages dealt round
+// kFuseShare threads
+constexpr int kFuseE = (2 * kFuseMaxM + 1 + kFuseShare - 1) / kFuseShare;
+constexpr int kFuseRoleZ = kFuseShare > 1 ? 1 : 0;  // share loading rp / z, adding the other colour's r.z
+// share with the fewest stages: the result (pre) / write-back (post) rows and
 // the r rows of the post-smoothing dot
 constexpr int kFuseRoleR = kFuseShare - 1;
 
@@ -816,20 +822,22 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
                : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-// Step s of the pipeline commits group s + kFuseAhead (row s + kFuseAhead
-// and the face row above it); group g holds row g.  Stage 0 at step s reads
-// rows up to s + 1 (post-smoothing: the z row above, loaded from global
-// memory), so all groups but the newest kFuseAhead - 1 must be complete.
+// Step s of the pipeline commits group s + kFuseAhead; group g holds rows 2g
+// and 2g + 1 and the face rows above them.  Stage 0 at step s reads rows up to
+// 2s + 2 (post-smoothing: the z row above, loaded from global memory), so all
+// groups but the newest kFuseAhead - 1 must be complete.
 __device__ __forceinline__ void cp_async_wait_ahead() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(kFuseAhead - 1) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// Ring depths: T / rp / z rows live from the prefetch (s + kFuseAhead, and the
-// face row above it) down to the result step (s - 2S); r rows (post) only
-// from their prefetch to the last stage.
-__host__ __device__ __forceinline__ int fuse_depth(int S) { return 2 * S + kFuseAhead + 3; }
-__host__ __device__ __forceinline__ int fuse_rdepth() { return kFuseAhead + 2; }
+// Ring depths (rows, even): T / rp / z rows live from the prefetch (rows
+// 2(s + kFuseAhead) + 1 and the face row above) down to the result rows
+// (2s - 3S, and the row below); r rows (post) only from their prefetch to
+// the last stage.  A copy issued at step s may land while slower threads
+// still compute step s - 1, hence one step more of each.
+__host__ __device__ __forceinline__ int fuse_depth(int S) { return 3 * S + 2 * kFuseAhead + 5; }
+__host__ __device__ __forceinline__ int fuse_rdepth() { return 2 * kFuseAhead + 4; }
 
 // Output columns per strip that fit `bytes` of shared memory and a CTA of
 // `threads` (kFuseShare threads per loaded column; a ring row also holds the
@@ -851,7 +859,9 @@ __device__ V fused_smooth(const DevLevel& L, int m, bool pre, unsigned win_off, 
   extern __shared__ __align__(16) unsigned char fuse_smem[];
   float* const win = (float*)(fuse_smem + win_off);
   const int S = 2 * m + 1, D = fuse_depth(S), DR = fuse_rdepth();
-  const int lag = pre ? 2 * S : 2 * S - 1;  // result (pre) / write-back (post) row = s - lag
+  // result (pre) / write-back (post) rows of step s: 2s - lag and the next;
+  // the last stage's rows: 2s - lastq and the next
+  const int lag = pre ? 3 * S : 3 * S - 1, lastq = 3 * (S - 1);
   const int nx = L.nx, ny = L.ny, px = L.px, off = (int)L.off;
   const float* gTx = (const float*)L.T[0];
   const float* gTy = (const float*)L.T[1];
@@ -864,7 +874,7 @@ __device__ V fused_smooth(const DevLevel& L, int m, bool pre, unsigned win_off, 
   // ring column (1 + the loaded column), and which share of the column's
   // stages (hs == kFuseShare: the few threads left over, idle)
   const int col = 1 + threadIdx.x % share, hs = threadIdx.x / share;
-  const int s_end = ny - 1 + lag;
+  const int s_end = (ny - 1 + lag) >> 1;  // the step whose result rows reach row ny - 1
   V acc = 0;
   for (int a0 = 0; a0 < nx; a0 += Wo) {
     const int a1 = min(nx, a0 + Wo), c0 = max(0, a0 - S), c1 = min(nx, a1 + S);
@@ -879,9 +889,10 @@ __device__ V fused_smooth(const DevLevel& L, int m, bool pre, unsigned win_off, 
     __syncthreads();
     // this thread's ring column `col` is column i of the level
     const int i = c0 - 1 + col;
+    const int ib = i & 1;  // the row of each stage's pair that has this column's cell
     const bool live = hs < kFuseShare;
-    const bool mine = live && col <= Ws - 2;  // a loaded cell (and its west x-face)
-    const bool east = mine && col == Ws - 2;  // ... and the strip's last x-face
+    const bool mine = live && col <= Ws - 2;     // a loaded cell (and its west x-face)
+    const bool east = mine && col == Ws - 2;     // ... and the strip's last x-face
     const bool own = live && i >= a0 && i < a1;  // a cell this strip writes
     // loads (share 0: T rows; share 1: rp and z rows; the last share: r rows)
     // walk down the level with running pointers
@@ -893,58 +904,70 @@ __device__ V fused_smooth(const DevLevel& L, int m, bool pre, unsigned win_off, 
     const float* prp = grp + off + i;
     const float* pz = gz + off + i;
     if (mine && hs == 0) cp_async4(sTy + col, ty_row(0));  // face row 0
-    int jl = 0, lo = 0;  // next row to load and its ring offset
+    int jl = 0, lo = 0;  // next row pair to load (rows jl, jl + 1) and the ring offset of row jl
     auto load_next = [&]() __attribute__((always_inline)) {
-      if (jl < ny) {
+      if (jl <= ny && mine) {
         if (hs == 0) {
-          const int fo = lo + Ws == DW ? 0 : lo + Ws;
-          if (mine) {
-            const float* tx = tx_row(jl);
-            cp_async4(sTx + lo + col, tx);
-            if (east) cp_async4(sTx + lo + col + 1, tx + 1);
-            cp_async4(sTy + fo + col, ty_row(jl + 1));
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            const int j = jl + r;
+            if (j < ny) {
+              const float* tx = tx_row(j);
+              cp_async4(sTx + lo + r * Ws + col, tx);
+              if (east) cp_async4(sTx + lo + r * Ws + col + 1, tx + 1);
+              // face row j + 1 into the slot of row j + 1
+              const int fo = lo + (r + 1) * Ws;
+              cp_async4(sTy + (fo == DW ? 0 : fo) + col, ty_row(j + 1));
+            }
           }
         }
-        if (hs == kFuseRoleZ && mine) {
-          cp_async4(srp + lo + col, prp);
-          if (!pre) cp_async4(sz + lo + col, pz);
+        if (hs == kFuseRoleZ) {
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            const int j = jl + r;
+            if (j < ny) {
+              cp_async4(srp + lo + r * Ws + col, prp + r * px);
+              if (!pre) cp_async4(sz + lo + r * Ws + col, pz + r * px);
+            } else if (j == ny && !pre) {
+              cp_async4(sz + lo + r * Ws + col, pz + r * px);  // the zero ghost row
+            }
+          }
         }
-        prp += px;
-        pz += px;
-      } else if (jl == ny && !pre && hs == kFuseRoleZ && mine) {
-        cp_async4(sz + lo + col, pz);  // the zero ghost row
       }
-      lo = lo + Ws == DW ? 0 : lo + Ws;
-      ++jl;
+      prp += 2 * px;
+      pz += 2 * px;
+      lo = lo + 2 * Ws == DW ? 0 : lo + 2 * Ws;
+      jl += 2;
     };
     for (int k = 0; k < kFuseAhead; ++k) {
       load_next();
       cp_async_commit();
     }
-    // stage q updates row s - 2q, whose colour at this column is (i+s)&1: the
-    // column takes the stages of that parity, dealt round its threads; the
-    // parity flips every step
-    int par = i & 1;
-    int sbo = 0;  // ring offset of row s
-    const int lago = lag * Ws, lasto = 2 * (S - 1) * Ws;
+    int sbo = 0;  // ring offset of row 2s
     for (int s = 0; s <= s_end; ++s) {
       load_next();
-      int rs = 0;
+      int rs = 0;  // r ring offset of the last stage's first row at this column
       if (!pre) {
-        const int jr = s + kFuseAhead - 2 * (S - 1);
-        if (hs == kFuseRoleR && own && jr >= 0 && jr < ny) {
-          V* dst = sr + (jr % DR) * Ws + col;
-          if (sizeof(V) == 8) cp_async8(dst, gr + off + px * jr + i);
-          else cp_async4(dst, gr + off + px * jr + i);
+        if (hs == kFuseRoleR && own) {
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            const int jr = 2 * (s + kFuseAhead) - lastq + r;
+            if (jr >= 0 && jr < ny) {
+              V* dst = sr + (jr % DR) * Ws + col;
+              if (sizeof(V) == 8) cp_async8(dst, gr + off + px * jr + i);
+              else cp_async4(dst, gr + off + px * jr + i);
+            }
+          }
         }
-        const int jd = s - 2 * (S - 1);
+        const int jd = 2 * s - lastq;  // even: rows jd, jd + 1 sit in neighbouring slots
         rs = (jd >= 0 ? jd % DR : 0) * Ws + col;
       }
       cp_async_commit();
       cp_async_wait_ahead();
       __syncthreads();
-      if (pre && s == ny) {
-        // the zero ghost row above the last row (its slot held an older row)
+      if (pre && (2 * s == ny - 1 || 2 * s == ny)) {
+        // the zero ghost row above the last row (its slot held an older row;
+        // no stage reads that row at this step)
         const int sl = (ny % D) * Ws;
         for (int e = threadIdx.x; e < Ws; e += bd) sz[sl + e] = 0.f;
       }
@@ -954,12 +977,13 @@ __device__ V fused_smooth(const DevLevel& L, int m, bool pre, unsigned win_off, 
         bool act[kFuseE];
 #pragma unroll
         for (int e = 0; e < kFuseE; ++e) {
-          const int q = par + 2 * hs + 2 * kFuseShare * e;
-          act[e] = q < S && s >= 2 * q && s < 2 * q + ny;
+          const int q = hs + kFuseShare * e;
+          const int j = 2 * s - 3 * q + ib;
+          act[e] = q < S && j >= 0 && j < ny;
           ro[e] = 0;
           v[e] = 0.f;
           if (act[e]) {
-            int r0 = sbo - 2 * q * Ws;
+            int r0 = sbo - (3 * q - ib) * Ws;
             if (r0 < 0) r0 += DW;
             const int ru = r0 + Ws == DW ? 0 : r0 + Ws, rd = r0 == 0 ? DW - Ws : r0 - Ws;
             const int c = r0 + col;
@@ -976,40 +1000,45 @@ __device__ V fused_smooth(const DevLevel& L, int m, bool pre, unsigned win_off, 
             }
             v[e] = quot<float>(sm, d);
             ro[e] = c;
-            if (!pre && q == S - 1 && own) acc += sr[rs] * (V)v[e];
+            if (!pre && q == S - 1 && own) acc += sr[rs + ib * Ws] * (V)v[e];
           }
         }
-        if (hs == 0 && pre && par == 1 && s < ny) sz[sbo + col] = 0.f;  // black cell of stage 0's row
-        if (hs == kFuseRoleR) {
-          if (own && s >= lag && s < lag + ny) {
-            int r0 = sbo - lago;
-            if (r0 < 0) r0 += DW;
-            const int c = r0 + col;
-            const float zc = sz[c];
-            const int g = off + px * (s - lag) + i;
-            if (pre) {
-              const int ru = r0 + Ws == DW ? 0 : r0 + Ws, rd = r0 == 0 ? DW - Ws : r0 - Ws;
-              const float a = apply_terms2<float>(sTx[c], sTx[c + 1], sTy[c], sTy[ru + col], zc, sz[c - 1], sz[c + 1],
-                                                  sz[rd + col], sz[ru + col]);
-              gt[g] = srp[c] - a;
+        if (hs == 0 && pre && 2 * s + 1 - ib < ny) sz[sbo + (1 - ib) * Ws + col] = 0.f;  // stage 0's black cell
+        if (hs == kFuseRoleR && own) {
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            const int jw = 2 * s - lag + r;
+            if (jw >= 0 && jw < ny) {
+              int r0 = sbo - (lag - r) * Ws;
+              if (r0 < 0) r0 += DW;
+              const int c = r0 + col;
+              const float zc = sz[c];
+              const int g = off + px * jw + i;
+              if (pre) {
+                const int ru = r0 + Ws == DW ? 0 : r0 + Ws, rd = r0 == 0 ? DW - Ws : r0 - Ws;
+                const float a = apply_terms2<float>(sTx[c], sTx[c + 1], sTy[c], sTy[ru + col], zc, sz[c - 1],
+                                                    sz[c + 1], sz[rd + col], sz[ru + col]);
+                gt[g] = srp[c] - a;
+              }
+              gzo[g] = zc;
             }
-            gzo[g] = zc;
           }
         }
-        if (hs == kFuseRoleZ && !pre && own && par != ((S - 1) & 1)) {
-          // the last stage's row at a cell of the other colour: final already
-          if (s >= 2 * (S - 1) && s < 2 * (S - 1) + ny) {
-            int r0 = sbo - lasto;
+        if (hs == kFuseRoleZ && !pre && own) {
+          // the last stage's other row at this column: a cell of the other
+          // colour, final already
+          const int jo = 2 * s - lastq + 1 - ib;
+          if (jo >= 0 && jo < ny) {
+            int r0 = sbo - (lastq - 1 + ib) * Ws;
             if (r0 < 0) r0 += DW;
-            acc += sr[rs] * (V)sz[r0 + col];
+            acc += sr[rs + (1 - ib) * Ws] * (V)sz[r0 + col];
           }
         }
 #pragma unroll
         for (int e = 0; e < kFuseE; ++e)
           if (act[e]) sz[ro[e]] = v[e];
       }
-      par ^= 1;
-      sbo = sbo + Ws == DW ? 0 : sbo + Ws;
+      sbo = sbo + 2 * Ws == DW ? 0 : sbo + 2 * Ws;
     }
     cp_async_wait_all();
     __syncthreads();
@@ -2487,11 +2516,11 @@ void launch_small_any(int dim, bool f32, const ProblemDesc* P, const int* order,
 }
 
 // Whether the batched solver may smooth HBM-resident levels in one pass.
-// Post-smoothing prefetches the r row its last stage reads kFuseAhead steps
-// ahead, starting at step 0 with row kFuseAhead - 2(S-1) = kFuseAhead - 4m:
-// for 4m < kFuseAhead the first rows would never be loaded, so m = 1 keeps
-// the per-half-sweep passes.
-bool fuse_on(const msrcg_hier* h) { return h->o.plain_sweeps == 0 && 4 * h->o.m >= kFuseAhead; }
+// Post-smoothing prefetches the r rows its last stage reads kFuseAhead steps
+// ahead, starting at step 0 with rows 2 kFuseAhead - 3(S-1) and the next:
+// the last stage's rows of the steps before must all lie below row 0
+// (2 kFuseAhead - 1 < 6m), else they would never be loaded.
+bool fuse_on(const msrcg_hier* h) { return h->o.plain_sweeps == 0 && 6 * h->o.m > 2 * kFuseAhead - 1; }
 
 // Dynamic shared memory of a single-CTA launch for levels lo..kmax of h: the
 // levels that fit (coarsest first) and the coarsest inverse; when a 2D FP32
