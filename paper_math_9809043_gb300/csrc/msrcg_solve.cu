@@ -1163,15 +1163,19 @@ __device__ void flush_counts(SolveState* S, int nlev, const long long* iters, co
 // the smoother type RP elsewhere).
 template <int DIM, typename V, typename RP>
 struct Ops {
-  // PCG entry (x = 0; r holds b_k): ||b_k||^2
+  // PCG entry (x = 0; r holds b_k): ||b_k||^2.  An FP64 level with an
+  // FP32 smoother also gets rp = (FP32) r here and at every update, the
+  // smoother's copy of the right-hand side.
   static __device__ V enter(BlockTeam& tm, const DevLevel& L) {
     V* x = (V*)L.x;
     const V* r = (const V*)L.r;
+    RP* rp = (RP*)L.rp;
     const int npad = (int)L.npad;
     V acc = 0;
     for_lin(npad, [&](int c) { return r[c]; }, [&](int c, V rv) {
       acc += rv * rv;
       x[c] = 0;
+      if (sizeof(V) != sizeof(RP)) rp[c] = (RP)rv;
     });
     return tm.sum<V>(acc);
   }
@@ -1181,14 +1185,8 @@ struct Ops {
     if constexpr (DIM == 2 && sizeof(RP) == sizeof(float)) {
       const int wo = fuse_wo<V>(L, m, a);
       if (wo > 0) {
-        if (sizeof(V) != sizeof(RP)) {
-          // the smoother-precision copy of the right-hand side
-          const V* r = (const V*)L.r;
-          RP* rp = (RP*)L.rp;
-          const int npad = (int)L.npad;
-          for_lin(npad, [&](int c) { return r[c]; }, [&](int c, V v) { rp[c] = (RP)v; });
-          tm.sync();
-        }
+        // (rp, the smoother-precision copy of r, comes from the level entry
+        // or the last update)
         fused_smooth<V>(L, m, true, a.win_off, wo, nullptr);
         release_window(a);
         t_restrict<DIM, RP>(xf_of(L), geo_of(C), (const RP*)L.t, (RP*)C.r);
@@ -1298,6 +1296,7 @@ struct Ops {
     const V alpha = rho / pq;
     V* x = (V*)L.x;
     V* r = (V*)L.r;
+    RP* rp = (RP*)L.rp;
     V acc2 = 0;
     if (flex) {
       V acc3 = 0;
@@ -1309,6 +1308,7 @@ struct Ops {
                 acc3 += rv * (V)v.b;
                 x[c] = xv;
                 r[c] = rv;
+                if (sizeof(V) != sizeof(RP)) rp[c] = (RP)rv;
               });
       rr_out = tm.sum<V>(acc2);
       ct.gamma_d = (double)tm.sum<V>(acc3);
@@ -1321,6 +1321,7 @@ struct Ops {
       acc2 += rv * rv;
       x[c] = xv;
       r[c] = rv;
+      if (sizeof(V) != sizeof(RP)) rp[c] = (RP)rv;
     });
     rr_out = tm.sum<V>(acc2);
     ct.gamma_ok = false;
