@@ -39,7 +39,7 @@ CANDIDATES: List[Dict[str, int]] = [
 
 
 # candidate floors of the FP32 inner levels (the first is the library's)
-FLOORS: List[float] = [1e-6, 1e-5, 1e-4, 1e-3, 3e-3, 1e-2]
+FLOORS: List[float] = [1e-6, 1e-5, 1e-4, 1e-3, 3e-3, 1e-2, 3e-2, 1e-1]
 
 
 def key_of(cand: Dict[str, int]) -> str:
