@@ -448,12 +448,17 @@ def run_3d(args, M, P, dev, stream, nb):
     nb problems per launch with their own sources, and single-solve latency."""
     import numpy as np
     import torch
+    from paper_math_9809043_gb300 import tune as TU
     base = P.grf3d_problem(128)
-    out = {"workload": "3D 128^3 7-point, GRF corr. 8 cells, 1e9 contrast, N(0,1) source", "concurrent_solves": nb}
+    gpu_name = torch.cuda.get_device_name(dev)
+    tuned_rec = TU.best(gpu_name, f"grf3d128x{nb}")
+    tuned = tuned_rec or {}
+    out = {"workload": "3D 128^3 7-point, GRF corr. 8 cells, 1e9 contrast, N(0,1) source", "concurrent_solves": nb,
+           "tile_shapes": TU.key_of(tuned) + (" (autotuner record)" if tuned_rec is not None else "")}
     for prec, key in ((1, "fp32_precond"), (0, "fp64_plain")):
         if prec == 0 and args.no_fp64:
             continue
-        opts = M.default_opts(precision=prec, inner_floor=1e-6 if prec else 0.0)
+        opts = M.default_opts(precision=prec, **({"inner_floor": 1e-6, **tuned} if prec else {"inner_floor": 0.0}))
         hs, bs = [], []
         for j in range(nb):
             rng = np.random.default_rng(1002 * 1000 + j)

@@ -17,7 +17,8 @@ FP64 outer PCG keeps the result at the requested tolerance either way.
 
 Records live in `tuned.json` beside this module, keyed by GPU name and a
 workload key chosen by the caller; `python -m paper_math_9809043_gb300.tune
---out FILE` tunes the 1024^2 and the uneven-batch workloads and writes them.
+--out FILE` tunes the 1024^2 batch, the uneven batch and the 128^3 batch (its
+inner floor only: the single pass is 2D) and writes them.
 """
 from __future__ import annotations
 
@@ -137,6 +138,20 @@ def _grf_batch(n_problems: int, side: int):
     return out
 
 
+def _grf3d_batch(n_problems: int, side: int):
+    import numpy as np
+
+    from . import problems as P
+
+    base = P.grf3d_problem(side)
+    out = []
+    for j in range(n_problems):
+        rng = np.random.default_rng(1002 * 1000 + j)
+        out.append(P.Problem(dim=3, n=base.n, h=base.h, K=base.K, bc=base.bc, gD=base.gD,
+                             f=rng.standard_normal(base.N), pbf=base.pbf))
+    return out
+
+
 def main(argv=None) -> int:
     import argparse
 
@@ -146,12 +161,19 @@ def main(argv=None) -> int:
 
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--out", default=TABLE)
+    ap.add_argument("--workloads", default="grf1024,uneven256,grf3d128",
+                    help="comma-separated subset of grf1024, uneven256, grf3d128")
     args = ap.parse_args(argv)
     gpu = torch.cuda.get_device_name()
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     table = load_table(args.out)
-    for workload, probs in ((f"grf1024x{sms}", _grf_batch(sms, 1024)), ("uneven256", P.batch_problems(256))):
-        fastest, times = tune(probs)
+    # the single pass is 2D only: the 3D batch tunes the inner floor alone
+    work = {"grf1024": lambda: (f"grf1024x{sms}", _grf_batch(sms, 1024), CANDIDATES),
+            "uneven256": lambda: ("uneven256", P.batch_problems(256), CANDIDATES),
+            "grf3d128": lambda: (f"grf3d128x{sms}", _grf3d_batch(sms, 128), [{}])}
+    for name in args.workloads.split(","):
+        workload, probs, cands = work[name]()
+        fastest, times = tune(probs, candidates=cands)
         record(table, gpu, workload, fastest, times)
         print(workload, key_of(fastest), {k: (round(v, 2) if v is not None else None) for k, v in times.items()},
               flush=True)
