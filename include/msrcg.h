@@ -231,6 +231,24 @@ int msrcg_batch_solve(int count, msrcg_hier* const* hs, const double* const* b, 
  * the last solve.  Errors: MSRCG_EINVAL for a bad level. */
 int msrcg_level_info(const msrcg_hier* h, int level, int dims[3], int64_t* iters, int64_t* calls);
 
+/* The level tree of the solves of h (Fig. 2 of the paper: how many iterations
+ * each call of each level's PCG takes, Sec. 3).  buf: device memory the
+ * caller owns and keeps alive while attached, 16-byte aligned,
+ * 16 + 16 * capacity bytes: a uint64 entry count (set to 0 at the start of
+ * every msrcg_solve / msrcg_batch_solve of h; it counts past `capacity`, the
+ * entries beyond are dropped), 8 unused bytes, then `capacity` entries of
+ * four int32: level, call (0-based index of this call of the level's PCG
+ * within the solve), iterations of that call, pass (0, or 1..3 for the
+ * restarts from the true residual).  One entry per PCG call, written when
+ * the call returns (so a coarse call precedes the finer call that made it);
+ * the inner levels of the multigrid preconditioner (precond 1) run no PCG
+ * and have none.  buf = NULL detaches.  While a buffer is attached,
+ * msrcg_solve runs every level in the single-CTA solver (one launch, no
+ * graph; slower on wide levels).
+ *  Errors: MSRCG_EINVAL (h NULL, capacity < 0 or above 2^31 - 1, buf not
+ *  16-byte aligned). */
+int msrcg_set_trace(msrcg_hier* h, void* buf, int64_t capacity);
+
 /* Copy level k's transmissibilities (FP64) into device arrays Tx
  * ((nx+1)*ny*nz), Ty (nx*(ny+1)*nz) and, in 3D, Tz (nx*ny*(nz+1)); Tz may be
  * NULL in 2D.  Stream ordered.  Errors: MSRCG_EINVAL, MSRCG_ECUDA. */

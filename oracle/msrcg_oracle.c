@@ -72,6 +72,11 @@ typedef struct {
   int precond;                          /* preconditioner of the level-0 PCG (Sec. 2): 0 recursive
                                            multi-scale (eq. 2.10), 1 multigrid (eq. 2.9, Tatebe),
                                            2 polynomial (eq. 2.6 with W = P^-1) */
+  /* level tree (Fig. 2): one entry (level, call, iterations, pass) per PCG
+     call, written when the call returns; NULL when off */
+  int32_t *trace;
+  int64_t trace_cap, trace_n;
+  int pass;                             /* restart of or_solve (0 .. 3) */
 } or_hier;
 
 static int64_t idx3(int i, int j, int k, int nx, int ny) {
@@ -765,7 +770,7 @@ static void precond(or_hier *H, int k, const double *r, double *z) {
  * x = 0.  Convergence on level k (Sec. 3): ||r||^2 / N_k < f^k eps^2, tested
  * after each update.  Level 0 uses eps^2 = tau^2 ||b||^2 / N_0.
  * ------------------------------------------------------------------------- */
-static void pcg(or_hier *H, int k, const double *b, double *x) {
+static void pcg_run(or_hier *H, int k, const double *b, double *x) {
   or_level *L = &H->L[k];
   int64_t n = L->n;
   double fk = 1.0;
@@ -807,6 +812,31 @@ static void pcg(or_hier *H, int k, const double *b, double *x) {
   }
 }
 
+/* One PCG call of level k and its entry in the level tree (Fig. 2: the
+ * iterations each call of each level takes).  The call's index is the
+ * level's call counter before it. */
+static void pcg(or_hier *H, int k, const double *b, double *x) {
+  const int64_t call = H->calls[k], it0 = H->iters[k];
+  pcg_run(H, k, b, x);
+  if (H->trace) {
+    if (H->trace_n < H->trace_cap) {
+      int32_t *e = H->trace + 4 * H->trace_n;
+      e[0] = k;
+      e[1] = (int32_t)call;
+      e[2] = (int32_t)(H->iters[k] - it0);
+      e[3] = H->pass;
+    }
+    H->trace_n++;
+  }
+}
+
+void or_set_trace(or_hier *H, int32_t *buf, int64_t cap) {
+  H->trace = buf;
+  H->trace_cap = buf ? cap : 0;
+  H->trace_n = 0;
+}
+int64_t or_trace_count(const or_hier *H) { return H->trace_n; }
+
 /* Solve A x = b to relative residual tau.  The level-0 PCG runs on the
  * recursive residual; afterwards the true residual b - A x is formed and, if
  * it misses tau, the PCG is restarted from it (at most 3 restarts).
@@ -816,6 +846,8 @@ int or_solve(or_hier *H, const double *b, double tau, double *x, double *out) {
   int64_t n = L->n;
   double bb = dot(b, b, n);
   or_reset_stats(H);
+  H->trace_n = 0;
+  H->pass = 0;
   memset(x, 0, sizeof(double) * n);
   out[0] = out[1] = 0.0;
   if (bb == 0.0) return OR_OK;
@@ -823,6 +855,7 @@ int or_solve(or_hier *H, const double *b, double tau, double *x, double *out) {
   double *rt = malloc(sizeof(double) * n), *dx = malloc(sizeof(double) * n);
   memcpy(rt, b, sizeof(double) * n);
   for (int restart = 0; restart < 4; ++restart) {
+    H->pass = restart;
     pcg(H, 0, rt, dx);
     for (int64_t i = 0; i < n; ++i) x[i] += dx[i];
     out[0] = sqrt(dot(L->r, L->r, n) / bb);

@@ -83,6 +83,10 @@ def lib():
         L.or_set_splitting.argtypes = [C.c_void_p, C.c_int]
         L.or_set_splitting.restype = None
         L.or_set_precond.argtypes = [C.c_void_p, C.c_int]
+        L.or_set_trace.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
+        L.or_set_trace.restype = None
+        L.or_trace_count.argtypes = [C.c_void_p]
+        L.or_trace_count.restype = C.c_int64
         L.or_set_precond.restype = None
         for name in ("or_apply_level", "or_sgs_level", "or_jacobi_level", "or_lex_level", "or_restrict_level",
                      "or_prolong_level"):
@@ -244,15 +248,26 @@ class Hierarchy:
                           np.ascontiguousarray(p.pbf, np.float64), b)
         return b
 
-    def solve(self, b, tau):
+    def solve(self, b, tau, trace_cap=0):
+        """x and stats; with trace_cap > 0 the stats also hold the level tree
+        (Fig. 2): "trace" = [(level, call, iterations, pass), ...] in the
+        order the PCG calls returned, "trace_count" = all of them."""
         x = np.zeros(self.ncells(0))
         out = np.zeros(2)
+        buf = np.zeros(4 * max(int(trace_cap), 1), np.int32)
+        lib().or_set_trace(self._h, buf.ctypes.data if trace_cap > 0 else None, int(trace_cap))
         st = lib().or_solve(self._h, np.ascontiguousarray(b, np.float64), tau, x, out)
         it = np.zeros(MAXLEV, np.int64)
         ca = np.zeros(MAXLEV, np.int64)
         lib().or_get_stats(self._h, it, ca)
-        return x, {"status": st, "iters": it[:self.nlev].tolist(), "calls": ca[:self.nlev].tolist(),
-                   "relres_recursive": float(out[0]), "relres_true": float(out[1])}
+        res = {"status": st, "iters": it[:self.nlev].tolist(), "calls": ca[:self.nlev].tolist(),
+               "relres_recursive": float(out[0]), "relres_true": float(out[1])}
+        if trace_cap > 0:
+            n = int(lib().or_trace_count(self._h))
+            res["trace_count"] = n
+            res["trace"] = [tuple(int(v) for v in e) for e in buf[:4 * min(n, int(trace_cap))].reshape(-1, 4)]
+            lib().or_set_trace(self._h, None, 0)
+        return x, res
 
     # ---- level-wise operators (tests) ----
     def apply(self, k, x):

@@ -161,6 +161,8 @@ struct ProblemDesc {
   int allow_flex;        // the stall test / an inner cap may switch to the flexible beta
   int flex0;             // flexible beta from the first iteration
   int precond;           // 0: recursive multi-scale (eq. 2.10), 1: multigrid (eq. 2.9), 2: polynomial
+  unsigned long long* trace;  // level-tree buffer (msrcg_set_trace) or null
+  int trace_cap;              // its entries
 };
 
 }  // namespace msrcg
@@ -178,6 +180,8 @@ struct msrcg_hier {
   void* TR[MSRCG_MAXLEV][3] = {};       // smoother precision copy (aliases T64 in FP64 mode)
   msrcg::DevLevel hL[MSRCG_MAXLEV] = {};
   msrcg::DevLevel* dL = nullptr;
+  void* trace = nullptr;                // level-tree buffer (msrcg_set_trace), caller owned
+  long long trace_cap = 0;
   double* Ainv = nullptr;
   int nc = 0;
   msrcg::SolveState* dS = nullptr;

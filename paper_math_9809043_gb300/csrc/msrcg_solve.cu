@@ -1109,7 +1109,19 @@ struct RecArgs {
   bool allow_flex;
   int stall_w;
   int precond;  // 0: recursive multi-scale (eq. 2.10), 1: multigrid (eq. 2.9), 2: polynomial (eq. 2.6, W = P^-1)
+  // level tree (msrcg_set_trace): count, pad, then entries (level, call,
+  // iterations, pass); null when off
+  unsigned long long* trace;
+  int trace_cap;
+  int pass;  // 0, or the restart from the true residual
 };
+
+// One level-tree entry (thread 0): level k's PCG call that just returned.
+__device__ __forceinline__ void trace_call(const RecArgs& a, int k, int it) {
+  const unsigned long long e = atomicAdd(a.trace, 1ULL);
+  if (e < (unsigned long long)a.trace_cap)
+    reinterpret_cast<int4*>(a.trace + 2)[e] = make_int4(k, (int)(a.calls[k] - 1), it, a.pass);
+}
 
 // Strip width of the single-pass smoother for level L, or 0 for the plain
 // half-sweeps (levels in shared memory, small levels, no room).
@@ -1356,6 +1368,7 @@ __device__ void recursion(BlockTeam& tm, const DevLevel* sL, int ks, const RecAr
     const bool dbl = a.top_double && k == 0;
     if (c.phase == kStart) {
       if (threadIdx.x == 0) a.calls[k]++;
+      c.it = 0;
       if (a.precond == 1 && k > 0) {
         // multigrid (eq. 2.9): this level applies its preconditioner once
         // to r_k; no PCG, no level test
@@ -1461,6 +1474,8 @@ __device__ void recursion(BlockTeam& tm, const DevLevel* sL, int ks, const RecAr
         c.phase = kIterate;
       }
     } else {  // kReturn
+      // (the multigrid preconditioner's inner levels run no PCG)
+      if (a.trace && threadIdx.x == 0 && !(a.precond == 1 && k > 0)) trace_call(a, k, c.it);
       if (k == ks) break;
       --k;
     }
@@ -1636,6 +1651,9 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallPerSM) k_small(const Prob
     a.allow_flex = pd.allow_flex != 0;
     a.stall_w = pd.stall_w;
     a.precond = pd.precond;
+    a.trace = pd.trace;
+    a.trace_cap = pd.trace_cap;
+    a.pass = 0;
     a.S = S;
     a.top_double = full;
     a.rc = s_rc;
@@ -1702,6 +1720,7 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallPerSM) k_small(const Prob
     level_consts(sL, pd.nlev, eps2, s_thrN_d, s_thrN_f, s_iters, s_calls);
     if (bb > 0.0 && isfinite(bb)) {
       for (int pass = 0; pass < 4; ++pass) {
+        a.pass = pass;
         recursion<DIM, RP>(bt, sL, 0, a);
         for (int c = threadIdx.x; c < (int)L0.npad; c += blockDim.x) xs[c] += x0[c];
         __syncthreads();
@@ -2577,6 +2596,8 @@ ProblemDesc make_desc(msrcg_hier* h, const double* b, double* x, double tol) {
                    : 0;
   pd.flex0 = h->o.flexible;
   pd.precond = h->o.precond;
+  pd.trace = (unsigned long long*)h->trace;
+  pd.trace_cap = (int)h->trace_cap;
   return pd;
 }
 
@@ -2638,8 +2659,10 @@ extern "C" int msrcg_solve(msrcg_hier* h, const double* b, double tol, double* x
   }
   SolveState hs;
   int restarts = 0;
-  if (h->ks == 0) {
-    // every level fits one CTA: one launch runs the whole solve
+  if (h->trace) MSRCG_CUDA_TRY(cudaMemsetAsync(h->trace, 0, sizeof(unsigned long long), s));
+  if (h->ks == 0 || h->trace) {
+    // every level fits one CTA, or the level tree is traced: one launch runs
+    // the whole solve
     launch_small_any(dim, f32, h->dP, nullptr, 1, 0, 2, nullptr, 1, levels_smem(h, 0, true), s);
     MSRCG_CUDA_TRY(cudaGetLastError());
   } else {
@@ -2717,6 +2740,7 @@ int msrcg_batch_enqueue(int count, msrcg_hier* const* hs, const double* const* b
       hs[i]->dirty = false;
     }
     pds[i] = make_desc(hs[i], b[i], x[i], tol);
+    if (hs[i]->trace) MSRCG_CUDA_TRY(cudaMemsetAsync(hs[i]->trace, 0, sizeof(unsigned long long), s));
     const double floor2 = prec == 1 ? hs[i]->o.inner_floor * hs[i]->o.inner_floor : 0.0;
     MSRCG_CUDA_TRY(cudaMemcpyAsync(&hs[i]->dS->inner_floor2, &floor2, sizeof(double), cudaMemcpyHostToDevice, s));
   }
@@ -2768,6 +2792,13 @@ int msrcg_batch_finish(int count, msrcg_hier* const* hs, const SolveState* host_
     }
   }
   return rc;
+}
+
+extern "C" int msrcg_set_trace(msrcg_hier* h, void* buf, int64_t capacity) {
+  if (!h || capacity < 0 || capacity > INT32_MAX || ((uintptr_t)buf & 15)) return MSRCG_EINVAL;
+  h->trace = buf;
+  h->trace_cap = buf ? capacity : 0;
+  return MSRCG_OK;
 }
 
 extern "C" int msrcg_batch_solve(int count, msrcg_hier* const* hs, const double* const* b, double tol, double* const* x,

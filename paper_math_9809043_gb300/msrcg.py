@@ -102,6 +102,7 @@ def lib():
         L.msrcg_profile_kernel_name.argtypes = [C.c_int]
         L.msrcg_profile_kernel_name.restype = C.c_char_p
         L.msrcg_profile_level.argtypes = [vp, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
+        L.msrcg_set_trace.argtypes = [vp, vp, C.c_int64]
         L.msrcg_strerror.argtypes = [C.c_int]
         L.msrcg_strerror.restype = C.c_char_p
         _lib = L
@@ -367,6 +368,31 @@ class Hierarchy:
         if rc != OK:
             raise MsrcgError(rc, "msrcg_get_trans")
         return Tx, Ty, Tz
+
+    def set_trace(self, capacity):
+        """Attach a level-tree buffer of `capacity` entries (msrcg_set_trace);
+        capacity 0 detaches.  The buffer is a device tensor held here."""
+        if capacity <= 0:
+            rc = lib().msrcg_set_trace(self._h, None, 0)
+            self._trace = None
+        else:
+            buf = torch.zeros(4 + 4 * int(capacity), dtype=torch.int32, device=self.device)
+            rc = lib().msrcg_set_trace(self._h, _ptr(buf), int(capacity))
+            self._trace = buf if rc == OK else None
+        if rc != OK:
+            raise MsrcgError(rc, "msrcg_set_trace")
+
+    def trace(self):
+        """The level tree of the last solve: (total entries, [(level, call,
+        iterations, pass), ...]) in the order the calls returned."""
+        buf = getattr(self, "_trace", None)
+        if buf is None:
+            return 0, []
+        host = buf.cpu()
+        count = int(host[:2].view(torch.int64)[0])
+        n = min(count, (host.numel() - 4) // 4)
+        ent = host[4:4 + 4 * n].view(-1, 4).tolist()
+        return count, [tuple(e) for e in ent]
 
     def profile_level(self, k, reps=20, stream=None):
         """Per-kernel mean launch time (ms) and algorithmic bytes of level k's

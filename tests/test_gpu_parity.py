@@ -859,3 +859,49 @@ def test_laplace_uses_less_memory(M):
         B = M.Hierarchy.laplace(2, prob.n, prob.h, 1.0, [1, 1, 0, 0, 0, 0], opts)
         saved = A.device_bytes() - B.device_bytes()
         assert saved >= (16 + (8 if prec else 0)) * prob.N, (A.device_bytes(), B.device_bytes())
+
+
+# ---------------------------------------------------------------------------
+# level tree (Fig. 2; msrcg_set_trace)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", [0, 1])
+def test_level_tree_trace(M, prec):
+    """The level tree of a solve through the C ABI: its structure as eq. 2.10
+    fixes it (tests/trees.py), against the solve's own counters; in FP64 the
+    oracle's tree of the same problem (per-call iterations equal where the
+    per-level totals are, else totals within the 3% band); the same tree from
+    msrcg_solve (routed to the single-CTA solver while tracing) and from the
+    batched path; a capacity below the number of calls keeps the first
+    entries and counts them all; detaching stops the recording."""
+    from trees import check_tree
+    prob = P.grf_problem((200, 72), seed=21, ell=6.0, half_span=4.5)
+    opts = M.default_opts(precision=prec, small_cells=256, **({"inner_floor": 1e-6} if prec else {}))
+    H = M.Hierarchy.from_problem(prob, opts)
+    assert H.nlev >= 3
+    b = H.rhs_for(prob)
+    H.set_trace(1 << 16)
+    x, st = H.solve(b, 1e-8)
+    assert st["status"] == 0 and st["relres_true"] < 1e-8
+    count, tr = H.trace()
+    assert count == len(tr) == sum(st["calls"])
+    check_tree(tr, st["iters"], st["calls"], H.nlev)
+    xs, sts = M.batch_solve([H], [b], 1e-8)
+    count2, tr2 = H.trace()
+    check_tree(tr2, sts[0]["iters"], sts[0]["calls"], H.nlev)
+    if prec == 0:
+        assert tr2 == tr  # same launch shape, same arithmetic
+        R = O.Hierarchy(prob)
+        xr, sr = R.solve(R.lift_rhs(), 1e-8, trace_cap=1 << 16)
+        assert sr["trace_count"] == len(sr["trace"])
+        if sr["iters"] == st["iters"]:
+            assert [e[:3] for e in tr] == [e[:3] for e in sr["trace"]]
+        else:
+            _counts_close(st["iters"], sr["iters"], sr["calls"])
+        assert [e[2] for e in tr if e[0] == 0] == [e[2] for e in sr["trace"] if e[0] == 0]
+    H.set_trace(3)
+    H.solve(b, 1e-8)
+    count3, tr3 = H.trace()
+    assert count3 == count and len(tr3) == 3 and tr3 == tr[:3]
+    H.set_trace(0)
+    x4, st4 = H.solve(b, 1e-8)
+    assert st4["status"] == 0 and H.trace() == (0, [])

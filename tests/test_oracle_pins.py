@@ -1117,3 +1117,26 @@ def test_paper_claims_on_the_preconditioners():
     assert all(it[n, 1] > it[n, 0] for n in (64, 128, 256))
     assert it[256, 1] > it[64, 1] + 5
     assert it[128, 2] > 2 * it[64, 2] and it[64, 2] > 3 * it[64, 1]
+
+
+def test_level_tree_of_the_oracle_has_the_recursion_structure():
+    """The oracle's level tree (Fig. 2) against the structure eq. 2.10 fixes
+    (tests/trees.py): children per call = the call's iterations, calls in
+    order, totals = the level counters, one iteration per coarsest call; and
+    a capacity below the number of calls keeps the first entries and counts
+    them all."""
+    from trees import check_tree
+    prob = P.grf_problem((48, 40), seed=5, ell=4.0, half_span=3.0)
+    R = O.Hierarchy(prob)
+    x, st = R.solve(R.lift_rhs(), 1e-8, trace_cap=1 << 16)
+    assert st["status"] == 0
+    tr = st["trace"]
+    assert st["trace_count"] == len(tr) == sum(st["calls"])
+    assert R.nlev >= 3
+    check_tree(tr, st["iters"], st["calls"], R.nlev)
+    # later coarse calls take fewer iterations than the first (Fig. 2's shape)
+    lev1 = [e[2] for e in tr if e[0] == 1]
+    assert len(lev1) >= 2 and lev1[-1] <= lev1[0]
+    x2, st2 = R.solve(R.lift_rhs(), 1e-8, trace_cap=5)
+    assert st2["trace_count"] == len(tr) and st2["trace"] == tr[:5]
+    assert np.array_equal(x, x2)
