@@ -374,6 +374,26 @@ __device__ __forceinline__ R gs_value(const LV& L, const R* Tx, const R* Ty, con
   return quot<R>(s, d);
 }
 
+// The numerator of gs_value alone, rhs_c + sum_f T_f x_nb (the same terms
+// in the same order), for the FP64 smoother, which multiplies it by the
+// cell's reciprocal diagonal instead of dividing.
+template <int DIM, typename R, class LV>
+__device__ __forceinline__ R gs_sum(const LV& L, const R* Tx, const R* Ty, const R* Tz, R rhs, const R* x, int i,
+                                    const Row& r) {
+  const int pc = r.pc + i;
+  R s = rhs;
+  s += Tx[r.fx + i] * x[pc - 1];
+  s += Tx[r.fx + i + 1] * x[pc + 1];
+  s += Ty[r.fy + i] * x[pc - L.px];
+  s += Ty[r.fy + i + L.nx] * x[pc + L.px];
+  if (DIM == 3) {
+    const int pl = (int)L.plane;
+    s += Tz[r.fz + i] * x[pc - pl];
+    s += Tz[r.fz + i + L.nx * L.ny] * x[pc + pl];
+  }
+  return s;
+}
+
 // (A x)_c = sum_f T_f (x_c - x_nb); a boundary face gives T_f x_c.
 template <int DIM, typename R, typename RX, class LV>
 __device__ __forceinline__ R apply_value(const LV& L, const R* Tx, const R* Ty, const R* Tz, const RX* x, int i,
@@ -482,8 +502,11 @@ __device__ __forceinline__ TLevel<RP> tlevel_of(const DevLevel& L) {
   return t;
 }
 
+// One red/black half-sweep of a level by the team.  inv: the cells'
+// reciprocal diagonals (padded layout), or null to divide.
 template <int DIM, typename RP, typename V>
-__device__ __forceinline__ V t_sweep(const TLevel<RP>& S, int colour, const V* r, RP* rp, RP* z, int mode) {
+__device__ __forceinline__ V t_sweep(const TLevel<RP>& S, int colour, const V* r, RP* rp, RP* z, int mode,
+                                     const RP* inv = nullptr) {
   const Geo& G = S.G;
   V acc = 0;
   if (mode == kZero) {
@@ -496,7 +519,9 @@ __device__ __forceinline__ V t_sweep(const TLevel<RP>& S, int colour, const V* r
       } else {
         rhs = rp[pc];
       }
-      z[pc] = ((i + rw.j + rw.k) & 1) == colour ? quot<RP>(rhs, diag_of<DIM, RP>(G, S.Tx, S.Ty, S.Tz, i, rw)) : (RP)0;
+      z[pc] = ((i + rw.j + rw.k) & 1) == colour
+                  ? (inv ? rhs * inv[pc] : quot<RP>(rhs, diag_of<DIM, RP>(G, S.Tx, S.Ty, S.Tz, i, rw)))
+                  : (RP)0;
     });
   } else {
     const bool dot = mode == kDot;
@@ -506,7 +531,8 @@ __device__ __forceinline__ V t_sweep(const TLevel<RP>& S, int colour, const V* r
       const int base = rw.pc;
       if (dot && i2 < G.nx) acc += r[base + i2] * (V)z[base + i2];
       if (i < G.nx) {
-        const RP v = gs_value<DIM, RP, RP>(G, S.Tx, S.Ty, S.Tz, rp[base + i], z, i, rw);
+        const RP v = inv ? gs_sum<DIM, RP>(G, S.Tx, S.Ty, S.Tz, rp[base + i], z, i, rw) * inv[base + i]
+                         : gs_value<DIM, RP, RP>(G, S.Tx, S.Ty, S.Tz, rp[base + i], z, i, rw);
         if (dot) acc += r[base + i] * (V)v;
         z[base + i] = v;
       }
@@ -646,6 +672,9 @@ __device__ V t_smooth(BlockTeam& tm, const DevLevel& L, const TLevel<RP>& S, int
       }
     }
     const int colour = (i + j + k) & 1;
+    // FP64: multiply by the reciprocal diagonal, as the general path does
+    const bool fp64 = sizeof(RP) == sizeof(double);
+    const RP dinv = fp64 ? (RP)1 / d : (RP)0;
     auto gs = [&]() __attribute__((always_inline)) {
       RP dd, sm = rp[pc];
       gs_terms2<RP>(dd, sm, tw, te, ts, tn, z[pc - 1], z[pc + 1], z[pc - G.px], z[pc + G.px]);
@@ -653,7 +682,7 @@ __device__ V t_smooth(BlockTeam& tm, const DevLevel& L, const TLevel<RP>& S, int
         sm += tb * z[pc - G.plane];
         sm += tt * z[pc + G.plane];
       }
-      z[pc] = quot<RP>(sm, d);
+      z[pc] = fp64 ? sm * dinv : quot<RP>(sm, d);
     };
     if (own) {
       if (from_zero) {
@@ -664,7 +693,7 @@ __device__ V t_smooth(BlockTeam& tm, const DevLevel& L, const TLevel<RP>& S, int
         } else {
           rhs = rp[pc];
         }
-        z[pc] = colour == 0 ? quot<RP>(rhs, d) : (RP)0;
+        z[pc] = colour == 0 ? (fp64 ? rhs * dinv : quot<RP>(rhs, d)) : (RP)0;
       } else if (colour == 0) {
         gs();
       }
@@ -677,13 +706,25 @@ __device__ V t_smooth(BlockTeam& tm, const DevLevel& L, const TLevel<RP>& S, int
     }
     return (V)0;
   }
-  t_sweep<DIM, RP, V>(S, 0, r, rp, z, from_zero ? kZero : kNormal);
+  // FP64: the reciprocal diagonals once per smoothing, in the t buffer (free
+  // while smoothing): a half-sweep then multiplies instead of dividing (the
+  // FP64 division is a long sequence on the narrow FP64 pipe)
+  const RP* inv = nullptr;
+  if (sizeof(RP) == sizeof(double)) {
+    RP* w = (RP*)L.t;
+    for_cells<DIM>(S.all, G, [&](int i, const Row& rw) {
+      w[rw.pc + i] = (RP)1 / diag_of<DIM, RP>(G, S.Tx, S.Ty, S.Tz, i, rw);
+    });
+    tm.sync();
+    inv = w;
+  }
+  t_sweep<DIM, RP, V>(S, 0, r, rp, z, from_zero ? kZero : kNormal, inv);
   tm.sync();
   for (int s = 0; s < m; ++s) {
-    t_sweep<DIM, RP, V>(S, 1, r, rp, z, kNormal);
+    t_sweep<DIM, RP, V>(S, 1, r, rp, z, kNormal, inv);
     tm.sync();
     const bool last = s == m - 1;
-    const V d = t_sweep<DIM, RP, V>(S, 0, r, rp, z, dot && last ? kDot : kNormal);
+    const V d = t_sweep<DIM, RP, V>(S, 0, r, rp, z, dot && last ? kDot : kNormal, inv);
     if (dot && last) return tm.sum<V>(d);
     tm.sync();
   }
