@@ -1956,6 +1956,8 @@ __global__ void k_sweep(DevLevel L, int colour, int zero) {
   const V* r = (const V*)L.r;
   RP* rp = (RP*)L.rp;
   RP* z = (RP*)L.z;
+  // FP64: the reciprocal diagonals k_inv_diag wrote into t for this smoothing
+  const RP* inv = sizeof(RP) == sizeof(double) ? (const RP*)L.t : nullptr;
   if (zero) {
     for_cells<DIM>(grid_map(), L, [&](int i, const Row& rw) {
       const int pc = rw.pc + i;
@@ -1966,13 +1968,28 @@ __global__ void k_sweep(DevLevel L, int colour, int zero) {
       } else {
         rhs = rp[pc];
       }
-      z[pc] = ((i + rw.j + rw.k) & 1) == colour ? quot<RP>(rhs, diag_of<DIM, RP>(L, Tx, Ty, Tz, i, rw)) : (RP)0;
+      z[pc] = ((i + rw.j + rw.k) & 1) == colour
+                  ? (inv ? rhs * inv[pc] : quot<RP>(rhs, diag_of<DIM, RP>(L, Tx, Ty, Tz, i, rw)))
+                  : (RP)0;
     });
   } else {
     for_colour<DIM>(grid_map(), L, colour, [&](int i, int, const Row& rw) {
-      if (i < L.nx) z[rw.pc + i] = gs_value<DIM, RP, RP>(L, Tx, Ty, Tz, rp[rw.pc + i], z, i, rw);
+      if (i < L.nx)
+        z[rw.pc + i] = inv ? gs_sum<DIM, RP>(L, Tx, Ty, Tz, rp[rw.pc + i], z, i, rw) * inv[rw.pc + i]
+                           : gs_value<DIM, RP, RP>(L, Tx, Ty, Tz, rp[rw.pc + i], z, i, rw);
     });
   }
+}
+
+// The cells' reciprocal diagonals 1/D into the t buffer (free while the level
+// smooths), for the FP64 half-sweeps of one smoothing.
+template <int DIM, typename RP>
+__global__ void k_inv_diag(DevLevel L) {
+  const RP *Tx = (const RP*)L.T[0], *Ty = (const RP*)L.T[1], *Tz = (const RP*)L.T[2];
+  RP* w = (RP*)L.t;
+  for_cells<DIM>(grid_map(), L, [&](int i, const Row& rw) {
+    w[rw.pc + i] = (RP)1 / diag_of<DIM, RP>(L, Tx, Ty, Tz, i, rw);
+  });
 }
 
 // The last red half-sweep of post-smoothing, with rho = r . z over all cells
@@ -1983,11 +2000,13 @@ __global__ void k_sweep_rho(DevLevel L, int k, SolveState* S, double* partials) 
   const V* r = (const V*)L.r;
   const RP* rp = (const RP*)L.rp;
   RP* z = (RP*)L.z;
+  const RP* inv = sizeof(RP) == sizeof(double) ? (const RP*)L.t : nullptr;
   V acc = 0;
   for_colour<DIM>(grid_map(), L, 0, [&](int i, int i2, const Row& rw) {
     if (i2 < L.nx) acc += r[rw.pc + i2] * (V)z[rw.pc + i2];
     if (i < L.nx) {
-      const RP v = gs_value<DIM, RP, RP>(L, Tx, Ty, Tz, rp[rw.pc + i], z, i, rw);
+      const RP v = inv ? gs_sum<DIM, RP>(L, Tx, Ty, Tz, rp[rw.pc + i], z, i, rw) * inv[rw.pc + i]
+                       : gs_value<DIM, RP, RP>(L, Tx, Ty, Tz, rp[rw.pc + i], z, i, rw);
       acc += r[rw.pc + i] * (V)v;
       z[rw.pc + i] = v;
     }
@@ -2384,6 +2403,7 @@ void emit_smooth(const DevLevel& L, int m, bool from_zero, bool with_rho, int k,
     }
     return;
   }
+  if (sizeof(RP) == sizeof(double)) k_inv_diag<DIM, RP><<<lc.grid, lc.block, 0, s>>>(L);
   if (from_zero) k_sweep<DIM, RP, V><<<lc.grid, lc.block, 0, s>>>(L, 0, 1);
   else k_sweep<DIM, RP, V><<<lp.grid, lp.block, 0, s>>>(L, 0, 0);
   for (int i = 0; i < m; ++i) {
@@ -2902,7 +2922,8 @@ __global__ void k_fill_ones(DevLevel L, DevLevel C) {
 const char* const kProfNames[] = {
     "k_sweep (red-black half-sweep)", "k_sweep (first half-sweep, from zero)", "k_sweep_rho (last half-sweep + r.z)",
     "k_residual (t = rp - A z)", "k_restrict (r_c = R t)", "k_prolong_black (z += E x_c, black cells)",
-    "k_direction (p = z + beta p)", "k_apply_dot (q = A p, p.q)", "k_update (x += alpha p, r -= alpha q, r.r)"};
+    "k_direction (p = z + beta p)", "k_apply_dot (q = A p, p.q)", "k_update (x += alpha p, r -= alpha q, r.r)",
+    "k_inv_diag (1/D for the FP64 half-sweeps)"};
 constexpr int kProfCount = (int)(sizeof(kProfNames) / sizeof(kProfNames[0]));
 
 template <int DIM, typename RP, typename V>
@@ -2926,16 +2947,18 @@ int profile_level_t(msrcg_hier* h, int k, int reps, cudaStream_t s, double* ms, 
   ls.thr = -1.0;
   MSRCG_CUDA_TRY(cudaMemcpyAsync(S, &st, sizeof(st), cudaMemcpyHostToDevice, s));
   const double n = (double)L.n, nc = (double)C.n, d = DIM, rsz = sizeof(RP), vsz = sizeof(V);
+  const double iv = rsz == sizeof(double) ? 0.5 : 0.0;  // FP64: one colour's 1/D read
   const double bytes_of[kProfCount] = {
-      (d + 1.5) * n * rsz,                                    // T, rp and z of one colour, the other colour's z
-      d * n * rsz + n * vsz + (vsz != rsz ? n * rsz : 0.0) + n * rsz,  // T, r (-> rp), z written
-      (d + 2.0) * n * rsz + n * vsz,                          // half-sweep + z and r of every cell
+      (d + 1.5 + iv) * n * rsz,                               // T, rp and z of one colour, the other colour's z
+      (iv > 0 ? iv * n * rsz : d * n * rsz) + n * vsz + (vsz != rsz ? n * rsz : 0.0) + n * rsz,  // T or 1/D, r (-> rp), z
+      (d + 2.0 + iv) * n * rsz + n * vsz,                     // half-sweep + z and r of every cell
       (d + 3.0) * n * rsz,                                    // T, rp, z, t
       (n + nc) * rsz,                                         // t, r_c
       (n + nc) * rsz,                                         // x_c, black z read and written
       n * rsz + 2.0 * n * vsz,                                // z, p read, p written
       (d + 2.0) * n * vsz,                                    // T (vector precision), p, q
-      6.0 * n * vsz};                                         // x, p, r, q read; x, r written
+      6.0 * n * vsz,                                          // x, p, r, q read; x, r written
+      (d + 1.0) * n * rsz};                                   // T read, 1/D written
   cudaEvent_t e0, e1;
   MSRCG_CUDA_TRY(cudaEventCreate(&e0));
   MSRCG_CUDA_TRY(cudaEventCreate(&e1));
@@ -2951,7 +2974,8 @@ int profile_level_t(msrcg_hier* h, int k, int reps, cudaStream_t s, double* ms, 
         case 5: k_prolong_black<DIM, RP><<<lp.grid, lp.block, 0, s>>>(L, C); break;
         case 6: k_direction<V, RP><<<ll.grid, ll.block, 0, s>>>(L, k, S); break;
         case 7: k_apply_dot<DIM, V><<<lc.grid, lc.block, 0, s>>>(L, k, S, part); break;
-        default: k_update<V, RP><<<lu.grid, lu.block, 0, s>>>(L, k, S, part, 0, 0); break;
+        case 8: k_update<V, RP><<<lu.grid, lu.block, 0, s>>>(L, k, S, part, 0, 0); break;
+        default: k_inv_diag<DIM, RP><<<lc.grid, lc.block, 0, s>>>(L); break;
       }
     };
     k_fill_ones<DIM, RP, V><<<lc.grid, lc.block, 0, s>>>(L, C);

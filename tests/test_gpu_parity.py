@@ -772,7 +772,7 @@ def test_profile_level_entry(M):
     prob = P.config_problem(1, scale=256)
     H = M.Hierarchy.from_problem(prob, M.default_opts(precision=1, inner_floor=1e-6))
     rows = H.profile_level(0, reps=3)
-    assert len(rows) == M.lib().msrcg_profile_kernel_count() == 9
+    assert len(rows) == M.lib().msrcg_profile_kernel_count() == 10
     assert all(r["ms"] > 0 and r["bytes"] > 0 and r["kernel"] for r in rows)
     with pytest.raises(M.MsrcgError):
         H.profile_level(H.nlev - 1)
