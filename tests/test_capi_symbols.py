@@ -49,3 +49,11 @@ def test_host_only_calls(libpath):
     assert (o.scale, o.m, abs(o.f - 0.1) < 1e-15, o.maxit_outer) == (4, 4, True, 200)
     assert M.strerror(M.EBREAKDOWN).startswith("conjugate gradient")
     assert M.lib().msrcg_default_opts(None) == M.EINVAL
+
+
+def test_set_trace_rejects_bad_arguments_on_the_host(libpath):
+    # argument checks only: no hierarchy is built, nothing runs on a device
+    from paper_math_9809043_gb300 import msrcg as M
+    L = M.lib()
+    assert L.msrcg_set_trace(None, None, 0) == M.EINVAL
+    assert L.msrcg_set_trace(None, None, 16) == M.EINVAL
