@@ -905,3 +905,22 @@ def test_level_tree_trace(M, prec):
     H.set_trace(0)
     x4, st4 = H.solve(b, 1e-8)
     assert st4["status"] == 0 and H.trace() == (0, [])
+
+
+@pytest.mark.parametrize("precond", [1, 2])
+def test_level_tree_without_inner_pcg(M, precond):
+    """Multigrid and polynomial preconditioning record the level-0 calls
+    alone (their inner levels run no PCG), as the oracle does."""
+    prob = P.grf_problem((200, 72), seed=21, ell=6.0, half_span=4.5)
+    opts = M.default_opts(precision=0, precond=precond, maxit_outer=2000)
+    H = M.Hierarchy.from_problem(prob, opts)
+    H.set_trace(64)
+    x, st = H.solve(H.rhs_for(prob), 1e-8)
+    assert st["status"] == 0
+    count, tr = H.trace()
+    assert count == len(tr) == st["calls"][0] and all(e[0] == 0 for e in tr)
+    assert sum(e[2] for e in tr) == st["iters"][0]
+    R = O.Hierarchy(prob, precond=precond, maxit_outer=2000)
+    xr, sr = R.solve(R.lift_rhs(), 1e-8, trace_cap=64)
+    assert len(sr["trace"]) == len(tr)
+    _counts_close([e[2] for e in tr], [e[2] for e in sr["trace"]], None)

@@ -1140,3 +1140,19 @@ def test_level_tree_of_the_oracle_has_the_recursion_structure():
     x2, st2 = R.solve(R.lift_rhs(), 1e-8, trace_cap=5)
     assert st2["trace_count"] == len(tr) and st2["trace"] == tr[:5]
     assert np.array_equal(x, x2)
+
+
+@pytest.mark.parametrize("precond", [1, 2])
+def test_level_tree_without_inner_pcg(precond):
+    """Multigrid (eq. 2.9) and polynomial (eq. 2.6) preconditioning run no
+    PCG below level 0: the level tree holds the level-0 calls alone, one per
+    pass, with the solve's iterations."""
+    prob = P.grf_problem((48, 40), seed=5, ell=4.0, half_span=3.0)
+    R = O.Hierarchy(prob, precond=precond, maxit_outer=2000)
+    x, st = R.solve(R.lift_rhs(), 1e-8, trace_cap=64)
+    assert st["status"] == 0
+    tr = st["trace"]
+    assert st["trace_count"] == len(tr) == st["calls"][0]
+    assert all(e[0] == 0 for e in tr)
+    assert [e[1] for e in tr] == list(range(len(tr))) and [e[3] for e in tr] == list(range(len(tr)))
+    assert sum(e[2] for e in tr) == st["iters"][0]
